@@ -1,0 +1,475 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA tests and the bench.
+
+This module holds no counting, prediction or fitting arithmetic: it only writes
+kernel descriptions in the affine loop-nest IR, draws tuning-space variants and
+parameter points, and draws weights / noisy timings that stand in for the
+paper's hardware measurement step (Fig. 1, "Hardware measurement").
+
+IR text format (one directive per line, tokens separated by blanks,
+expressions contain no blanks, ``#`` starts a comment)::
+
+    kernel NAME
+    param P1 [P2 ...]                       # at most 4 size parameters (Sec. 2, vector n)
+    array NAME global|local f32|f64 EXT[,EXT...]   # row-major extents, affine in params
+    dim NAME g0|g1|g2|l0|l1|l2|seq LO HI     # loop index range [LO, HI), quasi-affine in params
+    stmt NAME DIM[,DIM...]                   # an instruction, run once per point of its dims
+      guard LHS <|<=|>|>= RHS                # affine in the statement's dims and params
+      flop f32|f64 add|mul|div|pow|spec COUNT
+      load ARRAY[IDX,...] [x2|x4]
+      store ARRAY[IDX,...] [x2|x4]
+    end
+    barrier NAME DIM[,DIM...]                # one barrier per point of its (group/seq) dims
+
+The IR mirrors the Loopy model of a kernel (Sec. 3.1): a loop domain and scalar
+instructions, each executed once per integer point of the projection of the
+domain onto its own loop indices.  Barriers are explicit, as a schedule would
+place them (Sec. 3.2, last paragraph).  Group dims (g*) form the launch grid;
+local dims (l*) are work-item indices, l0 being the SIMD-lane axis used by the
+amortized stride fraction (Sec. 2.1).
+
+The eight templates follow the paper's measurement and test kernel families
+(Sec. 4.1, Sec. 5): vector add, axpy, strided copy, local-tile transpose,
+tiled matmul, 5-point stencil, local-memory tree reduction, batched matvec.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Sequence, Tuple
+
+import numpy as np
+
+TEMPLATES = ("vecadd", "axpy", "copy", "transpose", "matmul", "stencil", "reduction", "matvec")
+TEMPLATE_PARAMS = {
+    "vecadd": ("n",), "axpy": ("n",), "copy": ("n",), "transpose": ("n",),
+    "matmul": ("n", "m", "l"), "stencil": ("n",), "reduction": ("n",), "matvec": ("b",),
+}
+TILES = (8, 16, 32, 64)
+UNROLLS = (1, 2, 4, 8)
+WGS = (64, 128, 256, 512)
+STRIDES = (1, 2, 4, 8, 16)
+
+# Paper-style parameter box of the batched tuning workload.
+BOX_LO, BOX_HI = 64, 65536
+
+
+@dataclasses.dataclass(frozen=True)
+class Variant:
+    template: str
+    tx: int
+    ty: int
+    unroll: int
+    prefetch: bool
+    wg: int
+    stride: int = 1  # only meaningful for the strided copy
+
+    @property
+    def key(self) -> Tuple:
+        return (self.template, self.tx, self.ty, self.unroll, self.prefetch, self.wg, self.stride)
+
+    @property
+    def name(self) -> str:
+        return (f"{self.template}_t{self.tx}x{self.ty}_u{self.unroll}_p{int(self.prefetch)}"
+                f"_w{self.wg}" + (f"_s{self.stride}" if self.template == "copy" else ""))
+
+
+def _lin(terms: Sequence[Tuple[int, str]], const: int = 0) -> str:
+    """Render sum(coef*name) + const without blanks, dropping zero/empty terms."""
+    out = []
+    for c, v in terms:
+        if c == 0:
+            continue
+        out.append(v if c == 1 else f"{c}*{v}")
+    s = "+".join(out) if out else ""
+    if const:
+        s = f"{s}+{const}" if s else str(const) if const > 0 else str(const)
+        s = s.replace("+-", "-")
+    return s or "0"
+
+
+# --------------------------------------------------------------------------- templates
+
+def _one_d(v: Variant, dtype: str, body) -> str:
+    """Shared 1-D blocking: E = tx*ty elements per group, wg items, E/wg per item."""
+    E, W, u = v.tx * v.ty, v.wg, v.unroll
+    R = E // W
+    X = _lin([(E, "g"), (u * W, "ro"), (W, "ri"), (1, "l")])
+    lines = [
+        f"dim g g0 0 ceil(n/{E})",
+        f"dim ro seq 0 {R // u}",
+        f"dim ri seq 0 {u}",
+        f"dim l l0 0 {W}",
+        "stmt body g,ro,ri,l",
+        f"guard {X} < n",
+    ]
+    lines += body(X)
+    lines.append("end")
+    return "\n".join(lines)
+
+
+def ir_vecadd(v: Variant) -> str:
+    head = [f"kernel {v.name}", "param n",
+            "array a global f32 n", "array b global f32 n", "array c global f32 n"]
+    body = lambda X: [f"load a[{X}]", f"load b[{X}]", "flop f32 add 1", f"store c[{X}]"]
+    return "\n".join(head) + "\n" + _one_d(v, "f32", body) + "\n"
+
+
+def ir_axpy(v: Variant) -> str:
+    head = [f"kernel {v.name}", "param n", "array x global f64 n", "array y global f64 n"]
+    body = lambda X: [f"load x[{X}]", f"load y[{X}]", "flop f64 mul 1", "flop f64 add 1",
+                      f"store y[{X}]"]
+    return "\n".join(head) + "\n" + _one_d(v, "f64", body) + "\n"
+
+
+def ir_copy(v: Variant) -> str:
+    s = v.stride
+    head = [f"kernel {v.name}", "param n", f"array a global f32 {s}*n" if s > 1 else
+            "array a global f32 n", "array b global f32 n"]
+    body = lambda X: [f"load a[{s}*({X})]" if s > 1 else f"load a[{X}]", f"store b[{X}]"]
+    return "\n".join(head) + "\n" + _one_d(v, "f32", body) + "\n"
+
+
+def ir_reduction(v: Variant) -> str:
+    E, W, u = v.tx * v.ty, v.wg, v.unroll
+    R = E // W
+    X = _lin([(E, "g"), (u * W, "ro"), (W, "ri"), (1, "l")])
+    L = [f"kernel {v.name}", "param n",
+         "array a global f32 n", f"array out global f32 ceil(n/{E})", f"array s local f32 {W}",
+         f"dim g g0 0 ceil(n/{E})", f"dim ro seq 0 {R // u}", f"dim ri seq 0 {u}",
+         f"dim l l0 0 {W}",
+         "stmt acc g,ro,ri,l", f"guard {X} < n", f"load a[{X}]", "flop f32 add 1", "end",
+         "stmt put g,l", "store s[l]", "end",
+         "barrier b0 g"]
+    stages = int(math.log2(W))
+    S = W // 2
+    for k in range(1, stages + 1):
+        L += [f"stmt r{k} g,l", f"guard l < {S}", "load s[l]", f"load s[l+{S}]",
+              "flop f32 add 1", "store s[l]", "end"]
+        if k < stages:
+            L.append(f"barrier b{k} g")
+        S //= 2
+    L += ["stmt fin g", "load s[0]", "store out[g]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_transpose(v: Variant) -> str:
+    T, W, u = v.tx, v.wg, v.unroll
+    WY = W // T
+    RY = T // WY
+    R = _lin([(u * WY, "ro"), (WY, "ri"), (1, "ly")])
+    Y = _lin([(T, "gy"), (u * WY, "ro"), (WY, "ri"), (1, "ly")])
+    X = _lin([(T, "gx"), (1, "lx")])
+    Yt = _lin([(T, "gx"), (u * WY, "ro"), (WY, "ri"), (1, "ly")])   # output row
+    Xt = _lin([(T, "gy"), (1, "lx")])                               # output col
+    dims = "gx,gy,ro,ri,ly,lx"
+    L = [f"kernel {v.name}", "param n", "array in global f32 n,n", "array out global f32 n,n"]
+    if v.prefetch:
+        L.append(f"array t local f32 {T},{T + 1}")
+    L += [f"dim gx g0 0 ceil(n/{T})", f"dim gy g1 0 ceil(n/{T})",
+          f"dim ro seq 0 {RY // u}", f"dim ri seq 0 {u}",
+          f"dim ly l1 0 {WY}", f"dim lx l0 0 {T}"]
+    if v.prefetch:
+        L += [f"stmt ld {dims}", f"guard {Y} < n", f"guard {X} < n",
+              f"load in[{Y},{X}]", f"store t[{R},lx]", "end",
+              "barrier b1 gx,gy",
+              f"stmt st {dims}", f"guard {Yt} < n", f"guard {Xt} < n",
+              f"load t[lx,{R}]", f"store out[{Yt},{Xt}]", "end"]
+    else:
+        L += [f"stmt cp {dims}", f"guard {Y} < n", f"guard {X} < n",
+              f"load in[{Y},{X}]", f"store out[{X},{Y}]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_matmul(v: Variant) -> str:
+    TX, TY, W, u = v.tx, v.ty, v.wg, v.unroll
+    WY = W // TX
+    RY, RK = TY // WY, TX // WY
+    Y = _lin([(TY, "gy"), (WY, "ry"), (1, "ly")])
+    X = _lin([(TX, "gx"), (1, "lx")])
+    L = [f"kernel {v.name}", "param n m l",
+         "array A global f32 n,m", "array B global f32 m,l", "array C global f32 n,l"]
+    if v.prefetch:
+        L += [f"array As local f32 {TY},{TX}", f"array Bs local f32 {TX},{TX}"]
+    L += [f"dim gx g0 0 ceil(l/{TX})", f"dim gy g1 0 ceil(n/{TY})",
+          f"dim ry seq 0 {RY}", f"dim ly l1 0 {WY}", f"dim lx l0 0 {TX}"]
+    if v.prefetch:
+        K = _lin([(TX, "kt"), (u, "ko"), (1, "ki")])
+        Kb = _lin([(TX, "kt"), (WY, "rk"), (1, "ly")])
+        L += [f"dim kt seq 0 ceil(m/{TX})", f"dim rk seq 0 {RK}",
+              f"dim ko seq 0 {TX // u}", f"dim ki seq 0 {u}",
+              "stmt lda gx,gy,kt,ry,ly,lx", f"guard {Y} < n", f"guard {_lin([(TX, 'kt'), (1, 'lx')])} < m",
+              f"load A[{Y},{_lin([(TX, 'kt'), (1, 'lx')])}]", f"store As[{_lin([(WY, 'ry'), (1, 'ly')])},lx]", "end",
+              "stmt ldb gx,gy,kt,rk,ly,lx", f"guard {Kb} < m", f"guard {X} < l",
+              f"load B[{Kb},{X}]", f"store Bs[{_lin([(WY, 'rk'), (1, 'ly')])},lx]", "end",
+              "barrier b1 gx,gy,kt",
+              "stmt mac gx,gy,kt,ry,ko,ki,ly,lx", f"guard {Y} < n", f"guard {X} < l", f"guard {K} < m",
+              f"load As[{_lin([(WY, 'ry'), (1, 'ly')])},{_lin([(u, 'ko'), (1, 'ki')])}]",
+              f"load Bs[{_lin([(u, 'ko'), (1, 'ki')])},lx]",
+              "flop f32 mul 1", "flop f32 add 1", "end",
+              "barrier b2 gx,gy,kt"]
+    else:
+        Km = _lin([(u, "ko"), (1, "ki")])
+        L += [f"dim ko seq 0 floor(m/{u})", f"dim ki seq 0 {u}",
+              f"dim kr seq {u}*floor(m/{u}) m" if u > 1 else "dim kr seq m m",
+              "stmt mac gx,gy,ry,ko,ki,ly,lx", f"guard {Y} < n", f"guard {X} < l",
+              f"load A[{Y},{Km}]", f"load B[{Km},{X}]", "flop f32 mul 1", "flop f32 add 1", "end",
+              "stmt rem gx,gy,ry,kr,ly,lx", f"guard {Y} < n", f"guard {X} < l",
+              f"load A[{Y},kr]", f"load B[kr,{X}]", "flop f32 mul 1", "flop f32 add 1", "end"]
+    L += ["stmt st gx,gy,ry,ly,lx", f"guard {Y} < n", f"guard {X} < l",
+          f"store C[{Y},{X}]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_stencil(v: Variant) -> str:
+    TX, TY, W, u = v.tx, v.ty, v.wg, v.unroll
+    WY = W // TX
+    RY = TY // WY
+    R = _lin([(u * WY, "ro"), (WY, "ri"), (1, "ly")])
+    Y1 = _lin([(TY, "gy"), (u * WY, "ro"), (WY, "ri"), (1, "ly")], 1)   # interior row
+    X1 = _lin([(TX, "gx"), (1, "lx")], 1)                               # interior col
+    dims = "gx,gy,ro,ri,ly,lx"
+    L = [f"kernel {v.name}", "param n", "array u global f32 n,n", "array v global f32 n,n"]
+    if v.prefetch:
+        L.append(f"array t local f32 {TY + 2},{TX + 2}")
+    L += [f"dim gx g0 0 ceil((n-2)/{TX})", f"dim gy g1 0 ceil((n-2)/{TY})",
+          f"dim ro seq 0 {RY // u}", f"dim ri seq 0 {u}",
+          f"dim ly l1 0 {WY}", f"dim lx l0 0 {TX}"]
+    flops = ["flop f32 add 4", "flop f32 mul 2"]
+    if v.prefetch:
+        L += [f"stmt c {dims}", f"guard {Y1} < n", f"guard {X1} < n",
+              f"load u[{Y1},{X1}]", f"store t[{R}+1,lx+1]", "end",
+              "stmt ht gx,gy,lx", f"guard {X1} < n",
+              f"load u[{TY}*gy,{X1}]", "store t[0,lx+1]", "end",
+              "stmt hb gx,gy,lx", f"guard {TY}*gy+{TY + 1} < n", f"guard {X1} < n",
+              f"load u[{TY}*gy+{TY + 1},{X1}]", f"store t[{TY + 1},lx+1]", "end",
+              "stmt hl gx,gy,ro,ri,ly", f"guard {Y1} < n",
+              f"load u[{Y1},{TX}*gx]", f"store t[{R}+1,0]", "end",
+              "stmt hr gx,gy,ro,ri,ly", f"guard {TX}*gx+{TX + 1} < n", f"guard {Y1} < n",
+              f"load u[{Y1},{TX}*gx+{TX + 1}]", f"store t[{R}+1,{TX + 1}]", "end",
+              "barrier b1 gx,gy",
+              f"stmt pt {dims}", f"guard {Y1} < n-1", f"guard {X1} < n-1",
+              f"load t[{R},lx+1]", f"load t[{R}+2,lx+1]", f"load t[{R}+1,lx]",
+              f"load t[{R}+1,lx+2]", f"load t[{R}+1,lx+1]"] + flops + [f"store v[{Y1},{X1}]", "end"]
+    else:
+        L += [f"stmt pt {dims}", f"guard {Y1} < n-1", f"guard {X1} < n-1",
+              f"load u[{Y1}-1,{X1}]", f"load u[{Y1}+1,{X1}]", f"load u[{Y1},{X1}-1]",
+              f"load u[{Y1},{X1}+1]", f"load u[{Y1},{X1}]"] + flops + [f"store v[{Y1},{X1}]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_matvec(v: Variant) -> str:
+    W, u = v.wg, v.unroll
+    MPG = W // 32
+    M = _lin([(MPG, "g"), (1, "lm")])
+    K = _lin([(u, "ko"), (1, "ki")])
+    L = [f"kernel {v.name}", "param b", "array A global f64 b,32,32",
+         "array x global f64 b,32", "array y global f64 b,32"]
+    if v.prefetch:
+        L.append(f"array xs local f64 {MPG},32")
+    L += [f"dim g g0 0 ceil(b/{MPG})", f"dim lm l1 0 {MPG}", "dim lr l0 0 32",
+          f"dim ko seq 0 {32 // u}", f"dim ki seq 0 {u}"]
+    if v.prefetch:
+        L += ["stmt lx g,lm,lr", f"guard {M} < b", f"load x[{M},lr]", "store xs[lm,lr]", "end",
+              "barrier b1 g",
+              "stmt mac g,lm,lr,ko,ki", f"guard {M} < b", f"load A[{M},lr,{K}]",
+              f"load xs[lm,{K}]", "flop f64 mul 1", "flop f64 add 1", "end"]
+    else:
+        L += ["stmt mac g,lm,lr,ko,ki", f"guard {M} < b", f"load A[{M},lr,{K}]",
+              f"load x[{M},{K}]", "flop f64 mul 1", "flop f64 add 1", "end"]
+    L += ["stmt st g,lm,lr", f"guard {M} < b", f"store y[{M},lr]", "end"]
+    return "\n".join(L) + "\n"
+
+
+_IR = {"vecadd": ir_vecadd, "axpy": ir_axpy, "copy": ir_copy, "transpose": ir_transpose,
+       "matmul": ir_matmul, "stencil": ir_stencil, "reduction": ir_reduction, "matvec": ir_matvec}
+
+
+def variant_ir(v: Variant) -> str:
+    if not valid(v):
+        raise ValueError(f"invalid variant {v}")
+    return _IR[v.template](v)
+
+
+def valid(v: Variant) -> bool:
+    """Which knob combinations are meaningful for each template (others are redrawn)."""
+    t, tx, ty, u, p, W = v.template, v.tx, v.ty, v.unroll, v.prefetch, v.wg
+    if v.stride != 1 and t != "copy":
+        return False
+    if t in ("vecadd", "axpy", "copy", "reduction"):
+        E = tx * ty
+        return (not p) and E % W == 0 and (E // W) % u == 0
+    if t == "transpose":
+        if tx != ty or W > tx * tx or W % tx:
+            return False
+        WY = W // tx
+        return tx % WY == 0 and (tx // WY) % u == 0
+    if t == "matmul":
+        if W % tx:
+            return False
+        WY = W // tx
+        if WY > ty or ty % WY or tx % WY:
+            return False
+        return (tx % u == 0) if p else True
+    if t == "stencil":
+        if W % tx:
+            return False
+        WY = W // tx
+        return WY <= ty and ty % WY == 0 and ((ty // WY) % u == 0)
+    if t == "matvec":
+        return (tx, ty) == (8, 8) and 32 % u == 0
+    return False
+
+
+def canonical(template: str, stride: int = 1) -> Variant:
+    """The fixed small-workload instance: 16x16 tile, 256-item groups, no unroll,
+    local prefetch where it applies."""
+    pre = template in ("transpose", "matmul", "stencil", "matvec")
+    tx, ty = (8, 8) if template == "matvec" else (16, 16)
+    return Variant(template, tx, ty, 1, pre, 256, stride)
+
+
+def all_variants() -> List[Variant]:
+    out = []
+    for t in TEMPLATES:
+        for tx in TILES:
+            for ty in TILES:
+                for u in UNROLLS:
+                    for p in (False, True):
+                        for W in WGS:
+                            for s in (STRIDES if t == "copy" else (1,)):
+                                v = Variant(t, tx, ty, u, p, W, s)
+                                if valid(v):
+                                    out.append(v)
+    return out
+
+
+def draw_variants(n_variants: int, seed: int = 2) -> List[Variant]:
+    """Draw variants with replacement from the tuning space: template, tile in
+    {8..64}^2, unroll in {1,2,4,8}, prefetch on/off, work-group size in {64..512}.
+    Invalid combinations are redrawn, so duplicates occur (exact prediction ties)."""
+    rng = np.random.default_rng(seed)
+    out: List[Variant] = []
+    while len(out) < n_variants:
+        t = TEMPLATES[rng.integers(len(TEMPLATES))]
+        v = Variant(t, int(rng.choice(TILES)), int(rng.choice(TILES)), int(rng.choice(UNROLLS)),
+                    bool(rng.integers(2)), int(rng.choice(WGS)),
+                    int(rng.choice(STRIDES)) if t == "copy" else 1)
+        if valid(v):
+            out.append(v)
+    return out
+
+
+def group_by_template(variants: Sequence[Variant]) -> Dict[str, List[int]]:
+    g: Dict[str, List[int]] = {t: [] for t in TEMPLATES}
+    for i, v in enumerate(variants):
+        g[v.template].append(i)
+    return g
+
+
+def draw_points(n_params: int, n_points: int, seed: int, lo: int = BOX_LO, hi: int = BOX_HI) -> np.ndarray:
+    """Log-uniform integer parameter points in [lo, hi], int64 [n_points][n_params]."""
+    rng = np.random.default_rng(seed)
+    x = np.exp(rng.uniform(math.log(lo), math.log(hi + 1), size=(n_points, n_params)))
+    return np.clip(np.floor(x), lo, hi).astype(np.int64)
+
+
+def template_points(seed: int, n_points: int, lo: int = BOX_LO, hi: int = BOX_HI) -> Dict[str, np.ndarray]:
+    """One independent point set per template (seed offset by template index)."""
+    return {t: draw_points(len(TEMPLATE_PARAMS[t]), n_points, seed * 1000 + i, lo, hi)
+            for i, t in enumerate(TEMPLATES)}
+
+
+def draw_weights(k: int, n_models: int, seed: int, lo: float = 1e-12, hi: float = 1e-9) -> np.ndarray:
+    """Per-device weight vectors, uniform in [lo, hi] (units: seconds per operation)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(n_models, k))
+
+
+# --------------------------------------------------------------------------- small workload
+
+POW2_SMALL = (64, 128, 256)
+
+
+def tiny_points(template: str, n_points: int = 32, sizes: Sequence[int] = POW2_SMALL,
+                seed: int = 1) -> np.ndarray:
+    """Points of the small workload: powers of two from ``sizes``, taken from the
+    product grid for multi-parameter templates and cycled/padded otherwise."""
+    P = len(TEMPLATE_PARAMS[template])
+    grid = np.array(np.meshgrid(*([list(sizes)] * P), indexing="ij")).reshape(P, -1).T
+    rng = np.random.default_rng(seed)
+    if len(grid) >= n_points:
+        idx = rng.choice(len(grid), n_points, replace=False)
+        return grid[np.sort(idx)].astype(np.int64)
+    reps = int(math.ceil(n_points / len(grid)))
+    return np.tile(grid, (reps, 1))[:n_points].astype(np.int64)
+
+
+def tiny_variants() -> List[Variant]:
+    """The eight templates of the small workload; the strided copy takes s = 4."""
+    return [canonical(t, 4 if t == "copy" else 1) for t in TEMPLATES]
+
+
+# --------------------------------------------------------------------------- fit inputs
+
+def fit_features(rows: int, k: int = 32, seed: int = 5) -> np.ndarray:
+    """Feature rows shaped like the paper's measurement-kernel families (Sec. 4.1):
+    each row belongs to one family whose nonzero columns and size scaling
+    (n, n^2 or n^3 with log-uniform n) mimic that family's counts.  int64 [rows][k].
+    Column magnitudes span roughly 1e2..1e13."""
+    rng = np.random.default_rng(seed)
+    F = np.zeros((rows, k), dtype=np.int64)
+    fam = rng.integers(0, 8, size=rows)
+    n = np.exp(rng.uniform(math.log(2**8), math.log(2**13), size=rows))
+    n1 = np.floor(n * 64).astype(np.int64)            # 1-D sizes up to ~5e5
+    n2 = np.floor(n).astype(np.int64)                 # 2-D sizes
+    wg = rng.choice([128, 256, 512], size=rows)
+    F[:, 0] = 1
+    def put(mask, col, val):
+        F[mask, col] = np.asarray(val)[mask]
+    for f in range(8):
+        msk = fam == f
+        if f == 0:   # stride-1 streaming (copy / add arrays)
+            nl = rng.integers(0, 5, size=rows)
+            put(msk, 17, n1 * np.maximum(nl, 1)); put(msk, 24, n1); put(msk, 3, n1 * np.maximum(nl - 1, 0))
+            put(msk, 1, (n1 + wg - 1) // wg)
+        elif f == 1:  # strided vector scale-add (stride 2 or 3)
+            put(msk, 19, 2 * n1); put(msk, 24, n1); put(msk, 4, 2 * n1); put(msk, 3, n1)
+            put(msk, 1, (n1 + wg - 1) // wg)
+        elif f == 2:  # transpose, no prefetch
+            put(msk, 17, n2 * n2); put(msk, 26, n2 * n2); put(msk, 1, (n2 * n2 + 255) // 256)
+        elif f == 3:  # transpose, prefetch
+            put(msk, 17, n2 * n2); put(msk, 24, n2 * n2); put(msk, 13, n2 * n2); put(msk, 15, n2 * n2)
+            put(msk, 2, (n2 * n2 + 255) // 256); put(msk, 1, (n2 * n2 + 255) // 256)
+        elif f == 4:  # tiled matmul
+            nn = np.minimum(n2, 2048)
+            put(msk, 3, nn ** 3); put(msk, 4, nn ** 3); put(msk, 13, 2 * nn ** 3)
+            put(msk, 17, 2 * nn ** 3 // 16); put(msk, 15, 2 * nn ** 3 // 16); put(msk, 24, nn * nn)
+            put(msk, 2, 2 * (nn // 16) ** 3); put(msk, 1, (nn // 16) ** 2)
+        elif f == 5:  # naive matmul
+            nn = np.minimum(n2, 1024)
+            put(msk, 3, nn ** 3); put(msk, 4, nn ** 3); put(msk, 16, nn ** 3); put(msk, 17, nn ** 3)
+            put(msk, 24, nn * nn); put(msk, 1, (nn * nn + 255) // 256)
+        elif f == 6:  # arithmetic kernels (one op kind each)
+            kk = rng.choice([256, 512, 728], size=rows)
+            col = rng.choice([3, 4, 5, 6, 7], size=rows)
+            nn = np.minimum(n2, 1024)
+            for c in (3, 4, 5, 6, 7):
+                put(msk & (col == c), c, nn * nn * kk * rng.integers(6, 11, size=rows))
+            put(msk, 24, nn * nn); put(msk, 1, (nn * nn + 255) // 256)
+        else:         # empty kernel
+            put(msk, 1, (n2 * n2 + 255) // 256)
+    # Sparse remaining columns get an independent small family so every column is informative.
+    extra = rng.integers(0, k, size=rows)
+    for c in range(k):
+        msk = (extra == c) & (F[:, c] == 0)
+        F[msk, c] = n1[msk] * rng.integers(1, 4, size=rows)[msk]
+    return F
+
+
+def synth_timings(F: np.ndarray, w_true: np.ndarray, seed: int = 6, sigma: float = 0.05) -> np.ndarray:
+    """Stand-in for timing measurement kernels on hardware: t = (F w_true) * exp(e),
+    e ~ N(0, sigma^2), one column per device model.  fp64 [rows][models]."""
+    rng = np.random.default_rng(seed)
+    clean = F.astype(np.float64) @ np.asarray(w_true, dtype=np.float64).T
+    e = rng.normal(0.0, sigma, size=clean.shape)
+    return clean * np.exp(e)
