@@ -1,0 +1,335 @@
+"""Benchmark of the batched tuning workload: 10,000 kernel variants drawn from the
+tuning space over eight templates, 4,096 log-uniform parameter points per
+template, every (variant, point) pair evaluated (exact int64 counts), predicted
+(FP64-accurate) and ranked (top-16 per point) in one persistent launch.
+
+One step = one pass of that whole path over the batch.  Prints one JSON line.
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank runs the same per-GPU batch (weak scaling); no
+data-path collective, the process group only brackets the timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "model evals/s (variant x param points), fused evaluate+predict+top-16"
+UNIT = "evals/s"
+WORKLOAD = "batched tuning space: 10,000 variants x 4,096 points per template, 8 templates, top-16, FP64-accurate"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class Clocks:
+    """Samples nvidia-smi during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        def run():
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                         timeout=5).stdout.strip()
+                    if out:
+                        self.rows.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            for i, n in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(bp, w, target_s: float = 8.0):
+    """The oracle (structural counts + compensated dot + insertion top-16), as it
+    stands, on all host cores, on a bounded sample of the same workload: every
+    variant of every template, the first n points of each template."""
+    import numpy as np
+
+    import oracle
+    from paper_1604_04997_gb300 import workloads as W
+    cores = os.cpu_count() or 1
+    kern = {}
+    per_t = []
+    for ti, t in enumerate(bp.templates):
+        vs = bp.variants[bp.var_off[ti]:bp.var_off[ti + 1]]
+        ks = []
+        for v in vs:
+            if v.key not in kern:
+                kern[v.key] = oracle.Kernel(W.variant_ir(v))
+            ks.append(kern[v.key])
+        per_t.append(ks)
+    n = 8
+    while True:
+        evals = 0
+        t0 = time.perf_counter()
+        for ti, t in enumerate(bp.templates):
+            if not per_t[ti]:
+                continue
+            P = len(W.TEMPLATE_PARAMS[t])
+            p0 = int(bp.pt_off[ti])
+            pts = np.ascontiguousarray(bp.points[p0:p0 + n, :P])
+            oracle.eval_predict_topk(per_t[ti], pts, w, 16, n_threads=cores)
+            evals += len(per_t[ti]) * len(pts)
+        dt = time.perf_counter() - t0
+        if dt >= target_s or n >= 4096:
+            break
+        n = min(4096, max(n * 2, int(n * target_s / max(dt, 1e-3) * 1.1)))
+    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {len(bp.variants)} variants x first {n} points of each template "
+                      f"({evals} evals, {dt:.1f} s, OpenMP over points)"}
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1604_04997_gb300 import binding as B
+    from paper_1604_04997_gb300 import tuning
+    from paper_1604_04997_gb300 import workloads as W
+    import __graft_entry__
+    __graft_entry__.build()
+    ctx = B.Context(-1)
+    bp = tuning.build(ctx, args.variants, args.points)
+    w = W.draw_weights(32, 1, 4)[0]
+    base = cpu_baseline(bp, w, target_s=args.ref_step_s)
+    # each step: the same bounded sample as the baseline
+    n_pts = int(base["sample"].split("first ")[1].split(" points")[0])
+    kern, per_t = {}, []
+    for ti, t in enumerate(bp.templates):
+        ks = []
+        for v in bp.variants[bp.var_off[ti]:bp.var_off[ti + 1]]:
+            if v.key not in kern:
+                kern[v.key] = oracle.Kernel(W.variant_ir(v))
+            ks.append(kern[v.key])
+        per_t.append(ks)
+
+    def step():
+        ev = 0
+        for ti, t in enumerate(bp.templates):
+            if per_t[ti]:
+                P = len(W.TEMPLATE_PARAMS[t])
+                p0 = int(bp.pt_off[ti])
+                pts = np.ascontiguousarray(bp.points[p0:p0 + n_pts, :P])
+                oracle.eval_predict_topk(per_t[ti], pts, w, 16, n_threads=base["cores"])
+                ev += len(per_t[ti]) * len(pts)
+        return ev
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    ev = 0
+    for _ in range(args.steps):
+        ev += step()
+    dt = time.perf_counter() - t0
+    value = ev / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (CPU oracle on a bounded sample per step)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
+                             "sample": base["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1604_04997_gb300 import binding as B
+    from paper_1604_04997_gb300 import tuning
+    from paper_1604_04997_gb300 import workloads as W
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    __graft_entry__.build()
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ctx = B.Context(local)
+    ctx.tune(True, None)
+    bp = tuning.build(ctx, args.variants, args.points)
+    w = W.draw_weights(32, 1, 4)[0]
+    n = bp.points.shape[0]
+    stream = torch.cuda.Stream(dev)
+    d_pts = torch.from_numpy(bp.points).to(dev)
+    d_w = torch.from_numpy(w).to(dev)
+    idx = torch.empty((n, 16), dtype=torch.int32, device=dev)
+    tt = torch.empty((n, 16), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)   # 256 MB > L2
+
+    def step(s):
+        ctx.eval_predict_topk(bp.tables, bp.var_off, d_pts, bp.pt_off, d_w, 16, idx, tt, stream=s)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step(stream)
+    torch.cuda.synchronize()
+    ctx.sync_status(stream)
+    info = ctx.plan_info(bp.tables, bp.var_off, bp.pt_off)
+
+    clocks = Clocks(local)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.zero_()                                   # L2 flush between timed steps (not timed)
+            ev0[i].record(stream)
+            step(stream)
+            ev1[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    ctx.sync_status(stream)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    ms = sum(step_ms) / len(step_ms)
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+
+    # end to end through the C ABI with host buffers: points H2D, ranking D2H, every step
+    h_pts = torch.from_numpy(bp.points).pin_memory()
+    h_idx = torch.empty((n, 16), dtype=torch.int32).pin_memory()
+    h_t = torch.empty((n, 16), dtype=torch.float64).pin_memory()
+    e_steps = max(3, args.steps)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(e_steps):
+            d_pts.copy_(h_pts, non_blocking=True)
+            step(stream)
+            h_idx.copy_(idx, non_blocking=True)
+            h_t.copy_(tt, non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    evals = bp.total_evals
+    value = evals * ws / (ms / 1e3)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * 128 * max_mhz * 1e6           # lane-instruction issue rate at the maximum clock
+    achieved = evals * info["work_per_eval"] / (ms / 1e3)
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "eval_predict_topk_traffic.json")
+    if os.path.exists(prof):
+        try:
+            traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64 counts, fp32-compensated (FP64-accurate) predict",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "variants": len(bp.variants), "distinct_variants": bp.n_distinct,
+                       "points_per_template": args.points, "evals_per_step": evals, "topk": 16,
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "launch": {"warps_per_cta": info["nw"], "ctas": info["grid"], "units": info["units"]},
+                       "timed_region_wall_ms": wall * 1e3},
+            "e2e": {"value": evals * ws / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(bp.points.nbytes),
+                    "d2h_bytes_per_step": int(n * 16 * (4 + 8))},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T lane-ops/s", "frac": achieved / peak_ops, "traffic": traffic,
+                         "kernel": "k_eval_predict_topk",
+                         "ops_per_eval": info["work_per_eval"],
+                         "peak_note": f"{sms} SMs x 128 lanes x {max_mhz:.0f} MHz (issue bound, derived)"},
+            "clocks": ck,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(bp, w, target_s=args.cpu_s)
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variants", type=int, default=10000)
+    ap.add_argument("--points", type=int, default=4096)
+    ap.add_argument("--cpu-s", type=float, default=8.0)
+    ap.add_argument("--ref-step-s", type=float, default=4.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+// Host side of the C ABI: context, resident tables, argument checks, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pm.h"
+#include "pm_internal.h"
+#include "pm_table.h"
+
+int pm_compile_table(const char *ir, size_t len, int layout, const int64_t *plo, const int64_t *phi,
+                     std::vector<uint32_t> &words, int info[8], std::string &msg);
+
+static thread_local std::string g_err;
+
+pm_status pm_set_error(pm_status code, const std::string &m) {
+  g_err = m;
+  return code;
+}
+
+extern "C" const char *pm_last_error(void) { return g_err.c_str(); }
+
+#define CU(x)                                                                                          \
+  do {                                                                                                 \
+    cudaError_t e__ = (x);                                                                             \
+    if (e__ != cudaSuccess) return pm_set_error(PM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+// ------------------------------------------------------------------------------------- context
+
+pm_status ctx_device_guard(pm_ctx *c) {
+  if (!c) return pm_set_error(PM_ERR_INVALID_ARG, "null context");
+  if (c->device < 0) return pm_set_error(PM_ERR_INVALID_ARG, "host-only context has no device");
+  CU(cudaSetDevice(c->device));
+  return PM_OK;
+}
+
+extern "C" pm_status pm_create(pm_ctx **out, int device, size_t mem_budget_bytes) {
+  if (!out) return pm_set_error(PM_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  std::unique_ptr<pm_ctx> c(new pm_ctx());
+  c->device = device;
+  c->budget = mem_budget_bytes ? mem_budget_bytes : (size_t(16) << 30);
+  if (device >= 0) {
+    int n = 0;
+    CU(cudaGetDeviceCount(&n));
+    if (device >= n) return pm_set_error(PM_ERR_INVALID_ARG, "no such device");
+    CU(cudaSetDevice(device));
+    CU(cudaMalloc(&c->d_status, sizeof(int)));
+    CU(cudaMemset(c->d_status, 0, sizeof(int)));
+    CU(cudaMallocHost(&c->h_status, sizeof(int)));
+    CU(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, device));
+  }
+  *out = c.release();
+  return PM_OK;
+}
+
+extern "C" void pm_destroy(pm_ctx *c) {
+  if (!c) return;
+  pm_serve_stop(c);
+  if (c->device >= 0) {
+    cudaSetDevice(c->device);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->dcache) cudaFree(kv.second);
+    for (auto &kv : c->plans) {
+      if (kv.second->graph_exec) cudaGraphExecDestroy(kv.second->graph_exec);
+      for (void *p : kv.second->dev) cudaFree(p);
+    }
+    cudaFree(c->arena);
+    cudaFree(c->d_status);
+    cudaFree(c->scratch);
+    cudaFreeHost(c->h_status);
+  }
+  delete c;
+}
+
+extern "C" pm_status pm_sync_status(pm_ctx *c, void *stream) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  cudaStream_t st = (cudaStream_t)stream;
+  CU(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemsetAsync(c->d_status, 0, sizeof(int), st));
+  CU(cudaStreamSynchronize(st));
+  int s = *c->h_status;
+  if (s & pmd::ST_OUT_OF_BOX) return pm_set_error(PM_ERR_OUT_OF_BOX, "a parameter point lies outside its table's box");
+  if (s & pmd::ST_BAD_TABLE) return pm_set_error(PM_ERR_INVALID_ARG, "malformed table reached the device");
+  if (s & pmd::ST_TIMEOUT) return pm_set_error(PM_ERR_TIMEOUT, "a device wait ran out");
+  return PM_OK;
+}
+
+// Device copy of a small host array, cached by content (schedules, offsets).
+pm_status ctx_dcopy(pm_ctx *c, const void *h, size_t bytes, void **d) {
+  std::string key((const char *)h, bytes);
+  auto it = c->dcache.find(key);
+  if (it != c->dcache.end()) { *d = it->second; return PM_OK; }
+  if (c->dcache.size() > 4096) {
+    CU(cudaDeviceSynchronize());
+    for (auto &kv : c->dcache) cudaFree(kv.second);
+    c->dcache.clear();
+  }
+  void *p = nullptr;
+  CU(cudaMalloc(&p, std::max<size_t>(bytes, 16)));
+  CU(cudaMemcpy(p, h, bytes, cudaMemcpyHostToDevice));
+  c->dcache[key] = p;
+  *d = p;
+  return PM_OK;
+}
+
+pm_status ctx_scratch(pm_ctx *c, size_t bytes, void **d) {
+  if (bytes > c->scratch_cap) {
+    CU(cudaDeviceSynchronize());
+    cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_cap = 0;
+    CU(cudaMalloc(&c->scratch, bytes));
+    c->scratch_cap = bytes;
+  }
+  *d = c->scratch;
+  return PM_OK;
+}
+
+static pm_status upload_table(pm_ctx *c, int id) {
+  const auto &w = c->tables[id];
+  size_t need = c->arena_used + w.size();
+  if (need > c->arena_cap) {
+    size_t cap = std::max<size_t>(need * 2, size_t(1) << 20);
+    uint32_t *na = nullptr;
+    CU(cudaMalloc(&na, cap * 4));
+    if (c->arena_used) CU(cudaMemcpy(na, c->arena, c->arena_used * 4, cudaMemcpyDeviceToDevice));
+    CU(cudaDeviceSynchronize());
+    cudaFree(c->arena);
+    c->arena = na;
+    c->arena_cap = cap;
+  }
+  CU(cudaMemcpy(c->arena + c->arena_used, w.data(), w.size() * 4, cudaMemcpyHostToDevice));
+  c->dev_off[id] = (int64_t)c->arena_used;
+  c->arena_used += w.size();
+  return PM_OK;
+}
+
+// ------------------------------------------------------------------------------------- counting
+
+extern "C" pm_status pm_compile_counts(pm_ctx *c, const char *ir, size_t len, int32_t layout, const int64_t *lo,
+                                       const int64_t *hi, int32_t *out_id, pm_table_info *info) {
+  if (!c || !ir || !lo || !hi || !out_id) return pm_set_error(PM_ERR_INVALID_ARG, "null argument");
+  if (layout != PM_LAYOUT_12 && layout != PM_LAYOUT_32) return pm_set_error(PM_ERR_INVALID_ARG, "layout must be 12 or 32");
+  std::vector<uint32_t> words;
+  int inf[8];
+  std::string msg;
+  int rc = pm_compile_table(ir, len, layout, lo, hi, words, inf, msg);
+  if (rc) return pm_set_error(rc, msg);
+  std::lock_guard<std::mutex> lk(c->mu);
+  int id = (int)c->tables.size();
+  c->tables.push_back(std::move(words));
+  c->dev_off.push_back(-1);
+  if (c->device >= 0) {
+    pm_status g = ctx_device_guard(c);
+    if (g) return g;
+    pm_status u = upload_table(c, id);
+    if (u) return u;
+  }
+  *out_id = id;
+  if (info) {
+    info->n_params = inf[0]; info->n_atoms = inf[1]; info->n_conds = inf[2]; info->n_pieces = inf[3];
+    info->n_monomials = inf[4]; info->n_columns = inf[5]; info->n_words = inf[6]; info->degree = inf[7];
+  }
+  return PM_OK;
+}
+
+extern "C" pm_status pm_table_image(pm_ctx *c, int32_t id, uint32_t *buf, size_t cap, size_t *out_words) {
+  if (!c || id < 0 || id >= (int)c->tables.size()) return pm_set_error(PM_ERR_NOT_FOUND, "no such table");
+  const auto &w = c->tables[id];
+  if (out_words) *out_words = w.size();
+  if (buf) {
+    if (cap < w.size()) return pm_set_error(PM_ERR_INVALID_ARG, "buffer too small");
+    std::memcpy(buf, w.data(), w.size() * 4);
+  }
+  return PM_OK;
+}
+
+pm_status ctx_table_offsets(pm_ctx *c, const int32_t *ids, int n, int *P, int *K, const int64_t **d_off) {
+  std::vector<int64_t> off(n);
+  *P = -1;
+  *K = -1;
+  for (int i = 0; i < n; i++) {
+    int id = ids[i];
+    if (id < 0 || id >= (int)c->tables.size()) return pm_set_error(PM_ERR_NOT_FOUND, "unknown table id");
+    const auto &w = c->tables[id];
+    int p = (int)w[pmt::H_NPARAMS], k = (int)w[pmt::H_K];
+    if (*P < 0) { *P = p; *K = k; }
+    if (P && *P != p) return pm_set_error(PM_ERR_INVALID_ARG, "tables differ in parameter count");
+    if (*K != k) return pm_set_error(PM_ERR_INVALID_ARG, "tables differ in layout");
+    off[i] = c->dev_off[id];
+  }
+  void *d = nullptr;
+  pm_status s = ctx_dcopy(c, off.data(), off.size() * 8, &d);
+  *d_off = (const int64_t *)d;
+  return s;
+}
+
+extern "C" pm_status pm_eval_counts(pm_ctx *c, const int32_t *ids, int32_t n_tables, const int64_t *d_points,
+                                    int64_t n_points, int64_t *d_counts, void *stream) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  if (n_tables < 0 || n_points < 0 || (n_tables && !ids)) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
+  if (n_tables == 0 || n_points == 0) return PM_OK;
+  if (!d_points || !d_counts) return pm_set_error(PM_ERR_INVALID_ARG, "null device buffer");
+  if (n_points > (int64_t(1) << 40)) return pm_set_error(PM_ERR_INVALID_ARG, "too many points");
+  int P, K;
+  const int64_t *d_off;
+  pm_status s = ctx_table_offsets(c, ids, n_tables, &P, &K, &d_off);
+  if (s) return s;
+  CU(pmd::launch_eval_counts(c->arena, d_off, n_tables, d_points, n_points, P, K, d_counts, c->d_status,
+                             (cudaStream_t)stream));
+  return PM_OK;
+}
+
+// ------------------------------------------------------------------------------------- prediction
+
+extern "C" pm_status pm_predict(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *W, int32_t M,
+                                int32_t precision, double *T, void *stream) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  if (R < 0 || k <= 0 || M <= 0) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
+  if (R == 0) return PM_OK;
+  if (!F || !W || !T) return pm_set_error(PM_ERR_INVALID_ARG, "null device buffer");
+  if (precision == PM_PREC_BF16X3) return pm_predict_bf16x3(c, F, R, k, W, M, T, nullptr, nullptr, stream);
+  if (precision != PM_PREC_FP64 && precision != PM_PREC_NATIVE_FP64)
+    return pm_set_error(PM_ERR_INVALID_ARG, "unknown precision");
+  if (precision == PM_PREC_FP64 && (k > 40 || M > 64)) return pm_set_error(PM_ERR_INVALID_ARG, "k <= 40 and M <= 64");
+  CU(pmd::launch_predict(F, R, k, W, M, precision, T, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+extern "C" pm_status pm_predict_argmin(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *W,
+                                       int32_t M, int32_t precision, int64_t *arg, double *mn, void *stream) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  if (R < 0 || k <= 0 || k > 40 || M <= 0 || M > 64) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
+  if (!F || !W || !arg || !mn) return pm_set_error(PM_ERR_INVALID_ARG, "null device buffer");
+  if (precision == PM_PREC_BF16X3) return pm_predict_bf16x3(c, F, R, k, W, M, nullptr, arg, mn, stream);
+  if (precision != PM_PREC_FP64) return pm_set_error(PM_ERR_INVALID_ARG, "argmin supports PM_PREC_FP64 and PM_PREC_BF16X3");
+  void *scr = nullptr;
+  pm_status s = ctx_scratch(c, pmd::argmin_scratch_bytes(M, pmd::argmin_parts()), &scr);
+  if (s) return s;
+  CU(pmd::launch_predict_argmin(F, R, k, W, M, precision, scr, arg, mn, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+// ------------------------------------------------------------------------------------- batched eval+predict+top-k
+
+extern "C" pm_status pm_eval_predict_topk(pm_ctx *c, const int32_t *tables, const int32_t *var_off,
+                                          int32_t n_templates, const int64_t *d_points, const int64_t *pt_off,
+                                          const double *d_w, int32_t topk, int32_t *d_top_idx, double *d_top_t,
+                                          void *stream) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  if (n_templates <= 0 || !tables || !var_off || !pt_off || !d_points || !d_w || !d_top_idx || !d_top_t)
+    return pm_set_error(PM_ERR_INVALID_ARG, "null argument");
+  if (topk < 1 || topk > PM_MAX_TOPK) return pm_set_error(PM_ERR_INVALID_ARG, "topk must be 1..16");
+  Plan *plan = nullptr;
+  pm_status s = ctx_plan_k2(c, tables, var_off, n_templates, pt_off, &plan);
+  if (s) return s;
+  return ctx_run_k2(c, plan, d_points, d_w, topk, d_top_idx, d_top_t, (cudaStream_t)stream);
+}

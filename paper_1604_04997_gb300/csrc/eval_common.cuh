@@ -1,0 +1,165 @@
+// Device evaluation of compiled count tables (see pm_table.h for the format).
+//
+// A table holds the piecewise quasi-polynomial properties p_i(n) of one kernel
+// (Sec. 2: "cheaply reevaluated for changed values of the parameter vector n").
+// Evaluation is exact: atoms with 32-bit magic-number division, piece selection
+// with 64-bit condition sums, monomials in 64-bit two's-complement arithmetic
+// (exact whenever the final count fits in int64, which the compiler checks on
+// the declared parameter box).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+#include "pm_table.h"
+
+namespace pmd {
+
+// Granlund & Montgomery (1994), Fig. 4.1: q = floor(x / c) for unsigned 32-bit x.
+__device__ __forceinline__ uint32_t udiv_magic(uint32_t x, uint32_t m, uint32_t sh2) {
+  uint32_t t = __umulhi(m, x);
+  return (t + ((x - t) >> 1)) >> sh2;
+}
+
+// Mathematical floor(num / c), c >= 2.
+__device__ __forceinline__ int32_t floor_div(int32_t num, uint32_t c, uint32_t m, uint32_t sh2, bool mayneg) {
+  if (!mayneg) return (int32_t)udiv_magic((uint32_t)num, m, sh2);
+  bool neg = num < 0;
+  uint32_t x = neg ? (uint32_t)(-num) + c - 1u : (uint32_t)num;
+  int32_t q = (int32_t)udiv_magic(x, m, sh2);
+  return neg ? -q : q;
+}
+
+__device__ __forceinline__ int64_t ld64(const uint32_t *p) {
+  return (int64_t)((uint64_t)p[0] | ((uint64_t)p[1] << 32));
+}
+
+// Evaluate table T at point n (int32, already known to lie in T's box) for the
+// calling thread.  vals: this thread's value slots, stride `vs` (shared memory,
+// one column per thread).  emit(col, hold, value) is called once per non-empty
+// segment; post(col, value) once per post-op.  Returns false on a malformed table.
+template <class Emit, class Post>
+__device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const int32_t *n, int32_t *vals,
+                                           int vs, Emit &&emit, Post &&post) {
+  const int P = (int)T[pmt::H_NPARAMS];
+  const int A = (int)T[pmt::H_NATOMS];
+  const int NC = (int)T[pmt::H_NCONDS];
+  if (P > 4 || P + A > pmt::MAX_VALUES || NC > pmt::MAX_CONDS) return false;
+#pragma unroll
+  for (int p = 0; p < 4; p++)
+    if (p < P) vals[p * vs] = n[p];
+  const uint32_t *at = T + T[pmt::H_OFF_ATOMS];
+  for (int a = 0; a < A; a++, at += pmt::ATOM_WORDS) {
+    int32_t num = (int32_t)at[4];
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+      if (p < P) num += (int32_t)at[p] * n[p];
+    uint32_t packed = at[7];
+    vals[(P + a) * vs] = floor_div(num, at[5], at[6], (packed >> 8) & 0xFF, (packed >> 16) & 1);
+  }
+  uint32_t bits = 0;
+  const uint32_t *cd = T + T[pmt::H_OFF_CONDS];
+  for (int c = 0; c < NC; c++) {
+    int nt = (int)cd[0];
+    int64_t s = ld64(cd + 1);
+    for (int t = 0; t < nt; t++) s += (int64_t)(int32_t)cd[4 + 2 * t] * (int64_t)vals[cd[3 + 2 * t] * vs];
+    bits |= (uint32_t)(s >= 0) << c;
+    cd += 3 + 2 * nt;
+  }
+  const uint32_t *lut = T + T[pmt::H_OFF_LUT];
+  uint32_t piece = (lut[bits >> 2] >> (8 * (bits & 3))) & 0xFF;
+  if (piece >= T[pmt::H_NPIECES]) return false;
+  const uint32_t *pc = T + T[pmt::H_OFF_PIECES] + 2 * piece;
+  const uint32_t *seg = T + T[pmt::H_OFF_SEGS] + 2 * pc[0];
+  const uint32_t nseg = pc[1];
+  const uint32_t *monos = T + T[pmt::H_OFF_MONOS];
+  int64_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
+  for (uint32_t s = 0; s < nseg; s++, seg += 2) {
+    const uint32_t w0 = seg[0];
+    const uint32_t nm = w0 >> 16;
+    const uint32_t *mo = monos + pmt::MONO_WORDS * seg[1];
+    uint64_t acc = 0;
+    for (uint32_t q = 0; q < nm; q++, mo += pmt::MONO_WORDS) {
+      uint64_t prod = (uint64_t)ld64(mo);
+      const uint32_t f = mo[2];
+#pragma unroll
+      for (int d = 0; d < 4; d++) {
+        uint32_t v = (f >> (8 * d)) & 0xFF;
+        if (v != 0xFF) prod *= (uint64_t)(int64_t)vals[v * vs];
+      }
+      acc += prod;
+    }
+    const int64_t val = (int64_t)acc;
+    const uint32_t hold = (w0 >> 8) & 0xFF;
+    if (hold == 1) h0 = val;
+    else if (hold == 2) h1 = val;
+    else if (hold == 3) h2 = val;
+    else if (hold == 4) h3 = val;
+    emit((int)(w0 & 0xFF), val);
+  }
+  const uint32_t npost = T[pmt::H_NPOST];
+  const uint32_t *po = T + T[pmt::H_OFF_POST];
+  for (uint32_t q = 0; q < npost; q++) {
+    uint32_t w = po[q];
+    uint32_t a = (w >> 8) & 0xFF, b = (w >> 16) & 0xFF;
+    int64_t va = a == 0 ? h0 : a == 1 ? h1 : a == 2 ? h2 : h3;
+    int64_t vb = b == 0 ? h0 : b == 1 ? h1 : b == 2 ? h2 : h3;
+    post((int)(w & 0xFF), va < vb ? va : vb);
+  }
+  return true;
+}
+
+// Load a point (int64 [4] or [P]) and check it against T's box; writes int32 n.
+__device__ __forceinline__ bool point_in_box(const uint32_t *T, const int64_t *pt, int P, int32_t *n) {
+  bool ok = true;
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    if (p < P) {
+      int64_t x = pt[p];
+      int64_t lo = (int32_t)T[pmt::H_BOX_LO + p], hi = (int32_t)T[pmt::H_BOX_HI + p];
+      ok = ok && x >= lo && x <= hi;
+      n[p] = (int32_t)x;
+    } else {
+      n[p] = 0;
+    }
+  }
+  return ok;
+}
+
+// ---- FP64-accurate accumulation on FP32 pipes (Ogita, Rump & Oishi 2005, Dot2).
+// An exact int64 count v is split as vh + vl (vh = rn(v), vl = rn(v - vh)); the
+// weight w as wh + wl.  Each product's leading term is made error-free with an
+// FMA (TwoProduct) and summed error-free (TwoSum); the small cross terms and all
+// error terms go to a compensation accumulator.
+struct FF { float hi, lo; };
+
+__device__ __forceinline__ FF split_weight(double w) {
+  float h = __double2float_rn(w);
+  return FF{h, __double2float_rn(w - (double)h)};
+}
+
+// The _rn intrinsics keep the compiler from contracting these steps into FMAs,
+// which would break the error-free transformations.
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float p, float pe) {
+  float t = __fadd_rn(s, p);
+  float z = __fsub_rn(t, s);
+  float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ void dot2_term(float &s, float &c, float vh, float vl, float wh, float wl) {
+  float p = __fmul_rn(vh, wh);
+  float pe = __fmaf_rn(vh, wh, -p);
+  pe = __fmaf_rn(vh, wl, pe);
+  pe = __fmaf_rn(vl, wh, pe);
+  two_sum_acc(s, c, p, pe);
+}
+
+__device__ __forceinline__ void dot2_add(float &s, float &c, int64_t v, float wh, float wl) {
+  float vh = __ll2float_rn(v);
+  float vl = __ll2float_rn(v - (int64_t)vh);
+  dot2_term(s, c, vh, vl, wh, wl);
+}
+
+}  // namespace pmd

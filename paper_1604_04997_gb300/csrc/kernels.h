@@ -1,0 +1,43 @@
+// Launch interfaces between the host API layer and the CUDA kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pmd {
+
+// bits of the device status word
+enum StatusBits { ST_OUT_OF_BOX = 1, ST_BAD_TABLE = 2, ST_TIMEOUT = 4 };
+
+// K1 (eval.cu)
+cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, int n_tables, const int64_t *points,
+                               int64_t n_points, int P, int K, int64_t *out, int *status, cudaStream_t st);
+
+// K2 (eval.cu)
+struct K2Args {
+  const uint32_t *arena;
+  const int64_t *tab_off;      // [n_variants] word offsets into arena
+  const int32_t *var_off;      // [n_templates+1] CSR into tab_off
+  const int32_t *tmpl_nparams; // [n_templates]
+  const int4 *units;           // [n_units] (template, first point, count, 0)
+  int n_units;
+  int *unit_counter;           // reset to 0 before each launch
+  const int64_t *points;       // [total][4]
+  const double *w;             // [32]
+  int topk;
+  int32_t *top_idx;            // [total][topk]
+  double *top_t;               // [total][topk]
+  int *status;
+};
+cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st);
+int k2_max_blocks_per_sm(int nw);
+
+// predict.cu
+cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, int M, int precision, double *T,
+                           cudaStream_t st);
+// argmin: per-model partial results go to scratch (n_part [M] (double, int64) pairs), then reduced.
+size_t argmin_scratch_bytes(int M, int n_part);
+int argmin_parts();
+cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
+                                  void *scratch, int64_t *arg, double *mn, cudaStream_t st);
+
+}  // namespace pmd

@@ -1,0 +1,304 @@
+// Schedules for the persistent fused launch (pm_eval_predict_topk): work units,
+// longest-processing-time order, launch-shape tuning and CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <numeric>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "pm.h"
+#include "pm_internal.h"
+#include "pm_table.h"
+
+#define CU(x)                                                                                          \
+  do {                                                                                                 \
+    cudaError_t e__ = (x);                                                                             \
+    if (e__ != cudaSuccess) return pm_set_error(PM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+static constexpr int UNIT_POINTS = 32;
+
+// Algorithmic lane operations of one evaluation of a table (average over its pieces):
+//   atom floor((a.n + b)/c):  P multiply-adds, 1 add, 5 for the magic division   P + 6
+//   condition with t terms:   2 per 64-bit multiply-add, 2 for sum and compare    2t + 2
+//   monomial of degree d:     3 per 64-bit multiply, 2 for the 64-bit add         3d + 2
+//   non-empty column:         Dot2 term (split 4, products 4, TwoSum 6, comp. 1)  15
+//   post-op min(loads, stores): compare-select 2 + Dot2 term                      17
+//   box check, piece lookup, top-k compare                                        10
+static double table_work(const std::vector<uint32_t> &w) {
+  const int P = (int)w[pmt::H_NPARAMS], A = (int)w[pmt::H_NATOMS], NC = (int)w[pmt::H_NCONDS];
+  double ops = 10.0 + (double)A * (P + 6) + 17.0 * w[pmt::H_NPOST];
+  const uint32_t *cd = w.data() + w[pmt::H_OFF_CONDS];
+  for (int c = 0; c < NC; c++) {
+    ops += 2.0 * cd[0] + 2.0;
+    cd += 3 + 2 * cd[0];
+  }
+  const int np = std::max(1u, w[pmt::H_NPIECES]);
+  double per = 0;
+  for (int p = 0; p < np; p++) {
+    const uint32_t *pc = w.data() + w[pmt::H_OFF_PIECES] + 2 * p;
+    const uint32_t *seg = w.data() + w[pmt::H_OFF_SEGS] + 2 * pc[0];
+    for (uint32_t s = 0; s < pc[1]; s++, seg += 2) {
+      per += 15.0;
+      const uint32_t *mo = w.data() + w[pmt::H_OFF_MONOS] + pmt::MONO_WORDS * seg[1];
+      for (uint32_t q = 0; q < (seg[0] >> 16); q++, mo += pmt::MONO_WORDS) per += 3.0 * mo[3] + 2.0;
+    }
+  }
+  return ops + per / np;
+}
+
+pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, int T, const int64_t *pt_off,
+                      Plan **out) {
+  if (var_off[0] != 0 || pt_off[0] != 0) return pm_set_error(PM_ERR_INVALID_ARG, "offsets must start at 0");
+  for (int t = 0; t < T; t++)
+    if (var_off[t + 1] < var_off[t] || pt_off[t + 1] < pt_off[t])
+      return pm_set_error(PM_ERR_INVALID_ARG, "offsets must be non-decreasing");
+  const int nv = var_off[T];
+  const int64_t np = pt_off[T];
+  if (np > (int64_t(1) << 31) - 64) return pm_set_error(PM_ERR_INVALID_ARG, "too many points");
+  std::string key;
+  key.append((const char *)&T, sizeof T);
+  key.append((const char *)tables, sizeof(int32_t) * nv);
+  key.append((const char *)var_off, sizeof(int32_t) * (T + 1));
+  key.append((const char *)pt_off, sizeof(int64_t) * (T + 1));
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) { *out = it->second; return PM_OK; }
+
+  std::vector<int64_t> off(nv);
+  std::vector<int32_t> nparams(T, 0);
+  std::vector<double> tw(T, 0);
+  for (int t = 0; t < T; t++) {
+    for (int v = var_off[t]; v < var_off[t + 1]; v++) {
+      int id = tables[v];
+      if (id < 0 || id >= (int)c->tables.size()) return pm_set_error(PM_ERR_NOT_FOUND, "unknown table id");
+      const auto &w = c->tables[id];
+      if ((int)w[pmt::H_K] != 32) return pm_set_error(PM_ERR_INVALID_ARG, "fused ranking needs PM_LAYOUT_32 tables");
+      if (v == var_off[t]) nparams[t] = (int)w[pmt::H_NPARAMS];
+      else if (nparams[t] != (int)w[pmt::H_NPARAMS])
+        return pm_set_error(PM_ERR_INVALID_ARG, "variants of one template differ in parameter count");
+      off[v] = c->dev_off[id];
+      tw[t] += table_work(w);
+    }
+  }
+  // work units: (template, 32 consecutive points); most expensive first (LPT)
+  struct U { int t; int p0; int n; double cost; };
+  std::vector<U> units;
+  double total_work = 0;
+  int64_t evals = 0;
+  for (int t = 0; t < T; t++) {
+    int nvt = var_off[t + 1] - var_off[t];
+    for (int64_t p = pt_off[t]; p < pt_off[t + 1]; p += UNIT_POINTS) {
+      int n = (int)std::min<int64_t>(UNIT_POINTS, pt_off[t + 1] - p);
+      if (nvt == 0) { units.push_back({t, (int)p, n, 0}); continue; }
+      units.push_back({t, (int)p, n, tw[t] * UNIT_POINTS});
+      total_work += tw[t] * n;
+      evals += (int64_t)nvt * n;
+    }
+  }
+  std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
+  std::vector<int4> hu(units.size());
+  for (size_t i = 0; i < units.size(); i++) hu[i] = make_int4(units[i].t, units[i].p0, units[i].n, 0);
+
+  Plan *p = new Plan();
+  auto alloc = [&](const void *h, size_t bytes, void **d) -> pm_status {
+    CU(cudaMalloc(d, std::max<size_t>(bytes, 16)));
+    p->dev.push_back(*d);
+    if (h) CU(cudaMemcpy(*d, h, bytes, cudaMemcpyHostToDevice));
+    return PM_OK;
+  };
+  void *d;
+  pm_status s;
+  if ((s = alloc(off.data(), off.size() * 8, &d))) return s;
+  p->d_tab_off = (const int64_t *)d;
+  if ((s = alloc(var_off, sizeof(int32_t) * (T + 1), &d))) return s;
+  p->d_var_off = (const int32_t *)d;
+  if ((s = alloc(nparams.data(), sizeof(int32_t) * T, &d))) return s;
+  p->d_nparams = (const int32_t *)d;
+  if ((s = alloc(hu.data(), sizeof(int4) * hu.size(), &d))) return s;
+  p->d_units = (const int4 *)d;
+  if ((s = alloc(nullptr, sizeof(int), &d))) return s;
+  p->d_counter = (int *)d;
+  p->n_units = (int)hu.size();
+  p->n_templates = T;
+  p->total_points = np;
+  p->total_evals = evals;
+  p->work_per_eval = evals ? total_work / (double)evals : 0;
+  p->nw = 8;
+  int bps = pmd::k2_max_blocks_per_sm(p->nw);
+  p->grid = std::max(1, c->n_sms * std::max(1, bps));
+  c->plans[key] = p;
+  *out = p;
+  return PM_OK;
+}
+
+static pm_status launch_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w, int topk, int32_t *idx,
+                           double *t, cudaStream_t st, int nw, int grid) {
+  CU(cudaMemsetAsync(p->d_counter, 0, sizeof(int), st));
+  pmd::K2Args a;
+  a.arena = c->arena;
+  a.tab_off = p->d_tab_off;
+  a.var_off = p->d_var_off;
+  a.tmpl_nparams = p->d_nparams;
+  a.units = p->d_units;
+  a.n_units = p->n_units;
+  a.unit_counter = p->d_counter;
+  a.points = pts;
+  a.w = w;
+  a.topk = topk;
+  a.top_idx = idx;
+  a.top_t = t;
+  a.status = c->d_status;
+  CU(pmd::launch_eval_predict_topk(a, nw, grid, st));
+  return PM_OK;
+}
+
+// Launch-shape tuning: time each candidate (warps per CTA x CTAs per SM) on the
+// caller's own inputs and keep the fastest.  Results are cached per plan and,
+// when PM_TUNE_CACHE names a file, persisted by workload signature.
+static std::string plan_signature(const Plan *p) {
+  std::ostringstream o;
+  o << "T" << p->n_templates << "_P" << p->total_points << "_E" << p->total_evals << "_W"
+    << (int)(p->work_per_eval + 0.5);
+  return o.str();
+}
+
+static bool tune_lookup(const std::string &path, const std::string &sig, int *nw, int *bps) {
+  if (path.empty()) return false;
+  std::ifstream f(path);
+  std::string line;
+  while (std::getline(f, line)) {
+    char s[256];
+    int a, b;
+    if (sscanf(line.c_str(), " \"%255[^\"]\": [%d, %d]", s, &a, &b) == 3 && sig == s) {
+      *nw = a;
+      *bps = b;
+      return true;
+    }
+  }
+  return false;
+}
+
+static void tune_store(const std::string &path, const std::string &sig, int nw, int bps) {
+  if (path.empty()) return;
+  std::vector<std::string> lines;
+  {
+    std::ifstream f(path);
+    std::string line;
+    while (std::getline(f, line))
+      if (line.find("\": [") != std::string::npos && line.find("\"" + sig + "\"") == std::string::npos) {
+        while (!line.empty() && (line.back() == ',' || line.back() == ' ')) line.pop_back();
+        lines.push_back(line);
+      }
+  }
+  std::ostringstream o;
+  o << "  \"" << sig << "\": [" << nw << ", " << bps << "]";
+  lines.push_back(o.str());
+  std::ofstream f(path);
+  f << "{\n";
+  for (size_t i = 0; i < lines.size(); i++) f << lines[i] << (i + 1 < lines.size() ? ",\n" : "\n");
+  f << "}\n";
+}
+
+static pm_status tune_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w, int topk, int32_t *idx, double *t,
+                         cudaStream_t st) {
+  std::string sig = plan_signature(p);
+  int nw, bps;
+  if (tune_lookup(c->tune_path, sig, &nw, &bps)) {
+    p->nw = nw;
+    p->grid = c->n_sms * bps;
+    p->tuned = true;
+    return PM_OK;
+  }
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bnw = p->nw, bgrid = p->grid, bbps = 1;
+  for (int cand_nw : {4, 8}) {
+    int mx = std::max(1, pmd::k2_max_blocks_per_sm(cand_nw));
+    for (int cand_bps = 1; cand_bps <= mx; cand_bps++) {
+      int grid = c->n_sms * cand_bps;
+      pm_status s = launch_k2(c, p, pts, w, topk, idx, t, st, cand_nw, grid);  // warm-up
+      if (s) return s;
+      CU(cudaEventRecord(e0, st));
+      for (int r = 0; r < 2; r++) {
+        s = launch_k2(c, p, pts, w, topk, idx, t, st, cand_nw, grid);
+        if (s) return s;
+      }
+      CU(cudaEventRecord(e1, st));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) { best = ms; bnw = cand_nw; bgrid = grid; bbps = cand_bps; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->nw = bnw;
+  p->grid = bgrid;
+  p->tuned = true;
+  tune_store(c->tune_path, sig, bnw, bbps);
+  return PM_OK;
+}
+
+pm_status ctx_run_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w, int topk, int32_t *idx, double *t,
+                     cudaStream_t st) {
+  if (c->tune && !p->tuned) {
+    pm_status s = tune_k2(c, p, pts, w, topk, idx, t, st);
+    if (s) return s;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st) CU(cudaStreamIsCapturing(st, &cs));
+  if (!st || cs != cudaStreamCaptureStatusNone) return launch_k2(c, p, pts, w, topk, idx, t, st, p->nw, p->grid);
+  const void *key[6] = {pts, w, idx, t, c->arena, st};
+  bool same = p->graph_exec && p->g_topk == topk && p->g_nw == p->nw && p->g_grid == p->grid &&
+              std::memcmp(key, p->g_key, sizeof key) == 0;
+  if (!same) {
+    if (p->graph_exec) { cudaGraphExecDestroy(p->graph_exec); p->graph_exec = nullptr; }
+    cudaGraph_t g;
+    CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    pm_status s = launch_k2(c, p, pts, w, topk, idx, t, st, p->nw, p->grid);
+    cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (s) return s;
+    CU(ee);
+    cudaError_t ie = cudaGraphInstantiate(&p->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    CU(ie);
+    std::memcpy(p->g_key, key, sizeof key);
+    p->g_topk = topk;
+    p->g_nw = p->nw;
+    p->g_grid = p->grid;
+  }
+  CU(cudaGraphLaunch(p->graph_exec, st));
+  return PM_OK;
+}
+
+extern "C" pm_status pm_tune(pm_ctx *c, int32_t enable, const char *cache_path) {
+  if (!c) return pm_set_error(PM_ERR_INVALID_ARG, "null context");
+  c->tune = enable;
+  c->tune_path = cache_path ? cache_path : "";
+  return PM_OK;
+}
+
+extern "C" pm_status pm_plan_info(pm_ctx *c, const int32_t *tables, const int32_t *var_off, int32_t n_templates,
+                                  const int64_t *pt_off, int64_t *out /*[6]*/) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  Plan *p;
+  pm_status s = ctx_plan_k2(c, tables, var_off, n_templates, pt_off, &p);
+  if (s) return s;
+  out[0] = p->n_units;
+  out[1] = p->total_evals;
+  out[2] = (int64_t)(p->work_per_eval * 1000);
+  out[3] = p->nw;
+  out[4] = p->grid;
+  out[5] = p->tuned;
+  return PM_OK;
+}

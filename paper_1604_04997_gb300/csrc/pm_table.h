@@ -1,0 +1,46 @@
+// Compiled count table: the device-resident form of one kernel's piecewise
+// quasi-polynomial properties (Sec. 3.2: a key -> piecewise quasi-polynomial
+// mapping, here with keys already folded into feature columns).
+//
+// All fields are 32-bit words.  A table is evaluated at a parameter point n by
+//   1. values v[0..P)   = n (the parameters),
+//      values v[P..P+A) = atoms floor((a . n + b) / c), c >= 2;
+//   2. bits: condition j holds iff const_j + sum_t coef_jt * v[idx_jt] >= 0;
+//   3. piece = lut[bits];
+//   4. for each segment (column, monomials) of the piece:
+//        column value = sum over monomials of coef * prod v[f]  (exact int64);
+//   5. post-ops: column = min(held value A, held value B)   (min(loads, stores)).
+// Columns that no segment names are zero.  Hidden columns (index >= k) only feed
+// post-ops.
+#pragma once
+#include <stdint.h>
+
+namespace pmt {
+
+constexpr uint32_t MAGIC = 0x31544d50u;  // "PMT1"
+constexpr int MAX_VALUES = 32;
+constexpr int MAX_CONDS = 10;
+constexpr int MAX_DEGREE = 4;
+constexpr int MAX_HOLD = 4;
+constexpr int MAX_COLS = 40;           // visible + hidden
+constexpr int MAX_TABLE_WORDS = 4096;  // 16 KB
+
+enum Header {
+  H_MAGIC = 0, H_WORDS, H_NPARAMS, H_NATOMS, H_NCONDS, H_NPIECES, H_K, H_NHIDDEN, H_NPOST,
+  H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_SEGS, H_OFF_MONOS, H_OFF_POST,
+  H_BOX_LO = 16, H_BOX_HI = 20, H_NMONOS = 24, H_DEGREE = 25, H_NSEGS = 26, H_RESERVED = 27,
+  HEADER_WORDS = 28
+};
+
+// Atom: 8 words  a0 a1 a2 a3 b c magic packed
+//   packed: bits 0..7 shift1, 8..15 shift2, bit 16: numerator may be negative
+constexpr int ATOM_WORDS = 8;
+// Condition: [n_terms, const_lo, const_hi, (idx, coef) * n_terms]
+// LUT: 2^n_conds bytes (piece ids), packed 4 per word.
+// Piece: 2 words [seg_begin, n_segs]
+// Segment: 2 words [col | (hold+1) << 8 | n_mono << 16, mono_begin]
+// Monomial: 4 words [coef_lo, coef_hi, factors (4 x 8 bit, 0xFF = none), degree]
+constexpr int MONO_WORDS = 4;
+// Post-op: 1 word [out_col | holdA << 8 | holdB << 16]
+
+}  // namespace pmt

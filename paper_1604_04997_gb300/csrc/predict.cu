@@ -1,0 +1,221 @@
+// Prediction T = F W^T: the "small inner product" of Sec. 2,
+// T_wall(n) ~= sum_i alpha_i p_i(n), for many feature rows and device models.
+//
+// FP64-accurate path: FP32 compensated arithmetic (Dot2 of Ogita, Rump & Oishi,
+// SISC 2005) with every int64 count split into two floats and every weight into a
+// float pair, per-model power-of-two scaling into the FP32 range.  Error
+// <= ~k 2^-44 of sum_i |F_ri W_mi|.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "eval_common.cuh"
+#include "kernels.h"
+#include "pm.h"
+
+namespace pmd {
+
+constexpr int PR_ROWS = 32;     // rows per tile
+constexpr int PR_WARPS = 8;     // each warp: 4 rows of the tile
+constexpr int PR_MAXK = 40;
+constexpr int PR_MAXM = 64;
+
+struct PredictSmem {
+  float fh[PR_ROWS][PR_MAXK + 1], fl[PR_ROWS][PR_MAXK + 1];
+  float wh[PR_MAXK][PR_MAXM], wl[PR_MAXK][PR_MAXM];
+  double unscale[PR_MAXM];
+};
+
+__device__ void load_weights(PredictSmem &S, const double *W, int M, int k) {
+  // one thread per model: power-of-two scale so max |w| lies in [0.5, 1)
+  for (int m = threadIdx.x; m < PR_MAXM; m += blockDim.x) {
+    double mx = 0;
+    if (m < M) for (int i = 0; i < k; i++) mx = fmax(mx, fabs(W[(int64_t)m * k + i]));
+    int e = 0;
+    if (mx > 0) frexp(mx, &e);
+    double sc = ldexp(1.0, -e);
+    for (int i = 0; i < PR_MAXK; i++) {
+      FF f = split_weight((m < M && i < k) ? W[(int64_t)m * k + i] * sc : 0.0);
+      S.wh[i][m] = f.hi;
+      S.wl[i][m] = f.lo;
+    }
+    S.unscale[m] = ldexp(1.0, e);
+  }
+}
+
+__device__ void load_rows(PredictSmem &S, const int64_t *F, int64_t r0, int64_t R, int k) {
+  for (int i = threadIdx.x; i < PR_ROWS * k; i += blockDim.x) {
+    int r = i / k, c = i - r * k;
+    int64_t v = (r0 + r < R) ? F[(r0 + r) * k + c] : 0;
+    float vh = __ll2float_rn(v);
+    S.fh[r][c] = vh;
+    S.fl[r][c] = __ll2float_rn(v - (int64_t)vh);
+  }
+}
+
+// Each thread: rows warp + 8 q (q < 4), models lane + 32 j (j < 2).
+__device__ __forceinline__ void tile_dot2(const PredictSmem &S, int k, float s[4][2], float c[4][2]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int j = 0; j < 2; j++) s[q][j] = c[q][j] = 0.f;
+  for (int i = 0; i < k; i++) {
+    float wh0 = S.wh[i][lane], wl0 = S.wl[i][lane], wh1 = S.wh[i][lane + 32], wl1 = S.wl[i][lane + 32];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const float vh = S.fh[warp + 8 * q][i], vl = S.fl[warp + 8 * q][i];
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const float wh = j ? wh1 : wh0, wl = j ? wl1 : wl0;
+        dot2_term(s[q][j], c[q][j], vh, vl, wh, wl);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PR_WARPS * 32) k_predict_ff(const int64_t *__restrict__ F, int64_t R, int k,
+                                                              const double *__restrict__ W, int M,
+                                                              double *__restrict__ T) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  PredictSmem &S = *(PredictSmem *)smem_raw;
+  load_weights(S, W, M, k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ntiles = (R + PR_ROWS - 1) / PR_ROWS;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * PR_ROWS;
+    __syncthreads();
+    load_rows(S, F, r0, R, k);
+    __syncthreads();
+    float s[4][2], c[4][2];
+    tile_dot2(S, k, s, c);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int64_t r = r0 + warp + 8 * q;
+      if (r >= R) continue;
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const int m = lane + 32 * j;
+        if (m < M) T[r * M + m] = ((double)s[q][j] + (double)c[q][j]) * S.unscale[m];
+      }
+    }
+  }
+}
+
+// Plain double FMA (cross-check path).
+__global__ void k_predict_f64(const int64_t *__restrict__ F, int64_t R, int k, const double *__restrict__ W, int M,
+                              double *__restrict__ T) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= R * M) return;
+  const int64_t r = i / M;
+  const int m = (int)(i - r * M);
+  double acc = 0;
+  for (int c = 0; c < k; c++) acc = fma((double)F[r * k + c], W[(int64_t)m * k + c], acc);
+  T[i] = acc;
+}
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, int M, int precision, double *T,
+                           cudaStream_t st) {
+  if (R == 0) return cudaSuccess;
+  if (precision == PM_PREC_NATIVE_FP64) {
+    int64_t n = R * M;
+    k_predict_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(F, R, k, W, M, T);
+    return cudaGetLastError();
+  }
+  if (k > PR_MAXK || M > PR_MAXM) return cudaErrorInvalidValue;
+  size_t sm = sizeof(PredictSmem);
+  cudaFuncSetAttribute(k_predict_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  int64_t ntiles = (R + PR_ROWS - 1) / PR_ROWS;
+  int grid = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 8);
+  k_predict_ff<<<grid, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, T);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- argmin over rows per model
+
+struct ArgPart { double t; int64_t r; };
+
+__device__ __forceinline__ bool arg_less(double a, int64_t ra, double b, int64_t rb) {
+  return a < b || (a == b && ra < rb);
+}
+
+__global__ void __launch_bounds__(PR_WARPS * 32) k_predict_argmin_part(const int64_t *__restrict__ F, int64_t R,
+                                                                       int k, const double *__restrict__ W, int M,
+                                                                       ArgPart *__restrict__ part) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  PredictSmem &S = *(PredictSmem *)smem_raw;
+  __shared__ ArgPart red[PR_WARPS][PR_MAXM];
+  load_weights(S, W, M, k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double bt[2] = {__longlong_as_double(0x7ff0000000000000ll), __longlong_as_double(0x7ff0000000000000ll)};
+  int64_t br[2] = {INT64_MAX, INT64_MAX};
+  const int64_t ntiles = (R + PR_ROWS - 1) / PR_ROWS;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * PR_ROWS;
+    __syncthreads();
+    load_rows(S, F, r0, R, k);
+    __syncthreads();
+    float s[4][2], c[4][2];
+    tile_dot2(S, k, s, c);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int64_t r = r0 + warp + 8 * q;
+      if (r >= R) continue;
+#pragma unroll
+      for (int j = 0; j < 2; j++) {
+        const int m = lane + 32 * j;
+        const double tv = ((double)s[q][j] + (double)c[q][j]) * S.unscale[m < PR_MAXM ? m : 0];
+        if (arg_less(tv, r, bt[j], br[j])) { bt[j] = tv; br[j] = r; }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 2; j++) red[warp][lane + 32 * j] = ArgPart{bt[j], br[j]};
+  __syncthreads();
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    ArgPart b = red[0][m];
+    for (int w = 1; w < PR_WARPS; w++)
+      if (arg_less(red[w][m].t, red[w][m].r, b.t, b.r)) b = red[w][m];
+    part[(int64_t)blockIdx.x * M + m] = b;
+  }
+}
+
+__global__ void k_argmin_reduce(const ArgPart *__restrict__ part, int n_part, int M, int64_t *arg, double *mn) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  ArgPart b = part[m];
+  for (int p = 1; p < n_part; p++) {
+    ArgPart x = part[(int64_t)p * M + m];
+    if (arg_less(x.t, x.r, b.t, b.r)) b = x;
+  }
+  arg[m] = b.r == INT64_MAX ? -1 : b.r;
+  mn[m] = b.t;
+}
+
+int argmin_parts() { return num_sms() * 4; }
+size_t argmin_scratch_bytes(int M, int n_part) { return (size_t)M * n_part * sizeof(ArgPart); }
+
+cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
+                                  void *scratch, int64_t *arg, double *mn, cudaStream_t st) {
+  if (k > PR_MAXK || M > PR_MAXM || precision != PM_PREC_FP64) return cudaErrorInvalidValue;
+  size_t sm = sizeof(PredictSmem);
+  cudaFuncSetAttribute(k_predict_argmin_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int np = argmin_parts();
+  k_predict_argmin_part<<<np, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, (ArgPart *)scratch);
+  k_argmin_reduce<<<(M + 63) / 64, 64, 0, st>>>((const ArgPart *)scratch, np, M, arg, mn);
+  return cudaGetLastError();
+}
+
+}  // namespace pmd

@@ -1,0 +1,61 @@
+"""Batched tuning problems: compile a set of kernel variants and lay out the
+per-template variant and point lists that pm_eval_predict_topk consumes."""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Sequence
+
+import numpy as np
+
+from . import binding as B
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class Batched:
+    templates: List[str]
+    variants: List[W.Variant]          # in template-major order
+    tables: np.ndarray                 # int32 [n_variants] table ids (duplicates share a table)
+    var_off: np.ndarray                # int32 [T+1]
+    points: np.ndarray                 # int64 [total][4]
+    pt_off: np.ndarray                 # int64 [T+1]
+    n_distinct: int
+
+    @property
+    def total_evals(self) -> int:
+        return int(sum((self.var_off[t + 1] - self.var_off[t]) * (self.pt_off[t + 1] - self.pt_off[t])
+                       for t in range(len(self.templates))))
+
+
+def compile_variants(ctx: B.Context, variants: Sequence[W.Variant], lo: int, hi: int, layout: int = 32,
+                     cache: Dict = None) -> List[int]:
+    cache = {} if cache is None else cache
+    ids = []
+    for v in variants:
+        if v.key not in cache:
+            P = len(W.TEMPLATE_PARAMS[v.template])
+            cache[v.key] = ctx.compile_counts(W.variant_ir(v), layout, [lo] * P, [hi] * P)[0]
+        ids.append(cache[v.key])
+    return ids
+
+
+def build(ctx: B.Context, n_variants: int = 10000, n_points: int = 4096, variant_seed: int = 2,
+          point_seed: int = 3, lo: int = W.BOX_LO, hi: int = W.BOX_HI) -> Batched:
+    """The batched tuning workload: variants drawn with replacement from the tuning
+    space over the eight templates; per template n_points log-uniform points."""
+    drawn = W.draw_variants(n_variants, variant_seed)
+    groups = W.group_by_template(drawn)
+    pts = W.template_points(point_seed, n_points, lo, hi)
+    cache: Dict = {}
+    variants, tables, var_off, pt_rows, pt_off = [], [], [0], [], [0]
+    for t in W.TEMPLATES:
+        vs = [drawn[i] for i in groups[t]]
+        variants += vs
+        tables += compile_variants(ctx, vs, lo, hi, 32, cache)
+        var_off.append(len(tables))
+        p = np.zeros((n_points, 4), dtype=np.int64)
+        p[:, :pts[t].shape[1]] = pts[t]
+        pt_rows.append(p)
+        pt_off.append(pt_off[-1] + n_points)
+    return Batched(list(W.TEMPLATES), variants, np.array(tables, dtype=np.int32), np.array(var_off, dtype=np.int32),
+                   np.concatenate(pt_rows), np.array(pt_off, dtype=np.int64), len(cache))

@@ -1,0 +1,102 @@
+"""Test-only reader of compiled count tables (the layout of csrc/pm_table.h).
+
+It lets the CPU tests check the compiler's output against the oracle without a
+GPU.  It is never imported by the library, so it cannot act as a CPU fallback.
+"""
+import numpy as np
+
+H_MAGIC, H_WORDS, H_NPARAMS, H_NATOMS, H_NCONDS, H_NPIECES, H_K, H_NHIDDEN, H_NPOST = range(9)
+H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_SEGS, H_OFF_MONOS, H_OFF_POST = range(9, 16)
+H_BOX_LO, H_BOX_HI = 16, 20
+
+
+def _s32(x):
+    x = int(x) & 0xFFFFFFFF
+    return x - (1 << 32) if x >= (1 << 31) else x
+
+
+def _s64(lo, hi):
+    x = (int(lo) & 0xFFFFFFFF) | ((int(hi) & 0xFFFFFFFF) << 32)
+    return x - (1 << 64) if x >= (1 << 63) else x
+
+
+def magic_div(x, m, sh2):
+    """The kernels' unsigned division by an invariant (32-bit arithmetic)."""
+    t = (m * x) >> 32
+    return ((t + ((x - t) >> 1)) & 0xFFFFFFFF) >> sh2
+
+
+class Table:
+    def __init__(self, words):
+        self.w = [int(x) for x in np.asarray(words, dtype=np.uint32)]
+        w = self.w
+        assert w[H_MAGIC] == 0x31544D50
+        self.P, self.A, self.C = w[H_NPARAMS], w[H_NATOMS], w[H_NCONDS]
+        self.k, self.hidden = w[H_K], w[H_NHIDDEN]
+        self.box_lo = [_s32(w[H_BOX_LO + i]) for i in range(self.P)]
+        self.box_hi = [_s32(w[H_BOX_HI + i]) for i in range(self.P)]
+
+    def atoms(self):
+        w, o = self.w, self.w[H_OFF_ATOMS]
+        out = []
+        for a in range(self.A):
+            q = w[o + 8 * a: o + 8 * a + 8]
+            out.append(dict(a=[_s32(x) for x in q[:4]], b=_s32(q[4]), c=_s32(q[5]), m=q[6],
+                            sh2=(q[7] >> 8) & 0xFF, neg=(q[7] >> 16) & 1))
+        return out
+
+    def evaluate(self, n, check_magic=True):
+        """Exact feature columns at point n (Python integers)."""
+        w = self.w
+        P = self.P
+        for i in range(P):
+            assert self.box_lo[i] <= n[i] <= self.box_hi[i]
+        vals = list(n[:P])
+        for at in self.atoms():
+            num = at["b"] + sum(at["a"][i] * n[i] for i in range(P))
+            f = num // at["c"]
+            if check_magic:
+                if num >= 0:
+                    g = magic_div(num, at["m"], at["sh2"])
+                else:
+                    assert at["neg"]
+                    g = -magic_div(-num + at["c"] - 1, at["m"], at["sh2"])
+                assert g == f, (num, at)
+            vals.append(f)
+        bits, o = 0, w[H_OFF_CONDS]
+        for c in range(self.C):
+            nt = w[o]
+            s = _s64(w[o + 1], w[o + 2])
+            for t in range(nt):
+                s += _s32(w[o + 4 + 2 * t]) * vals[w[o + 3 + 2 * t]]
+            bits |= int(s >= 0) << c
+            o += 3 + 2 * nt
+        lut = w[H_OFF_LUT]
+        piece = (w[lut + (bits >> 2)] >> (8 * (bits & 3))) & 0xFF
+        assert piece < w[H_NPIECES]
+        pb = w[H_OFF_PIECES] + 2 * piece
+        seg0, nseg = w[pb], w[pb + 1]
+        cols = [0] * (self.k + self.hidden)
+        hold = [0, 0, 0, 0]
+        for s in range(nseg):
+            so = w[H_OFF_SEGS] + 2 * (seg0 + s)
+            col, h, nm = w[so] & 0xFF, (w[so] >> 8) & 0xFF, w[so] >> 16
+            mo = w[H_OFF_MONOS] + 4 * w[so + 1]
+            acc = 0
+            for q in range(nm):
+                coef = _s64(w[mo], w[mo + 1])
+                f = w[mo + 2]
+                for d in range(4):
+                    v = (f >> (8 * d)) & 0xFF
+                    if v != 0xFF:
+                        coef *= vals[v]
+                acc += coef
+                mo += 4
+            cols[col] = acc
+            if h:
+                hold[h - 1] = acc
+        po = w[H_OFF_POST]
+        for q in range(w[H_NPOST]):
+            x = w[po + q]
+            cols[x & 0xFF] = min(hold[(x >> 8) & 0xFF], hold[(x >> 16) & 0xFF])
+        return cols[:self.k]

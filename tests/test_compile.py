@@ -1,0 +1,123 @@
+"""The count compiler (host side of pm_compile_counts) against the oracle, on CPU.
+
+Compiled tables are read back through the C ABI and evaluated by a test-only
+interpreter; the oracle computes the same counts by brute force / per-axis.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_04997_gb300 import binding as B
+from paper_1604_04997_gb300 import workloads as W
+from table_interp import Table, magic_div
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    c = B.Context(-1)
+    yield c
+    c.close()
+
+
+def test_library_exports_every_declared_symbol(ctx):
+    decl = set(re.findall(r"\b(pm_[a-z_0-9]+)\s*\(", open(os.path.join(ROOT, "include", "pm.h")).read()))
+    L = B.lib()
+    missing = [s for s in decl if not hasattr(L, s)]
+    assert not missing and set(B.exported_symbols()) <= decl
+
+
+@pytest.mark.parametrize("t", W.TEMPLATES)
+def test_small_n_all_pieces(ctx, t):
+    """Every n in [1, 96] on the box [1, 65536]: remainder tiles and small-n pieces."""
+    for v in [W.canonical(t, 2 if t == "copy" else 1)] + [
+            x for i, x in enumerate(v for v in W.all_variants() if v.template == t) if i % 37 == 3][:4]:
+        ir = W.variant_ir(v)
+        P = len(W.TEMPLATE_PARAMS[t])
+        tid, info = ctx.compile_counts(ir, 32, [1] * P, [65536] * P)
+        T = Table(ctx.table_image(tid))
+        k = oracle.Kernel(ir)
+        if P == 1:
+            pts = np.arange(1, 97).reshape(-1, 1)
+        else:
+            vals = [1, 2, 15, 16, 17, 33, 64, 96]
+            pts = np.array([(a, b, c) for a in vals for b in vals for c in vals])
+        ref = k.features(pts, 32, "struct")
+        for p, f in zip(pts, ref):
+            assert T.evaluate([int(x) for x in p]) == list(f), (v.name, p)
+
+
+def test_layout12_with_hidden_column(ctx):
+    for v in W.tiny_variants():
+        ir = W.variant_ir(v)
+        P = len(W.TEMPLATE_PARAMS[v.template])
+        tid, _ = ctx.compile_counts(ir, 12, [1] * P, [8192] * P)
+        T = Table(ctx.table_image(tid))
+        k = oracle.Kernel(ir)
+        pts = W.tiny_points(v.template, 32, (64, 128, 256, 8192))
+        ref = k.features(pts, 12, "struct")
+        for p, f in zip(pts, ref):
+            assert T.evaluate([int(x) for x in p]) == list(f)
+
+
+def test_tuning_space_sample(ctx):
+    """Random variants of the tuning space at log-uniform points of [64, 65536]."""
+    allv = W.all_variants()
+    rng = np.random.default_rng(5)
+    for j in rng.choice(len(allv), 120, replace=False):
+        v = allv[j]
+        P = len(W.TEMPLATE_PARAMS[v.template])
+        ir = W.variant_ir(v)
+        tid, info = ctx.compile_counts(ir, 32, [64] * P, [65536] * P)
+        assert info["n_words"] <= 1024
+        T = Table(ctx.table_image(tid))
+        pts = W.draw_points(P, 16, int(j))
+        ref = oracle.Kernel(ir).features(pts, 32, "struct")
+        for p, f in zip(pts, ref):
+            assert T.evaluate([int(x) for x in p]) == list(f), v.name
+
+
+def test_magic_division():
+    """Granlund-Montgomery constants reproduce floor division for 32-bit numerators."""
+    from table_interp import _s32
+    rng = np.random.default_rng(1)
+    ctx = B.Context(-1)
+    for c in list(range(2, 70)) + [97, 255, 256, 1000, 4095, 4096, 65535, 65536, 1 << 20]:
+        ir = f"kernel d\nparam n\ndim g g0 0 floor((n+7)/{c})\nstmt s g\nflop f32 add 1\nend\n"
+        tid, _ = ctx.compile_counts(ir, 32, [0], [(1 << 30) - 8])
+        T = Table(ctx.table_image(tid))
+        (at,) = T.atoms()
+        assert at["c"] == c or c % at["c"] == 0
+        xs = np.concatenate([rng.integers(0, 1 << 31, 2000), np.arange(0, 3 * c), [(1 << 31) - 1]])
+        for x in xs:
+            assert magic_div(int(x), at["m"], at["sh2"]) == int(x) // at["c"]
+
+
+@pytest.mark.parametrize("ir,code", [
+    # coupled guard: i + j < n is not a per-axis form
+    ("kernel c\nparam n\ndim i g0 0 n\ndim j seq 0 n\nstmt s i,j\nguard i+j < n\nflop f32 add 1\nend\n", -3),
+    ("kernel c\nparam n\ndim i g0 0 n\nstmt s i\nload a[i]\nend\n", -2),
+    # n^3 * n with n up to 2^20 leaves int64
+    ("kernel c\nparam n\ndim a g0 0 n\ndim b seq 0 n\ndim c seq 0 n\ndim d seq 0 n\n"
+     "stmt s a,b,c,d\nflop f32 add 1000\nend\n", -4),
+])
+def test_compile_errors(ir, code):
+    ctx = B.Context(-1)
+    with pytest.raises(B.PMError) as e:
+        ctx.compile_counts(ir, 32, [1], [1 << 20])
+    assert e.value.code == code
+
+
+def test_loopy_example_table(ctx):
+    ir = open(os.path.join(os.path.dirname(__file__), "golden", "loopy_double.ir")).read()
+    tid, info = ctx.compile_counts(ir, 32, [1], [1 << 20])
+    T = Table(ctx.table_image(tid))
+    for n in (1, 7, 64, 65, 1000, 1 << 20):
+        F = T.evaluate([n])
+        assert (F[4], F[17], F[24], F[1]) == (n, n, n, -(-n // 64))
