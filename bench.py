@@ -192,7 +192,7 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     ctx = B.Context(local)
-    ctx.tune(True, None)
+    ctx.tune(not args.no_tune, None)
     bp = tuning.build(ctx, args.variants, args.points)
     w = W.draw_weights(32, 1, 4)[0]
     n = bp.points.shape[0]
@@ -324,6 +324,7 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=8.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (8 warps, 2 CTAs/SM)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
