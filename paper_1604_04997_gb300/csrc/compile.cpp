@@ -21,6 +21,7 @@
 #include <array>
 #include <cstdint>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <set>
 #include <string>
@@ -1313,51 +1314,72 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
     for (size_t b = 0; b < 4 && i + b < lut.size(); b++) w |= (uint32_t)lut[i + b] << (8 * b);
     W.push_back(w);
   }
-  // pieces, segments, monomials
-  std::vector<uint32_t> segs, monos;
-  std::vector<uint32_t> pw;
-  int degree = 0, nmono = 0;
+  // pieces: the distinct monomials of each piece become products (each one value times
+  // an earlier product, prefixes added as needed); columns become coefficient entries
+  std::vector<uint32_t> pw, prods, entries;
+  int degree = 0, nentry = 0, maxprod = 0;
   for (auto &pc : pieces) {
-    pw.push_back((uint32_t)(segs.size() / 2));
-    uint32_t nseg = 0;
+    std::map<Mono, int> pid;  // monomial (new value ids, sorted) -> product index
+    std::vector<uint32_t> plist;
+    std::function<int(const Mono &)> need = [&](const Mono &m) -> int {
+      int d = mono_deg(m);
+      if (d == 0) return 0xFF;
+      auto it = pid.find(m);
+      if (it != pid.end()) return it->second;
+      Mono pre = m;
+      pre[d - 1] = 0xFF;
+      int src = need(pre);
+      int id = (int)plist.size();
+      plist.push_back((uint32_t)src | ((uint32_t)m[d - 1] << 8));
+      pid[m] = id;
+      return id;
+    };
+    std::vector<std::array<uint32_t, 4>> ent;
     for (int col = 0; col < ncols; col++) {
       const Poly &p = pc[col];
       if (p.empty()) continue;
       int h = hold.count(col) ? hold[col] + 1 : 0;
-      if (p.size() > 0xFFFF) fail(E_UNSUP, "segment too long");
-      segs.push_back((uint32_t)col | ((uint32_t)h << 8) | ((uint32_t)p.size() << 16));
-      segs.push_back((uint32_t)(monos.size() / pmt::MONO_WORDS));
+      size_t first = ent.size();
       for (auto &kv : p) {
-        put64(monos, kv.second);
-        uint32_t f = 0;
-        int d = 0;
-        for (int q = 0; q < 4; q++) {
-          uint32_t v = kv.first[q] == 0xFF ? 0xFF : (uint32_t)vmap(kv.first[q]);
-          if (v != 0xFF) d++;
-          f |= v << (8 * q);
-        }
-        monos.push_back(f);
-        monos.push_back((uint32_t)d);
-        degree = std::max(degree, d);
-        nmono++;
+        Mono m = {0xFF, 0xFF, 0xFF, 0xFF};
+        std::vector<uint8_t> f;
+        for (auto x : kv.first) if (x != 0xFF) f.push_back((uint8_t)vmap(x));
+        std::sort(f.begin(), f.end());
+        for (size_t q = 0; q < f.size(); q++) m[q] = f[q];
+        degree = std::max(degree, (int)f.size());
+        int pr = need(m);
+        int64_t cf = (int64_t)kv.second;
+        ent.push_back({(uint32_t)((uint64_t)cf & 0xffffffffu), (uint32_t)((uint64_t)cf >> 32),
+                       (uint32_t)col | ((uint32_t)pr << 8) | ((uint32_t)h << 16), 0u});
       }
-      nseg++;
+      ent.back()[2] |= pmt::ENTRY_LAST;
+      (void)first;
     }
-    pw.push_back(nseg);
+    if ((int)plist.size() > pmt::MAX_PRODS) fail(E_UNSUP, "more than 16 monomial products in a piece");
+    maxprod = std::max(maxprod, (int)plist.size());
+    pw.push_back((uint32_t)prods.size());
+    pw.push_back((uint32_t)plist.size());
+    pw.push_back((uint32_t)(entries.size() / pmt::ENTRY_WORDS));
+    pw.push_back((uint32_t)ent.size());
+    prods.insert(prods.end(), plist.begin(), plist.end());
+    for (auto &e : ent) entries.insert(entries.end(), e.begin(), e.end());
+    nentry += (int)ent.size();
   }
+  while (W.size() % 4) W.push_back(0);  // 16-byte alignment of the piece headers
   W[pmt::H_OFF_PIECES] = (uint32_t)W.size();
   W.insert(W.end(), pw.begin(), pw.end());
-  W[pmt::H_OFF_SEGS] = (uint32_t)W.size();
-  W.insert(W.end(), segs.begin(), segs.end());
-  while (W.size() % 2) W.push_back(0);  // 8-byte alignment of the monomial block
-  W[pmt::H_OFF_MONOS] = (uint32_t)W.size();
-  W.insert(W.end(), monos.begin(), monos.end());
+  W[pmt::H_OFF_PRODS] = (uint32_t)W.size();
+  W.insert(W.end(), prods.begin(), prods.end());
+  while (W.size() % 4) W.push_back(0);  // 16-byte alignment of the entry block
+  W[pmt::H_OFF_ENTRIES] = (uint32_t)W.size();
+  W.insert(W.end(), entries.begin(), entries.end());
   W[pmt::H_OFF_POST] = (uint32_t)W.size();
   for (auto &po : LD.post) W.push_back((uint32_t)po[0] | ((uint32_t)hold[po[1]] << 8) | ((uint32_t)hold[po[2]] << 16));
   while (W.size() % 4) W.push_back(0);  // 16-byte multiple for bulk copies
-  W[pmt::H_NMONOS] = nmono;
+  W[pmt::H_NENTRIES] = nentry;
   W[pmt::H_DEGREE] = degree;
-  W[pmt::H_NSEGS] = (uint32_t)(segs.size() / 2);
+  W[pmt::H_NPRODS] = (uint32_t)prods.size();
+  W[pmt::H_MAXPROD] = maxprod;
   W[pmt::H_WORDS] = (uint32_t)W.size();
   if (W.size() > (size_t)pmt::MAX_TABLE_WORDS) fail(E_UNSUP, "compiled table larger than 16 KB");
   Result r;
@@ -1365,7 +1387,7 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
   r.n_atoms = na;
   r.n_conds = NC;
   r.n_pieces = (int)pieces.size();
-  r.n_monos = nmono;
+  r.n_monos = nentry;
   r.degree = degree;
   return r;
 }

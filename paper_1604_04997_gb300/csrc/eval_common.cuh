@@ -35,12 +35,13 @@ __device__ __forceinline__ int64_t ld64(const uint32_t *p) {
 }
 
 // Evaluate table T at point n (int32, already known to lie in T's box) for the
-// calling thread.  vals: this thread's value slots, stride `vs` (shared memory,
-// one column per thread).  emit(col, hold, value) is called once per non-empty
-// segment; post(col, value) once per post-op.  Returns false on a malformed table.
+// calling thread.  vals: this thread's value slots (int32, stride vs); prods: its
+// product slots (int64, stride ps), both in shared memory.  emit(col, value) is
+// called once per non-empty column of the selected piece, post(col, value) once
+// per post-op.  Returns false on a malformed table.
 template <class Emit, class Post>
-__device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const int32_t *n, int32_t *vals,
-                                           int vs, Emit &&emit, Post &&post) {
+__device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const int32_t *n, int32_t *vals, int vs,
+                                           int64_t *prods, int ps, Emit &&emit, Post &&post) {
   const int P = (int)T[pmt::H_NPARAMS];
   const int A = (int)T[pmt::H_NATOMS];
   const int NC = (int)T[pmt::H_NCONDS];
@@ -50,12 +51,13 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
     if (p < P) vals[p * vs] = n[p];
   const uint32_t *at = T + T[pmt::H_OFF_ATOMS];
   for (int a = 0; a < A; a++, at += pmt::ATOM_WORDS) {
-    int32_t num = (int32_t)at[4];
-#pragma unroll
-    for (int p = 0; p < 4; p++)
-      if (p < P) num += (int32_t)at[p] * n[p];
-    uint32_t packed = at[7];
-    vals[(P + a) * vs] = floor_div(num, at[5], at[6], (packed >> 8) & 0xFF, (packed >> 16) & 1);
+    const uint4 q0 = *(const uint4 *)at, q1 = *(const uint4 *)(at + 4);
+    int32_t num = (int32_t)q1.x;
+    num += (int32_t)q0.x * n[0];
+    if (P > 1) num += (int32_t)q0.y * n[1];
+    if (P > 2) num += (int32_t)q0.z * n[2];
+    if (P > 3) num += (int32_t)q0.w * n[3];
+    vals[(P + a) * vs] = floor_div(num, q1.y, q1.z, (q1.w >> 8) & 0xFF, (q1.w >> 16) & 1);
   }
   uint32_t bits = 0;
   const uint32_t *cd = T + T[pmt::H_OFF_CONDS];
@@ -67,35 +69,35 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
     cd += 3 + 2 * nt;
   }
   const uint32_t *lut = T + T[pmt::H_OFF_LUT];
-  uint32_t piece = (lut[bits >> 2] >> (8 * (bits & 3))) & 0xFF;
+  const uint32_t piece = (lut[bits >> 2] >> (8 * (bits & 3))) & 0xFF;
   if (piece >= T[pmt::H_NPIECES]) return false;
-  const uint32_t *pc = T + T[pmt::H_OFF_PIECES] + 2 * piece;
-  const uint32_t *seg = T + T[pmt::H_OFF_SEGS] + 2 * pc[0];
-  const uint32_t nseg = pc[1];
-  const uint32_t *monos = T + T[pmt::H_OFF_MONOS];
+  const uint4 pc = *(const uint4 *)(T + T[pmt::H_OFF_PIECES] + 4 * piece);
+  if (pc.y > (uint32_t)pmt::MAX_PRODS) return false;
+  const uint32_t *pr = T + T[pmt::H_OFF_PRODS] + pc.x;
+  for (uint32_t j = 0; j < pc.y; j++) {
+    const uint32_t w = pr[j];
+    const uint32_t src = w & 0xFF;
+    const int64_t v = (int64_t)vals[((w >> 8) & 0xFF) * vs];
+    prods[j * ps] = src == 0xFF ? v : (int64_t)((uint64_t)prods[src * ps] * (uint64_t)v);
+  }
+  const uint4 *en = (const uint4 *)(T + T[pmt::H_OFF_ENTRIES]) + pc.z;
   int64_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
-  for (uint32_t s = 0; s < nseg; s++, seg += 2) {
-    const uint32_t w0 = seg[0];
-    const uint32_t nm = w0 >> 16;
-    const uint32_t *mo = monos + pmt::MONO_WORDS * seg[1];
-    uint64_t acc = 0;
-    for (uint32_t q = 0; q < nm; q++, mo += pmt::MONO_WORDS) {
-      uint64_t prod = (uint64_t)ld64(mo);
-      const uint32_t f = mo[2];
-#pragma unroll
-      for (int d = 0; d < 4; d++) {
-        uint32_t v = (f >> (8 * d)) & 0xFF;
-        if (v != 0xFF) prod *= (uint64_t)(int64_t)vals[v * vs];
-      }
-      acc += prod;
+  uint64_t acc = 0;
+  for (uint32_t e = 0; e < pc.w; e++) {
+    const uint4 E = en[e];
+    const uint32_t p = (E.z >> 8) & 0xFF;
+    const uint64_t coef = (uint64_t)E.x | ((uint64_t)E.y << 32);
+    acc += p == 0xFF ? coef : coef * (uint64_t)prods[p * ps];
+    if (E.z & pmt::ENTRY_LAST) {
+      const int64_t val = (int64_t)acc;
+      const uint32_t hold = (E.z >> 16) & 0xF;
+      if (hold == 1) h0 = val;
+      else if (hold == 2) h1 = val;
+      else if (hold == 3) h2 = val;
+      else if (hold == 4) h3 = val;
+      emit((int)(E.z & 0xFF), val);
+      acc = 0;
     }
-    const int64_t val = (int64_t)acc;
-    const uint32_t hold = (w0 >> 8) & 0xFF;
-    if (hold == 1) h0 = val;
-    else if (hold == 2) h1 = val;
-    else if (hold == 3) h2 = val;
-    else if (hold == 4) h3 = val;
-    emit((int)(w0 & 0xFF), val);
   }
   const uint32_t npost = T[pmt::H_NPOST];
   const uint32_t *po = T + T[pmt::H_OFF_POST];

@@ -13,14 +13,20 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
                                int64_t n_points, int P, int K, int64_t *out, int *status, cudaStream_t st);
 
 // K2 (eval.cu)
+constexpr int K2_MAX_SLICES = 16;
 struct K2Args {
   const uint32_t *arena;
   const int64_t *tab_off;      // [n_variants] word offsets into arena
   const int32_t *var_off;      // [n_templates+1] CSR into tab_off
   const int32_t *tmpl_nparams; // [n_templates]
-  const int4 *units;           // [n_units] (template, first point, count, 0)
+  const int32_t *tmpl_slices;  // [n_templates] variant slices S per point chunk (<= K2_MAX_SLICES)
+  const int4 *chunks;          // [n_chunks] (template, first point, point count <= 32, first partial slot)
+  const int4 *units;           // [n_units] (chunk, slice, first variant, end variant), schedule order
   int n_units;
   int *unit_counter;           // reset to 0 before each launch
+  int *chunk_count;            // [n_chunks] slices finished, reset to 0 before each launch
+  float *part_h, *part_l;      // [slots][16][32] partial lists of chunks with S > 1
+  int *part_i;
   const int64_t *points;       // [total][4]
   const double *w;             // [32]
   int topk;

@@ -24,11 +24,13 @@
   } while (0)
 
 static constexpr int UNIT_POINTS = 32;
+static constexpr int SLICE_VARIANTS = 160;
 
 // Algorithmic lane operations of one evaluation of a table (average over its pieces):
 //   atom floor((a.n + b)/c):  P multiply-adds, 1 add, 5 for the magic division   P + 6
 //   condition with t terms:   2 per 64-bit multiply-add, 2 for sum and compare    2t + 2
-//   monomial of degree d:     3 per 64-bit multiply, 2 for the 64-bit add         3d + 2
+//   monomial product:         one 64-bit multiply                                 3
+//   coefficient entry:        64-bit multiply and add                             5
 //   non-empty column:         Dot2 term (split 4, products 4, TwoSum 6, comp. 1)  15
 //   post-op min(loads, stores): compare-select 2 + Dot2 term                      17
 //   box check, piece lookup, top-k compare                                        10
@@ -43,12 +45,12 @@ static double table_work(const std::vector<uint32_t> &w) {
   const int np = std::max(1u, w[pmt::H_NPIECES]);
   double per = 0;
   for (int p = 0; p < np; p++) {
-    const uint32_t *pc = w.data() + w[pmt::H_OFF_PIECES] + 2 * p;
-    const uint32_t *seg = w.data() + w[pmt::H_OFF_SEGS] + 2 * pc[0];
-    for (uint32_t s = 0; s < pc[1]; s++, seg += 2) {
-      per += 15.0;
-      const uint32_t *mo = w.data() + w[pmt::H_OFF_MONOS] + pmt::MONO_WORDS * seg[1];
-      for (uint32_t q = 0; q < (seg[0] >> 16); q++, mo += pmt::MONO_WORDS) per += 3.0 * mo[3] + 2.0;
+    const uint32_t *pc = w.data() + w[pmt::H_OFF_PIECES] + 4 * p;
+    per += 3.0 * pc[1];                                    // products: one 64-bit multiply each
+    const uint32_t *en = w.data() + w[pmt::H_OFF_ENTRIES] + pmt::ENTRY_WORDS * pc[2];
+    for (uint32_t e = 0; e < pc[3]; e++, en += pmt::ENTRY_WORDS) {
+      per += 5.0;                                          // 64-bit multiply-add
+      if (en[2] & pmt::ENTRY_LAST) per += 15.0;            // Dot2 term of the column
     }
   }
   return ops + per / np;
@@ -83,28 +85,47 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
       if (v == var_off[t]) nparams[t] = (int)w[pmt::H_NPARAMS];
       else if (nparams[t] != (int)w[pmt::H_NPARAMS])
         return pm_set_error(PM_ERR_INVALID_ARG, "variants of one template differ in parameter count");
+      if ((int)(w[pmt::H_NPARAMS] + w[pmt::H_NATOMS]) > 16)
+        return pm_set_error(PM_ERR_UNSUPPORTED, "fused ranking supports tables with at most 16 values");
       off[v] = c->dev_off[id];
       tw[t] += table_work(w);
     }
   }
-  // work units: (template, 32 consecutive points); most expensive first (LPT)
-  struct U { int t; int p0; int n; double cost; };
+  // Point chunks of 32 (one point per lane); each chunk's variants are cut into S slices
+  // of about SLICE_VARIANTS so that work units stay small; units are ordered most
+  // expensive first (longest processing time first).
+  std::vector<int32_t> slices(T, 1);
+  for (int t = 0; t < T; t++) {
+    int nvt = var_off[t + 1] - var_off[t];
+    slices[t] = std::max(1, std::min(pmd::K2_MAX_SLICES, (nvt + SLICE_VARIANTS - 1) / SLICE_VARIANTS));
+  }
+  struct U { int chunk, slice, vb, ve; double cost; };
+  std::vector<int4> chunks;
   std::vector<U> units;
   double total_work = 0;
   int64_t evals = 0;
+  int slots = 0;
   for (int t = 0; t < T; t++) {
-    int nvt = var_off[t + 1] - var_off[t];
+    const int nvt = var_off[t + 1] - var_off[t];
+    const int S = slices[t];
+    const int L = std::max(1, (nvt + S - 1) / S);
     for (int64_t p = pt_off[t]; p < pt_off[t + 1]; p += UNIT_POINTS) {
-      int n = (int)std::min<int64_t>(UNIT_POINTS, pt_off[t + 1] - p);
-      if (nvt == 0) { units.push_back({t, (int)p, n, 0}); continue; }
-      units.push_back({t, (int)p, n, tw[t] * UNIT_POINTS});
+      const int n = (int)std::min<int64_t>(UNIT_POINTS, pt_off[t + 1] - p);
+      const int c = (int)chunks.size();
+      chunks.push_back(make_int4(t, (int)p, n, slots));
+      slots += S;
+      for (int s = 0; s < S; s++) {
+        int vb = var_off[t] + std::min(nvt, s * L), ve = var_off[t] + std::min(nvt, (s + 1) * L);
+        double per = nvt ? tw[t] / nvt : 0;
+        units.push_back({c, s, vb, ve, per * (ve - vb) * n});
+      }
       total_work += tw[t] * n;
       evals += (int64_t)nvt * n;
     }
   }
   std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
   std::vector<int4> hu(units.size());
-  for (size_t i = 0; i < units.size(); i++) hu[i] = make_int4(units[i].t, units[i].p0, units[i].n, 0);
+  for (size_t i = 0; i < units.size(); i++) hu[i] = make_int4(units[i].chunk, units[i].slice, units[i].vb, units[i].ve);
 
   Plan *p = new Plan();
   auto alloc = [&](const void *h, size_t bytes, void **d) -> pm_status {
@@ -121,10 +142,22 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   p->d_var_off = (const int32_t *)d;
   if ((s = alloc(nparams.data(), sizeof(int32_t) * T, &d))) return s;
   p->d_nparams = (const int32_t *)d;
+  if ((s = alloc(slices.data(), sizeof(int32_t) * T, &d))) return s;
+  p->d_slices = (const int32_t *)d;
+  if ((s = alloc(chunks.data(), sizeof(int4) * chunks.size(), &d))) return s;
+  p->d_chunks = (const int4 *)d;
   if ((s = alloc(hu.data(), sizeof(int4) * hu.size(), &d))) return s;
   p->d_units = (const int4 *)d;
-  if ((s = alloc(nullptr, sizeof(int), &d))) return s;
-  p->d_counter = (int *)d;
+  if ((s = alloc(nullptr, sizeof(int) * (chunks.size() + 1), &d))) return s;
+  p->d_counter = (int *)d;  // [0] unit counter, [1..] per-chunk slice counters
+  const size_t part = (size_t)slots * 16 * 32 * 4;
+  if ((s = alloc(nullptr, part, &d))) return s;
+  p->d_part_h = (float *)d;
+  if ((s = alloc(nullptr, part, &d))) return s;
+  p->d_part_l = (float *)d;
+  if ((s = alloc(nullptr, part, &d))) return s;
+  p->d_part_i = (int *)d;
+  p->n_chunks = (int)chunks.size();
   p->n_units = (int)hu.size();
   p->n_templates = T;
   p->total_points = np;
@@ -140,15 +173,21 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
 
 static pm_status launch_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w, int topk, int32_t *idx,
                            double *t, cudaStream_t st, int nw, int grid) {
-  CU(cudaMemsetAsync(p->d_counter, 0, sizeof(int), st));
+  CU(cudaMemsetAsync(p->d_counter, 0, sizeof(int) * (p->n_chunks + 1), st));
   pmd::K2Args a;
   a.arena = c->arena;
   a.tab_off = p->d_tab_off;
   a.var_off = p->d_var_off;
   a.tmpl_nparams = p->d_nparams;
+  a.tmpl_slices = p->d_slices;
+  a.chunks = p->d_chunks;
   a.units = p->d_units;
   a.n_units = p->n_units;
   a.unit_counter = p->d_counter;
+  a.chunk_count = p->d_counter + 1;
+  a.part_h = p->d_part_h;
+  a.part_l = p->d_part_l;
+  a.part_i = p->d_part_i;
   a.points = pts;
   a.w = w;
   a.topk = topk;

@@ -17,9 +17,13 @@ struct Plan {
   const int64_t *d_tab_off = nullptr;
   const int32_t *d_var_off = nullptr;
   const int32_t *d_nparams = nullptr;
+  const int32_t *d_slices = nullptr;
+  const int4 *d_chunks = nullptr;
   const int4 *d_units = nullptr;
   int *d_counter = nullptr;
-  int n_units = 0, n_templates = 0;
+  float *d_part_h = nullptr, *d_part_l = nullptr;
+  int *d_part_i = nullptr;
+  int n_units = 0, n_templates = 0, n_chunks = 0;
   int64_t total_points = 0, total_evals = 0;
   double work_per_eval = 0;         // average (atoms + conditions + monomials) per evaluation
   int nw = 8, grid = 0;             // launch shape (autotuned when enabled)

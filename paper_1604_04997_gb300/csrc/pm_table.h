@@ -7,8 +7,8 @@
 //      values v[P..P+A) = atoms floor((a . n + b) / c), c >= 2;
 //   2. bits: condition j holds iff const_j + sum_t coef_jt * v[idx_jt] >= 0;
 //   3. piece = lut[bits];
-//   4. for each segment (column, monomials) of the piece:
-//        column value = sum over monomials of coef * prod v[f]  (exact int64);
+//   4. the piece's products (distinct monomials prod v[f]) are formed once, then
+//      each column value = sum of integer coef * product over its entries (exact int64);
 //   5. post-ops: column = min(held value A, held value B)   (min(loads, stores)).
 // Columns that no segment names are zero.  Hidden columns (index >= k) only feed
 // post-ops.
@@ -27,20 +27,27 @@ constexpr int MAX_TABLE_WORDS = 4096;  // 16 KB
 
 enum Header {
   H_MAGIC = 0, H_WORDS, H_NPARAMS, H_NATOMS, H_NCONDS, H_NPIECES, H_K, H_NHIDDEN, H_NPOST,
-  H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_SEGS, H_OFF_MONOS, H_OFF_POST,
-  H_BOX_LO = 16, H_BOX_HI = 20, H_NMONOS = 24, H_DEGREE = 25, H_NSEGS = 26, H_RESERVED = 27,
+  H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_PRODS, H_OFF_ENTRIES, H_OFF_POST,
+  H_BOX_LO = 16, H_BOX_HI = 20, H_NENTRIES = 24, H_DEGREE = 25, H_NPRODS = 26, H_MAXPROD = 27,
   HEADER_WORDS = 28
 };
+
+constexpr int MAX_PRODS = 16;  // products per piece
 
 // Atom: 8 words  a0 a1 a2 a3 b c magic packed
 //   packed: bits 0..7 shift1, 8..15 shift2, bit 16: numerator may be negative
 constexpr int ATOM_WORDS = 8;
 // Condition: [n_terms, const_lo, const_hi, (idx, coef) * n_terms]
 // LUT: 2^n_conds bytes (piece ids), packed 4 per word.
-// Piece: 2 words [seg_begin, n_segs]
-// Segment: 2 words [col | (hold+1) << 8 | n_mono << 16, mono_begin]
-// Monomial: 4 words [coef_lo, coef_hi, factors (4 x 8 bit, 0xFF = none), degree]
-constexpr int MONO_WORDS = 4;
+// Piece: 4 words [prod_begin, n_prods, entry_begin, n_entries]
+// Product: 1 word [src | value << 8]; product_j = (src == 0xFF ? 1 : product_src) * v[value],
+//   src < j, so products are computed in order (the distinct monomials of the piece
+//   and the prefixes they are built from).
+// Entry: 4 words [coef_lo, coef_hi, packed, 0]; entries are sorted by column and
+//   column value = sum of coef * product over its entries (prod 0xFF = constant 1).
+//   packed: col (8) | prod << 8 | (hold+1) << 16 (4 bits) | last-of-column << 20
+constexpr int ENTRY_WORDS = 4;
+constexpr uint32_t ENTRY_LAST = 1u << 20;
 // Post-op: 1 word [out_col | holdA << 8 | holdB << 16]
 
 }  // namespace pmt

@@ -6,7 +6,7 @@ GPU.  It is never imported by the library, so it cannot act as a CPU fallback.
 import numpy as np
 
 H_MAGIC, H_WORDS, H_NPARAMS, H_NATOMS, H_NCONDS, H_NPIECES, H_K, H_NHIDDEN, H_NPOST = range(9)
-H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_SEGS, H_OFF_MONOS, H_OFF_POST = range(9, 16)
+H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_PRODS, H_OFF_ENTRIES, H_OFF_POST = range(9, 16)
 H_BOX_LO, H_BOX_HI = 16, 20
 
 
@@ -74,27 +74,30 @@ class Table:
         lut = w[H_OFF_LUT]
         piece = (w[lut + (bits >> 2)] >> (8 * (bits & 3))) & 0xFF
         assert piece < w[H_NPIECES]
-        pb = w[H_OFF_PIECES] + 2 * piece
-        seg0, nseg = w[pb], w[pb + 1]
+        pb = w[H_OFF_PIECES] + 4 * piece
+        p0, n_prod, e0, n_ent = w[pb:pb + 4]
+        prods = []
+        for j in range(n_prod):
+            x = w[w[H_OFF_PRODS] + p0 + j]
+            src, v = x & 0xFF, (x >> 8) & 0xFF
+            assert src == 0xFF or src < j
+            prods.append((1 if src == 0xFF else prods[src]) * vals[v])
         cols = [0] * (self.k + self.hidden)
         hold = [0, 0, 0, 0]
-        for s in range(nseg):
-            so = w[H_OFF_SEGS] + 2 * (seg0 + s)
-            col, h, nm = w[so] & 0xFF, (w[so] >> 8) & 0xFF, w[so] >> 16
-            mo = w[H_OFF_MONOS] + 4 * w[so + 1]
-            acc = 0
-            for q in range(nm):
-                coef = _s64(w[mo], w[mo + 1])
-                f = w[mo + 2]
-                for d in range(4):
-                    v = (f >> (8 * d)) & 0xFF
-                    if v != 0xFF:
-                        coef *= vals[v]
-                acc += coef
-                mo += 4
-            cols[col] = acc
-            if h:
-                hold[h - 1] = acc
+        acc = 0
+        for e in range(n_ent):
+            eo = w[H_OFF_ENTRIES] + 4 * (e0 + e)
+            coef = _s64(w[eo], w[eo + 1])
+            pk = w[eo + 2]
+            pr = (pk >> 8) & 0xFF
+            acc += coef * (1 if pr == 0xFF else prods[pr])
+            if pk & (1 << 20):
+                col, h = pk & 0xFF, (pk >> 16) & 0xF
+                cols[col] = acc
+                if h:
+                    hold[h - 1] = acc
+                acc = 0
+        assert acc == 0
         po = w[H_OFF_POST]
         for q in range(w[H_NPOST]):
             x = w[po + q]
