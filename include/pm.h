@@ -54,7 +54,7 @@ typedef int32_t pm_status;
 #define PM_LAYOUT_12 12           /* 12 aggregated feature columns */
 #define PM_LAYOUT_32 32           /* 32 feature columns */
 
-#define PM_PREC_FP64 0            /* FP64-accurate (compensated arithmetic on FP32 pipes) */
+#define PM_PREC_FP64 0            /* FP64-accurate (exact fixed-point products, 128-bit sums) */
 #define PM_PREC_BF16X3 1          /* three-term bf16 split on tensor cores, FP32 accumulate */
 #define PM_PREC_NATIVE_FP64 2     /* plain double FMA (cross-check path) */
 
@@ -116,7 +116,9 @@ pm_status pm_eval_counts(pm_ctx *ctx, const int32_t *h_table_ids, int32_t n_tabl
 /* ------------------------------------------------------------------ prediction (Sec. 2) */
 
 /* d_T[r][m] = sum_i d_F[r][i] * d_W[m][i]   (F int64 [R][k], W fp64 [M][k], T fp64 [R][M]).
- * precision PM_PREC_FP64: relative error <= ~k 2^-44 of sum_i |F_ri W_mi|;
+ * precision PM_PREC_FP64: weights rounded to 58-bit fixed point per model, products and
+ *   sums exact in 128 bits: error <= 2^-59 (max_i|W_mi| / min_i|W_mi|) sum_i |F_ri W_mi|
+ *   plus 2^-56 |T|;
  * PM_PREC_BF16X3: <= ~1e-6 of the same (tensor cores, power-of-two column scaling);
  * PM_PREC_NATIVE_FP64: double FMA. */
 pm_status pm_predict(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t k, const double *d_W,

@@ -91,11 +91,7 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
 constexpr int K2_TOPK = 16;
 constexpr int TB_WORDS = 768;   // per-warp staging buffer (3 KB), double-buffered
 constexpr int K2_VMAX = 16;     // value slots per lane
-
-// Ranking key: a normalised float-float time (hi = fl(hi + lo)) and the variant index.
-__device__ __forceinline__ bool key_less(float ah, float al, int ai, float bh, float bl, int bi) {
-  return ah < bh || (ah == bh && (al < bl || (al == bl && ai < bi)));
-}
+constexpr uint64_t OFF_MASK = (1ull << 40) - 1;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
   unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -105,74 +101,79 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_all;\n" ::); }
 
+__device__ __forceinline__ bool kid_less(int64_t ak, int ai, int64_t bk, int bi) {
+  return ak < bk || (ak == bk && ai < bi);
+}
+
+// The 16 best (key, variant) pairs of one point, sorted.  Within one warp variants
+// arrive in increasing index order, so a strict key comparison keeps ties in index order.
 struct TopK {
-  float h[K2_TOPK], l[K2_TOPK];
+  int64_t k[K2_TOPK];
   int id[K2_TOPK];
   __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int q = 0; q < K2_TOPK; q++) { h[q] = __int_as_float(0x7f800000); l[q] = 0.f; id[q] = 0x7fffffff; }
+    for (int q = 0; q < K2_TOPK; q++) { k[q] = INT64_MAX; id[q] = 0x7fffffff; }
   }
-  __device__ __forceinline__ void insert(float th, float tl, int ti) {
-    if (!key_less(th, tl, ti, h[K2_TOPK - 1], l[K2_TOPK - 1], id[K2_TOPK - 1])) return;
+  __device__ __forceinline__ void insert(int64_t key, int vid) {
 #pragma unroll
-    for (int q = K2_TOPK - 1; q >= 0; q--) {
-      if (key_less(th, tl, ti, h[q], l[q], id[q])) {
-        if (q == 0 || key_less(h[q - 1], l[q - 1], id[q - 1], th, tl, ti)) { h[q] = th; l[q] = tl; id[q] = ti; }
-        else { h[q] = h[q - 1]; l[q] = l[q - 1]; id[q] = id[q - 1]; }
-      }
+    for (int q = K2_TOPK - 1; q > 0; q--) {
+      const bool shift = key < k[q - 1];
+      const bool here = !shift && key < k[q];
+      k[q] = shift ? k[q - 1] : (here ? key : k[q]);
+      id[q] = shift ? id[q - 1] : (here ? vid : id[q]);
     }
+    if (key < k[0]) { k[0] = key; id[0] = vid; }
   }
 };
 
-// Merge n sorted lists of 16 (stored at base + list*stride_list + q*stride_q, SoA) for this lane.
+// Merge n sorted lists of 16 (element (list, q) at list*stride_list + q*stride_q) for this lane.
 template <int MAXN, bool CG>
-__device__ __forceinline__ void merge_lists(const float *hs, const float *ls, const int *is, int n, int stride_list,
-                                            int stride_q, TopK &out) {
+__device__ __forceinline__ void merge_lists(const int64_t *ks, const int *is, int n, int stride_list, int stride_q,
+                                            TopK &out) {
   int head[MAXN];
 #pragma unroll
   for (int w = 0; w < MAXN; w++) head[w] = 0;
 #pragma unroll
   for (int q = 0; q < K2_TOPK; q++) {
     int best = -1;
-    float bh = 0.f, bl = 0.f;
+    int64_t bk = INT64_MAX;
     int bi = 0x7fffffff;
 #pragma unroll
     for (int w = 0; w < MAXN; w++) {
       if (w < n && head[w] < K2_TOPK) {
         const int o = w * stride_list + head[w] * stride_q;
-        float xh, xl;
-        int xi;
-        if (CG) { xh = __ldcg(hs + o); xl = __ldcg(ls + o); xi = __ldcg(is + o); }
-        else { xh = hs[o]; xl = ls[o]; xi = is[o]; }
-        if (best < 0 || key_less(xh, xl, xi, bh, bl, bi)) { best = w; bh = xh; bl = xl; bi = xi; }
+        const int64_t xk = CG ? __ldcg(ks + o) : ks[o];
+        const int xi = CG ? __ldcg(is + o) : is[o];
+        if (best < 0 || kid_less(xk, xi, bk, bi)) { best = w; bk = xk; bi = xi; }
       }
     }
 #pragma unroll
     for (int w = 0; w < MAXN; w++) if (w == best) head[w]++;
-    out.h[q] = bh;
-    out.l[q] = bl;
+    out.k[q] = bk;
     out.id[q] = bi;
   }
 }
 
 // Warp w of a CTA evaluates variants vb+w, vb+w+NW, ... < ve of the unit's template
 // for the unit's points (one point per lane; the table is shared by the warp and read
-// as broadcasts from shared memory).  Each lane keeps the 16 best (time, variant)
-// pairs of its point in registers.  The CTA merges its warps' lists; a point chunk
-// split into S variant slices is finished by the last of its S units (partial lists
-// in a scratch buffer, a fence and an atomic counter; no waiting).
+// as broadcasts from shared memory).  Counts are exact; the predicted time is the
+// exact fixed-point sum S = sum_i count_i W_i (128-bit, integer pipes only), ranked by
+// a monotone 64-bit key.  Each lane keeps its point's 16 best (key, variant) pairs in
+// registers; a per-point threshold shared by the CTA's warps rejects most candidates.
+// The CTA merges its warps' lists; a point chunk split into S variant slices is
+// finished by the last of its S units (partial lists in a scratch buffer, a fence and
+// an atomic counter; no waiting).
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *tbuf = (uint32_t *)smem;                                  // [NW][2][TB_WORDS]
   int32_t *vals = (int32_t *)(tbuf + NW * 2 * TB_WORDS);              // [NW][VMAX][32]
   int64_t *prods = (int64_t *)(vals + NW * K2_VMAX * 32);             // [NW][16][32]
-  float *mh = (float *)smem;                                          // merge lists [NW][16][32] (alias tbuf)
-  float *ml = mh + NW * K2_TOPK * 32;
-  int *mi = (int *)(ml + NW * K2_TOPK * 32);
-  __shared__ float s_wh[pmt::MAX_COLS], s_wl[pmt::MAX_COLS];
-  __shared__ double s_unscale;
-  __shared__ int s_unit, s_last;
+  int64_t *mk = (int64_t *)smem;                                      // merge lists [NW][16][32] (alias tbuf)
+  int *mi = (int *)(mk + NW * K2_TOPK * 32);
+  __shared__ int64_t s_W[pmt::MAX_COLS];
+  __shared__ unsigned long long s_thr[32];
+  __shared__ int s_E, s_unit;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *mybuf = tbuf + warp * 2 * TB_WORDS;
@@ -180,23 +181,15 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   int64_t *myprods = prods + warp * pmt::MAX_PRODS * 32 + lane;
 
   if (threadIdx.x == 0) {
-    // power-of-two scaling of the weights into the FP32 range
-    double mx = 0;
-    for (int c = 0; c < 32; c++) mx = fmax(mx, fabs(a.w[c]));
-    int e = 0;
-    if (mx > 0) frexp(mx, &e);
-    const double sc = ldexp(1.0, -e);
-    for (int c = 0; c < pmt::MAX_COLS; c++) {
-      FF f = split_weight(c < 32 ? a.w[c] * sc : 0.0);
-      s_wh[c] = f.hi;
-      s_wl[c] = f.lo;
-    }
-    s_unscale = ldexp(1.0, e);
+    const int E = weight_exponent(a.w, 32);
+    for (int c = 0; c < pmt::MAX_COLS; c++) s_W[c] = c < 32 ? llrint(ldexp(a.w[c], E)) : 0;
+    s_E = E;
   }
   __syncthreads();
 
   while (true) {
     if (threadIdx.x == 0) s_unit = atomicAdd(a.unit_counter, 1);
+    if (threadIdx.x < 32) s_thr[threadIdx.x] = (unsigned long long)INT64_MAX;
     __syncthreads();
     const int u = s_unit;
     __syncthreads();
@@ -219,43 +212,46 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     const int v0 = a.var_off[t];
     const int ve = U.w;
     int v = U.z + warp;
-    auto stage_table = [&](int vv, int slot) {
-      if (vv < ve) {
-        const uint32_t *g = a.arena + a.tab_off[vv];
-        const int words = (int)g[pmt::H_WORDS];
-        if (words <= TB_WORDS)
-          for (int i = lane; i < words / 4; i += 32) cp_async16(mybuf + slot * TB_WORDS + 4 * i, g + 4 * i);
+    auto stage = [&](uint64_t po, int slot) {
+      const int words = (int)(po >> 40);
+      if (words <= TB_WORDS) {
+        const uint32_t *g = a.arena + (po & OFF_MASK);
+        for (int i = lane; i < words / 4; i += 32) cp_async16(mybuf + slot * TB_WORDS + 4 * i, g + 4 * i);
       }
       cp_async_commit();
     };
-    stage_table(v, 0);
+    uint64_t po_cur = v < ve ? a.tab_off[v] : 0;
+    uint64_t po_nxt = v + NW < ve ? a.tab_off[v + NW] : 0;
+    stage(po_cur, 0);
     int slot = 0;
     for (; v < ve; v += NW) {
-      stage_table(v + NW, slot ^ 1);
+      const uint64_t po_nn = v + 2 * NW < ve ? a.tab_off[v + 2 * NW] : 0;  // used next iteration
+      stage(po_nxt, slot ^ 1);
       cp_async_wait1();
       __syncwarp();
-      const uint32_t *gT = a.arena + a.tab_off[v];
-      const int words = (int)gT[pmt::H_WORDS];
-      const uint32_t *T = words <= TB_WORDS ? mybuf + slot * TB_WORDS : gT;
+      const uint32_t *T = (int)(po_cur >> 40) <= TB_WORDS ? mybuf + slot * TB_WORDS : a.arena + (po_cur & OFF_MASK);
       if (live) {
         int32_t n[4];
         if (!point_in_box(T, pt, P, n)) {
           atomicOr(a.status, ST_OUT_OF_BOX);
         } else {
-          float s = 0.f, c = 0.f;
+          Acc128 acc;
+          acc.zero();
           const bool ok = eval_table(
               T, n, myvals, 32, myprods, 32,
-              [&](int col, int64_t val) { if (col < 32) dot2_add(s, c, val, s_wh[col], s_wl[col]); },
-              [&](int col, int64_t val) { dot2_add(s, c, val, s_wh[col], s_wl[col]); });
+              [&](int col, int64_t val) { if (col < 32) acc.add_mul((uint64_t)val, s_W[col]); },
+              [&](int col, int64_t val) { acc.add_mul((uint64_t)val, s_W[col]); });
           if (!ok) atomicOr(a.status, ST_BAD_TABLE);
-          // normalise (s, c) to hi = fl(s + c) with the exact remainder in lo (TwoSum)
-          const float hi = __fadd_rn(s, c);
-          const float z = __fsub_rn(hi, s);
-          const float lo = __fadd_rn(__fsub_rn(s, __fsub_rn(hi, z)), __fsub_rn(c, z));
-          tk.insert(hi, lo, v - v0);
+          const int64_t key = acc_key(acc);
+          if (key < tk.k[K2_TOPK - 1] && key <= (int64_t)s_thr[lane]) {
+            tk.insert(key, v - v0);
+            if (tk.k[K2_TOPK - 1] != INT64_MAX) atomicMin(&s_thr[lane], (unsigned long long)tk.k[K2_TOPK - 1] ^ 0ull);
+          }
         }
       }
       __syncwarp();
+      po_cur = po_nxt;
+      po_nxt = po_nn;
       slot ^= 1;
     }
     cp_async_wait0();
@@ -263,22 +259,20 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 #pragma unroll
     for (int q = 0; q < K2_TOPK; q++) {
       const int o = (warp * K2_TOPK + q) * 32 + lane;
-      mh[o] = tk.h[q];
-      ml[o] = tk.l[q];
+      mk[o] = tk.k[q];
       mi[o] = tk.id[q];
     }
     __syncthreads();
     if (warp == 0) {
       TopK m;
-      merge_lists<NW, false>(mh + lane, ml + lane, mi + lane, NW, K2_TOPK * 32, 32, m);
+      merge_lists<NW, false>(mk + lane, mi + lane, NW, K2_TOPK * 32, 32, m);
       bool write_out = S == 1;
       if (S > 1) {
         // publish this slice's list, then the last slice of the chunk merges all of them
         const int64_t slot0 = (int64_t)(C.w + U.y) * K2_TOPK * 32 + lane;
 #pragma unroll
         for (int q = 0; q < K2_TOPK; q++) {
-          a.part_h[slot0 + q * 32] = m.h[q];
-          a.part_l[slot0 + q * 32] = m.l[q];
+          a.part_k[slot0 + q * 32] = m.k[q];
           a.part_i[slot0 + q * 32] = m.id[q];
         }
         __threadfence();
@@ -289,19 +283,20 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
         if (last) {
           __threadfence();
           const int64_t b = (int64_t)C.w * K2_TOPK * 32 + lane;
-          merge_lists<K2_MAX_SLICES, true>(a.part_h + b, a.part_l + b, a.part_i + b, S, K2_TOPK * 32, 32, m);
+          merge_lists<K2_MAX_SLICES, true>(a.part_k + b, a.part_i + b, S, K2_TOPK * 32, 32, m);
           write_out = true;
         }
       }
       if (write_out && live) {
         int32_t *oi = a.top_idx + p * a.topk;
         double *ot = a.top_t + p * a.topk;
+        const int E = s_E;
 #pragma unroll
         for (int q = 0; q < K2_TOPK; q++) {
           if (q < a.topk) {
             const bool real = m.id[q] != 0x7fffffff;
             oi[q] = real ? m.id[q] : -1;
-            ot[q] = real ? ((double)m.h[q] + (double)m.l[q]) * s_unscale : __longlong_as_double(0x7ff0000000000000ll);
+            ot[q] = real ? key_value(m.k[q], E) : __longlong_as_double(0x7ff0000000000000ll);
           }
         }
       }
@@ -311,7 +306,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 }
 
 size_t k2_smem_bytes(int nw) {
-  static_assert(3 * K2_TOPK * 32 * 4 <= 2 * TB_WORDS * 4, "merge lists must fit in the table buffers");
+  static_assert(K2_TOPK * 32 * 12 <= 2 * TB_WORDS * 4, "merge lists must fit in the table buffers");
   return (size_t)nw * 2 * TB_WORDS * 4 + (size_t)nw * K2_VMAX * 32 * 4 + (size_t)nw * pmt::MAX_PRODS * 32 * 8;
 }
 

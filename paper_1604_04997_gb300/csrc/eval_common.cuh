@@ -128,40 +128,58 @@ __device__ __forceinline__ bool point_in_box(const uint32_t *T, const int64_t *p
   return ok;
 }
 
-// ---- FP64-accurate accumulation on FP32 pipes (Ogita, Rump & Oishi 2005, Dot2).
-// An exact int64 count v is split as vh + vl (vh = rn(v), vl = rn(v - vh)); the
-// weight w as wh + wl.  Each product's leading term is made error-free with an
-// FMA (TwoProduct) and summed error-free (TwoSum); the small cross terms and all
-// error terms go to a compensation accumulator.
-struct FF { float hi, lo; };
+// ---- Exact fixed-point prediction on the integer pipes.
+// Weights become integers W = round(w * 2^E) (|W| < 2^58, one E per weight vector);
+// each exact count v >= 0 contributes v * W to a 128-bit accumulator, so the sum
+// S = sum_i v_i W_i is exact and T = S * 2^-E differs from sum_i v_i w_i by at most
+// 2^-(E+1) sum_i v_i, i.e. <= 2^-59 (max|w| / min|w|) of sum_i |v_i w_i|.
+struct Acc128 {
+  uint64_t lo, hi;  // two's complement
+  __device__ __forceinline__ void zero() { lo = hi = 0; }
+  __device__ __forceinline__ void add_mul(uint64_t v, int64_t W) {
+    const uint64_t w = (uint64_t)W;
+    const uint64_t plo = v * w;
+    const uint64_t phi = __umul64hi(v, w) - (W < 0 ? v : 0ull);
+    const uint64_t nl = lo + plo;
+    hi += phi + (nl < plo ? 1ull : 0ull);
+    lo = nl;
+  }
+};
 
-__device__ __forceinline__ FF split_weight(double w) {
-  float h = __double2float_rn(w);
-  return FF{h, __double2float_rn(w - (double)h)};
+// Monotone 64-bit key of a 128-bit signed value: sign, 7-bit exponent and the 56 bits
+// below the leading one (a float with a 56-bit mantissa; equal values give equal keys).
+__device__ __forceinline__ int64_t acc_key(const Acc128 &a) {
+  const bool neg = (int64_t)a.hi < 0;
+  uint64_t ml = neg ? ~a.lo + 1ull : a.lo;
+  uint64_t mh = neg ? ~a.hi + (a.lo == 0 ? 1ull : 0ull) : a.hi;
+  if ((mh | ml) == 0) return 0;
+  const int lz = mh ? __clzll((long long)mh) : 64 + __clzll((long long)ml);
+  // normalise so that bit 127 is the leading one
+  if (lz >= 64) { mh = ml << (lz - 64); ml = 0; }
+  else if (lz > 0) { mh = (mh << lz) | (ml >> (64 - lz)); ml <<= lz; }
+  const int64_t e = 127 - lz;                       // 0..126
+  const int64_t k = ((e + 1) << 56) | (int64_t)((mh >> 7) & ((1ull << 56) - 1));
+  return neg ? -k : k;
 }
 
-// The _rn intrinsics keep the compiler from contracting these steps into FMAs,
-// which would break the error-free transformations.
-__device__ __forceinline__ void two_sum_acc(float &s, float &c, float p, float pe) {
-  float t = __fadd_rn(s, p);
-  float z = __fsub_rn(t, s);
-  float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
-  s = t;
-  c = __fadd_rn(c, __fadd_rn(e, pe));
+// Inverse of acc_key times 2^-E, for output.
+__device__ __forceinline__ double key_value(int64_t k, int E) {
+  if (k == 0) return 0.0;
+  const bool neg = k < 0;
+  const int64_t a = neg ? -k : k;
+  const int e = (int)(a >> 56) - 1;
+  const double m = 1.0 + ldexp((double)(a & ((1ll << 56) - 1)), -56);
+  const double v = ldexp(m, e - E);
+  return neg ? -v : v;
 }
 
-__device__ __forceinline__ void dot2_term(float &s, float &c, float vh, float vl, float wh, float wl) {
-  float p = __fmul_rn(vh, wh);
-  float pe = __fmaf_rn(vh, wh, -p);
-  pe = __fmaf_rn(vh, wl, pe);
-  pe = __fmaf_rn(vl, wh, pe);
-  two_sum_acc(s, c, p, pe);
-}
-
-__device__ __forceinline__ void dot2_add(float &s, float &c, int64_t v, float wh, float wl) {
-  float vh = __ll2float_rn(v);
-  float vl = __ll2float_rn(v - (int64_t)vh);
-  dot2_term(s, c, vh, vl, wh, wl);
+// Fixed-point weights: W_i = round(w_i * 2^E) with max |W_i| in [2^57, 2^58).
+__device__ __forceinline__ int weight_exponent(const double *w, int k) {
+  double mx = 0;
+  for (int c = 0; c < k; c++) mx = fmax(mx, fabs(w[c]));
+  int e = 0;
+  if (mx > 0) frexp(mx, &e);  // mx in [2^(e-1), 2^e)
+  return 58 - e;
 }
 
 }  // namespace pmd

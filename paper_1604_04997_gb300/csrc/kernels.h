@@ -16,7 +16,7 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
 constexpr int K2_MAX_SLICES = 16;
 struct K2Args {
   const uint32_t *arena;
-  const int64_t *tab_off;      // [n_variants] word offsets into arena
+  const uint64_t *tab_off;     // [n_variants] word offset into arena | table words << 40
   const int32_t *var_off;      // [n_templates+1] CSR into tab_off
   const int32_t *tmpl_nparams; // [n_templates]
   const int32_t *tmpl_slices;  // [n_templates] variant slices S per point chunk (<= K2_MAX_SLICES)
@@ -25,8 +25,8 @@ struct K2Args {
   int n_units;
   int *unit_counter;           // reset to 0 before each launch
   int *chunk_count;            // [n_chunks] slices finished, reset to 0 before each launch
-  float *part_h, *part_l;      // [slots][16][32] partial lists of chunks with S > 1
-  int *part_i;
+  int64_t *part_k;             // [slots][16][32] partial lists (ranking keys) of chunks with S > 1
+  int *part_i;                 // [slots][16][32] their variant indices
   const int64_t *points;       // [total][4]
   const double *w;             // [32]
   int topk;

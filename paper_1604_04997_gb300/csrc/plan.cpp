@@ -24,7 +24,7 @@
   } while (0)
 
 static constexpr int UNIT_POINTS = 32;
-static constexpr int SLICE_VARIANTS = 160;
+static constexpr int SLICE_VARIANTS = 400;
 
 // Algorithmic lane operations of one evaluation of a table (average over its pieces):
 //   atom floor((a.n + b)/c):  P multiply-adds, 1 add, 5 for the magic division   P + 6
@@ -87,7 +87,7 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
         return pm_set_error(PM_ERR_INVALID_ARG, "variants of one template differ in parameter count");
       if ((int)(w[pmt::H_NPARAMS] + w[pmt::H_NATOMS]) > 16)
         return pm_set_error(PM_ERR_UNSUPPORTED, "fused ranking supports tables with at most 16 values");
-      off[v] = c->dev_off[id];
+      off[v] = (int64_t)((uint64_t)c->dev_off[id] | ((uint64_t)w[pmt::H_WORDS] << 40));
       tw[t] += table_work(w);
     }
   }
@@ -137,7 +137,7 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   void *d;
   pm_status s;
   if ((s = alloc(off.data(), off.size() * 8, &d))) return s;
-  p->d_tab_off = (const int64_t *)d;
+  p->d_tab_off = (const uint64_t *)d;
   if ((s = alloc(var_off, sizeof(int32_t) * (T + 1), &d))) return s;
   p->d_var_off = (const int32_t *)d;
   if ((s = alloc(nparams.data(), sizeof(int32_t) * T, &d))) return s;
@@ -150,12 +150,10 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   p->d_units = (const int4 *)d;
   if ((s = alloc(nullptr, sizeof(int) * (chunks.size() + 1), &d))) return s;
   p->d_counter = (int *)d;  // [0] unit counter, [1..] per-chunk slice counters
-  const size_t part = (size_t)slots * 16 * 32 * 4;
-  if ((s = alloc(nullptr, part, &d))) return s;
-  p->d_part_h = (float *)d;
-  if ((s = alloc(nullptr, part, &d))) return s;
-  p->d_part_l = (float *)d;
-  if ((s = alloc(nullptr, part, &d))) return s;
+  const size_t part = (size_t)slots * 16 * 32;
+  if ((s = alloc(nullptr, part * 8, &d))) return s;
+  p->d_part_k = (int64_t *)d;
+  if ((s = alloc(nullptr, part * 4, &d))) return s;
   p->d_part_i = (int *)d;
   p->n_chunks = (int)chunks.size();
   p->n_units = (int)hu.size();
@@ -185,8 +183,7 @@ static pm_status launch_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double 
   a.n_units = p->n_units;
   a.unit_counter = p->d_counter;
   a.chunk_count = p->d_counter + 1;
-  a.part_h = p->d_part_h;
-  a.part_l = p->d_part_l;
+  a.part_k = p->d_part_k;
   a.part_i = p->d_part_i;
   a.points = pts;
   a.w = w;

@@ -14,14 +14,14 @@ struct ServeState;
 // Cached schedule of one pm_eval_predict_topk argument set.
 struct Plan {
   std::vector<void *> dev;          // device allocations owned by the plan
-  const int64_t *d_tab_off = nullptr;
+  const uint64_t *d_tab_off = nullptr;    // word offset | table words << 40
   const int32_t *d_var_off = nullptr;
   const int32_t *d_nparams = nullptr;
   const int32_t *d_slices = nullptr;
   const int4 *d_chunks = nullptr;
   const int4 *d_units = nullptr;
   int *d_counter = nullptr;
-  float *d_part_h = nullptr, *d_part_l = nullptr;
+  int64_t *d_part_k = nullptr;
   int *d_part_i = nullptr;
   int n_units = 0, n_templates = 0, n_chunks = 0;
   int64_t total_points = 0, total_evals = 0;

@@ -1,10 +1,12 @@
 // Prediction T = F W^T: the "small inner product" of Sec. 2,
 // T_wall(n) ~= sum_i alpha_i p_i(n), for many feature rows and device models.
 //
-// FP64-accurate path: FP32 compensated arithmetic (Dot2 of Ogita, Rump & Oishi,
-// SISC 2005) with every int64 count split into two floats and every weight into a
-// float pair, per-model power-of-two scaling into the FP32 range.  Error
-// <= ~k 2^-44 of sum_i |F_ri W_mi|.
+// FP64-accurate path: exact fixed-point arithmetic on the integer pipes.  Each
+// model's weights become integers W = round(w * 2^E_m) with |W| < 2^58; every
+// product F_ri W_mi is formed exactly and summed in 128 bits, then converted once.
+// Error <= 2^-(E_m+1) sum_i |F_ri| + 2^-56 |T|, i.e. about 2^-59 (max|w|/min|w|)
+// of sum_i |F_ri w_mi|.  (64-bit integer <-> float conversions, which would be
+// needed per term by a float-float scheme, run on the FP64 pipe of this GPU.)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,55 +24,50 @@ constexpr int PR_MAXK = 40;
 constexpr int PR_MAXM = 64;
 
 struct PredictSmem {
-  float fh[PR_ROWS][PR_MAXK + 1], fl[PR_ROWS][PR_MAXK + 1];
-  float wh[PR_MAXK][PR_MAXM], wl[PR_MAXK][PR_MAXM];
-  double unscale[PR_MAXM];
+  int64_t f[PR_ROWS][PR_MAXK + 1];
+  int64_t w[PR_MAXK][PR_MAXM];
+  int E[PR_MAXM];
 };
 
 __device__ void load_weights(PredictSmem &S, const double *W, int M, int k) {
-  // one thread per model: power-of-two scale so max |w| lies in [0.5, 1)
   for (int m = threadIdx.x; m < PR_MAXM; m += blockDim.x) {
-    double mx = 0;
-    if (m < M) for (int i = 0; i < k; i++) mx = fmax(mx, fabs(W[(int64_t)m * k + i]));
-    int e = 0;
-    if (mx > 0) frexp(mx, &e);
-    double sc = ldexp(1.0, -e);
-    for (int i = 0; i < PR_MAXK; i++) {
-      FF f = split_weight((m < M && i < k) ? W[(int64_t)m * k + i] * sc : 0.0);
-      S.wh[i][m] = f.hi;
-      S.wl[i][m] = f.lo;
-    }
-    S.unscale[m] = ldexp(1.0, e);
+    const int E = m < M ? weight_exponent(W + (int64_t)m * k, k) : 0;
+    for (int i = 0; i < PR_MAXK; i++) S.w[i][m] = (m < M && i < k) ? llrint(ldexp(W[(int64_t)m * k + i], E)) : 0;
+    S.E[m] = E;
   }
 }
 
 __device__ void load_rows(PredictSmem &S, const int64_t *F, int64_t r0, int64_t R, int k) {
   for (int i = threadIdx.x; i < PR_ROWS * k; i += blockDim.x) {
     int r = i / k, c = i - r * k;
-    int64_t v = (r0 + r < R) ? F[(r0 + r) * k + c] : 0;
-    float vh = __ll2float_rn(v);
-    S.fh[r][c] = vh;
-    S.fl[r][c] = __ll2float_rn(v - (int64_t)vh);
+    S.f[r][c] = (r0 + r < R) ? F[(r0 + r) * k + c] : 0;
   }
 }
 
+// signed 64 x signed 64 -> 128-bit accumulate
+__device__ __forceinline__ void acc_add_signed(Acc128 &a, int64_t v, int64_t W) {
+  const uint64_t x = (uint64_t)v, w = (uint64_t)W;
+  const uint64_t plo = x * w;
+  const uint64_t phi = __umul64hi(x, w) - (W < 0 ? x : 0ull) - (v < 0 ? w : 0ull);
+  const uint64_t nl = a.lo + plo;
+  a.hi += phi + (nl < plo ? 1ull : 0ull);
+  a.lo = nl;
+}
+
 // Each thread: rows warp + 8 q (q < 4), models lane + 32 j (j < 2).
-__device__ __forceinline__ void tile_dot2(const PredictSmem &S, int k, float s[4][2], float c[4][2]) {
+__device__ __forceinline__ void tile_fixed(const PredictSmem &S, int k, Acc128 acc[4][2]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int q = 0; q < 4; q++)
 #pragma unroll
-    for (int j = 0; j < 2; j++) s[q][j] = c[q][j] = 0.f;
+    for (int j = 0; j < 2; j++) acc[q][j].zero();
   for (int i = 0; i < k; i++) {
-    float wh0 = S.wh[i][lane], wl0 = S.wl[i][lane], wh1 = S.wh[i][lane + 32], wl1 = S.wl[i][lane + 32];
+    const int64_t w0 = S.w[i][lane], w1 = S.w[i][lane + 32];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
-      const float vh = S.fh[warp + 8 * q][i], vl = S.fl[warp + 8 * q][i];
-#pragma unroll
-      for (int j = 0; j < 2; j++) {
-        const float wh = j ? wh1 : wh0, wl = j ? wl1 : wl0;
-        dot2_term(s[q][j], c[q][j], vh, vl, wh, wl);
-      }
+      const int64_t v = S.f[warp + 8 * q][i];
+      acc_add_signed(acc[q][0], v, w0);
+      acc_add_signed(acc[q][1], v, w1);
     }
   }
 }
@@ -88,8 +85,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_ff(const int64_t *__r
     __syncthreads();
     load_rows(S, F, r0, R, k);
     __syncthreads();
-    float s[4][2], c[4][2];
-    tile_dot2(S, k, s, c);
+    Acc128 acc[4][2];
+    tile_fixed(S, k, acc);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int64_t r = r0 + warp + 8 * q;
@@ -97,7 +94,7 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_ff(const int64_t *__r
 #pragma unroll
       for (int j = 0; j < 2; j++) {
         const int m = lane + 32 * j;
-        if (m < M) T[r * M + m] = ((double)s[q][j] + (double)c[q][j]) * S.unscale[m];
+        if (m < M) T[r * M + m] = key_value(acc_key(acc[q][j]), S.E[m]);
       }
     }
   }
@@ -167,8 +164,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_argmin_part(const int
     __syncthreads();
     load_rows(S, F, r0, R, k);
     __syncthreads();
-    float s[4][2], c[4][2];
-    tile_dot2(S, k, s, c);
+    Acc128 acc[4][2];
+    tile_fixed(S, k, acc);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int64_t r = r0 + warp + 8 * q;
@@ -176,7 +173,7 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_argmin_part(const int
 #pragma unroll
       for (int j = 0; j < 2; j++) {
         const int m = lane + 32 * j;
-        const double tv = ((double)s[q][j] + (double)c[q][j]) * S.unscale[m < PR_MAXM ? m : 0];
+        const double tv = key_value(acc_key(acc[q][j]), S.E[m]);
         if (arg_less(tv, r, bt[j], br[j])) { bt[j] = tv; br[j] = r; }
       }
     }
