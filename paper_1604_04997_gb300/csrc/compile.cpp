@@ -1319,18 +1319,20 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
   std::vector<uint32_t> pw, prods, entries;
   int degree = 0, nentry = 0, maxprod = 0;
   for (auto &pc : pieces) {
-    std::map<Mono, int> pid;  // monomial (new value ids, sorted) -> product index
+    std::map<Mono, int> pid;  // monomial (new value ids, sorted) -> slot
     std::vector<uint32_t> plist;
+    const int V = C.P + na;
     std::function<int(const Mono &)> need = [&](const Mono &m) -> int {
       int d = mono_deg(m);
-      if (d == 0) return 0xFF;
+      if (d == 0) return (int)pmt::CONST_SLOT;
+      if (d == 1) return m[0];
       auto it = pid.find(m);
       if (it != pid.end()) return it->second;
       Mono pre = m;
       pre[d - 1] = 0xFF;
-      int src = need(pre);
-      int id = (int)plist.size();
-      plist.push_back((uint32_t)src | ((uint32_t)m[d - 1] << 8));
+      int a = need(pre);
+      int id = V + (int)plist.size();
+      plist.push_back((uint32_t)a | ((uint32_t)m[d - 1] << 8));
       pid[m] = id;
       return id;
     };
@@ -1355,7 +1357,7 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
       ent.back()[2] |= pmt::ENTRY_LAST;
       (void)first;
     }
-    if ((int)plist.size() > pmt::MAX_PRODS) fail(E_UNSUP, "more than 16 monomial products in a piece");
+    if (V + (int)plist.size() > pmt::MAX_PRODS) fail(E_UNSUP, "more than 27 values and products in a piece");
     maxprod = std::max(maxprod, (int)plist.size());
     pw.push_back((uint32_t)prods.size());
     pw.push_back((uint32_t)plist.size());

@@ -22,8 +22,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_eval_counts(const uint32_t *__re
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *sT = (uint32_t *)smem;                                   // table, <= 16 KB
   int64_t *stage = (int64_t *)(smem + pmt::MAX_TABLE_WORDS * 4);     // [threads][K+1]
-  int64_t *prods = stage + K1_THREADS * (K + 1);                     // [16][threads]
-  int32_t *vals = (int32_t *)(prods + pmt::MAX_PRODS * K1_THREADS);  // [32][threads]
+  int64_t *slots = stage + K1_THREADS * (K + 1);                     // [32][threads]
   const int tid = threadIdx.x;
   const uint32_t *gT = arena + tab_off[blockIdx.y];
   const int words = (int)gT[pmt::H_WORDS];
@@ -44,7 +43,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_eval_counts(const uint32_t *__re
       atomicOr(status, ST_OUT_OF_BOX);
     } else {
       bool ok = eval_table(
-          sT, n, vals + tid, K1_THREADS, prods + tid, K1_THREADS,
+          sT, n, slots + tid, K1_THREADS,
           [&](int col, int64_t v) { if (col < K) row[col] = v; },
           [&](int col, int64_t v) { if (col < K) row[col] = v; });
       if (!ok) {
@@ -66,7 +65,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_eval_counts(const uint32_t *__re
 
 size_t k1_smem_bytes(int K) {
   return (size_t)pmt::MAX_TABLE_WORDS * 4 + (size_t)K1_THREADS * (K + 1) * 8 +
-         (size_t)pmt::MAX_PRODS * K1_THREADS * 8 + (size_t)pmt::MAX_VALUES * K1_THREADS * 4;
+         (size_t)pmt::MAX_SLOTS * K1_THREADS * 8;
 }
 
 cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, int n_tables, const int64_t *points,
@@ -89,8 +88,7 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
 // ------------------------------------------------------------------------------------ K2
 
 constexpr int K2_TOPK = 16;
-constexpr int TB_WORDS = 768;   // per-warp staging buffer (3 KB), double-buffered
-constexpr int K2_VMAX = 16;     // value slots per lane
+constexpr int TB_WORDS = 704;   // per-warp staging buffer (2.75 KB), double-buffered
 constexpr uint64_t OFF_MASK = (1ull << 40) - 1;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
@@ -167,9 +165,8 @@ template <int NW>
 __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *tbuf = (uint32_t *)smem;                                  // [NW][2][TB_WORDS]
-  int32_t *vals = (int32_t *)(tbuf + NW * 2 * TB_WORDS);              // [NW][VMAX][32]
-  int64_t *prods = (int64_t *)(vals + NW * K2_VMAX * 32);             // [NW][16][32]
-  int64_t *mk = (int64_t *)smem;                                      // merge lists [NW][16][32] (alias tbuf)
+  int64_t *slots = (int64_t *)(tbuf + NW * 2 * TB_WORDS);             // [NW][32 slots][32 lanes]
+  int64_t *mk = (int64_t *)smem;                                      // merge lists [NW][16][32] (alias tbuf, slots)
   int *mi = (int *)(mk + NW * K2_TOPK * 32);
   __shared__ int64_t s_W[pmt::MAX_COLS];
   __shared__ unsigned long long s_thr[32];
@@ -177,8 +174,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t *mybuf = tbuf + warp * 2 * TB_WORDS;
-  int32_t *myvals = vals + warp * K2_VMAX * 32 + lane;
-  int64_t *myprods = prods + warp * pmt::MAX_PRODS * 32 + lane;
+  int64_t *myslots = slots + warp * pmt::MAX_SLOTS * 32 + lane;
 
   if (threadIdx.x == 0) {
     const int E = weight_exponent(a.w, 32);
@@ -199,13 +195,25 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     const int t = C.x;
     const int S = a.tmpl_slices[t];
     const int64_t p = (int64_t)C.y + lane;
-    const bool live = lane < C.z;
     const int P = a.tmpl_nparams[t];
-    int64_t pt[4] = {0, 0, 0, 0};
+    // every table of a plan's template shares one parameter box: check the point once
+    int32_t n[4] = {0, 0, 0, 0};
+    const bool live = lane < C.z;   // the lane has a point
+    bool valid = live;              // ... inside the box (else its ranking stays empty)
     if (live) {
       const int64_t *src = a.points + p * 4;
+      const int4 lo = a.tmpl_box[2 * t], hi = a.tmpl_box[2 * t + 1];
+      const int l4[4] = {lo.x, lo.y, lo.z, lo.w}, h4[4] = {hi.x, hi.y, hi.z, hi.w};
+      bool ok = true;
 #pragma unroll
-      for (int q = 0; q < 4; q++) pt[q] = src[q];
+      for (int q = 0; q < 4; q++) {
+        if (q < P) {
+          const int64_t x = src[q];
+          ok = ok && x >= l4[q] && x <= h4[q];
+          n[q] = (int32_t)x;
+        }
+      }
+      if (!ok) { atomicOr(a.status, ST_OUT_OF_BOX); valid = false; }
     }
     TopK tk;
     tk.init();
@@ -213,11 +221,9 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     const int ve = U.w;
     int v = U.z + warp;
     auto stage = [&](uint64_t po, int slot) {
-      const int words = (int)(po >> 40);
-      if (words <= TB_WORDS) {
-        const uint32_t *g = a.arena + (po & OFF_MASK);
-        for (int i = lane; i < words / 4; i += 32) cp_async16(mybuf + slot * TB_WORDS + 4 * i, g + 4 * i);
-      }
+      const int words = min((int)(po >> 40), TB_WORDS);
+      const uint32_t *g = a.arena + (po & OFF_MASK);
+      for (int i = lane; i < words / 4; i += 32) cp_async16(mybuf + slot * TB_WORDS + 4 * i, g + 4 * i);
       cp_async_commit();
     };
     uint64_t po_cur = v < ve ? a.tab_off[v] : 0;
@@ -229,24 +235,19 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       stage(po_nxt, slot ^ 1);
       cp_async_wait1();
       __syncwarp();
-      const uint32_t *T = (int)(po_cur >> 40) <= TB_WORDS ? mybuf + slot * TB_WORDS : a.arena + (po_cur & OFF_MASK);
-      if (live) {
-        int32_t n[4];
-        if (!point_in_box(T, pt, P, n)) {
-          atomicOr(a.status, ST_OUT_OF_BOX);
-        } else {
-          Acc128 acc;
-          acc.zero();
-          const bool ok = eval_table(
-              T, n, myvals, 32, myprods, 32,
-              [&](int col, int64_t val) { if (col < 32) acc.add_mul((uint64_t)val, s_W[col]); },
-              [&](int col, int64_t val) { acc.add_mul((uint64_t)val, s_W[col]); });
-          if (!ok) atomicOr(a.status, ST_BAD_TABLE);
-          const int64_t key = acc_key(acc);
-          if (key < tk.k[K2_TOPK - 1] && key <= (int64_t)s_thr[lane]) {
-            tk.insert(key, v - v0);
-            if (tk.k[K2_TOPK - 1] != INT64_MAX) atomicMin(&s_thr[lane], (unsigned long long)tk.k[K2_TOPK - 1] ^ 0ull);
-          }
+      const uint32_t *T = mybuf + slot * TB_WORDS;   // the plan admits only tables that fit
+      if (valid) {
+        Acc128 acc;
+        acc.zero();
+        const bool ok = eval_table(
+            T, n, myslots, 32,
+            [&](int col, int64_t val) { if (col < 32) acc.add_mul((uint64_t)val, s_W[col]); },
+            [&](int col, int64_t val) { acc.add_mul((uint64_t)val, s_W[col]); });
+        if (!ok) atomicOr(a.status, ST_BAD_TABLE);
+        const int64_t key = acc_key(acc);
+        if (key < tk.k[K2_TOPK - 1] && key <= (int64_t)s_thr[lane]) {
+          tk.insert(key, v - v0);
+          if (tk.k[K2_TOPK - 1] != INT64_MAX) atomicMin(&s_thr[lane], (unsigned long long)tk.k[K2_TOPK - 1]);
         }
       }
       __syncwarp();
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       slot ^= 1;
     }
     cp_async_wait0();
-    __syncthreads();  // table buffers are reused as merge buffers below
+    __syncthreads();  // table and slot buffers are reused as merge buffers below
 #pragma unroll
     for (int q = 0; q < K2_TOPK; q++) {
       const int o = (warp * K2_TOPK + q) * 32 + lane;
@@ -305,9 +306,12 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   }
 }
 
+int k2_table_words() { return TB_WORDS; }
+
 size_t k2_smem_bytes(int nw) {
-  static_assert(K2_TOPK * 32 * 12 <= 2 * TB_WORDS * 4, "merge lists must fit in the table buffers");
-  return (size_t)nw * 2 * TB_WORDS * 4 + (size_t)nw * K2_VMAX * 32 * 4 + (size_t)nw * pmt::MAX_PRODS * 32 * 8;
+  static_assert(K2_TOPK * 32 * 12 <= 2 * TB_WORDS * 4 + pmt::MAX_SLOTS * 32 * 8,
+                "merge lists must fit in the table and slot buffers");
+  return (size_t)nw * 2 * TB_WORDS * 4 + (size_t)nw * pmt::MAX_SLOTS * 32 * 8;
 }
 
 cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st) {

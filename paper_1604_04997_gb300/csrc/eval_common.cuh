@@ -35,20 +35,19 @@ __device__ __forceinline__ int64_t ld64(const uint32_t *p) {
 }
 
 // Evaluate table T at point n (int32, already known to lie in T's box) for the
-// calling thread.  vals: this thread's value slots (int32, stride vs); prods: its
-// product slots (int64, stride ps), both in shared memory.  emit(col, value) is
-// called once per non-empty column of the selected piece, post(col, value) once
-// per post-op.  Returns false on a malformed table.
+// calling thread.  slots: this thread's pmt::MAX_SLOTS int64 slots (stride ss, shared
+// memory).  emit(col, value) is called once per non-empty column of the selected
+// piece, post(col, value) once per post-op.  Returns false on a malformed table.
 template <class Emit, class Post>
-__device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const int32_t *n, int32_t *vals, int vs,
-                                           int64_t *prods, int ps, Emit &&emit, Post &&post) {
+__device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const int32_t *n, int64_t *slots, int ss,
+                                           Emit &&emit, Post &&post) {
   const int P = (int)T[pmt::H_NPARAMS];
   const int A = (int)T[pmt::H_NATOMS];
   const int NC = (int)T[pmt::H_NCONDS];
   if (P > 4 || P + A > pmt::MAX_VALUES || NC > pmt::MAX_CONDS) return false;
 #pragma unroll
   for (int p = 0; p < 4; p++)
-    if (p < P) vals[p * vs] = n[p];
+    if (p < P) slots[p * ss] = n[p];
   const uint32_t *at = T + T[pmt::H_OFF_ATOMS];
   for (int a = 0; a < A; a++, at += pmt::ATOM_WORDS) {
     const uint4 q0 = *(const uint4 *)at, q1 = *(const uint4 *)(at + 4);
@@ -57,14 +56,14 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
     if (P > 1) num += (int32_t)q0.y * n[1];
     if (P > 2) num += (int32_t)q0.z * n[2];
     if (P > 3) num += (int32_t)q0.w * n[3];
-    vals[(P + a) * vs] = floor_div(num, q1.y, q1.z, (q1.w >> 8) & 0xFF, (q1.w >> 16) & 1);
+    slots[(P + a) * ss] = floor_div(num, q1.y, q1.z, (q1.w >> 8) & 0xFF, (q1.w >> 16) & 1);
   }
   uint32_t bits = 0;
   const uint32_t *cd = T + T[pmt::H_OFF_CONDS];
   for (int c = 0; c < NC; c++) {
-    int nt = (int)cd[0];
+    const int nt = (int)cd[0];
     int64_t s = ld64(cd + 1);
-    for (int t = 0; t < nt; t++) s += (int64_t)(int32_t)cd[4 + 2 * t] * (int64_t)vals[cd[3 + 2 * t] * vs];
+    for (int t = 0; t < nt; t++) s += (int64_t)(int32_t)cd[4 + 2 * t] * slots[(cd[3 + 2 * t] & 31) * ss];
     bits |= (uint32_t)(s >= 0) << c;
     cd += 3 + 2 * nt;
   }
@@ -72,29 +71,25 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
   const uint32_t piece = (lut[bits >> 2] >> (8 * (bits & 3))) & 0xFF;
   if (piece >= T[pmt::H_NPIECES]) return false;
   const uint4 pc = *(const uint4 *)(T + T[pmt::H_OFF_PIECES] + 4 * piece);
-  if (pc.y > (uint32_t)pmt::MAX_PRODS) return false;
+  if (P + A + pc.y > (uint32_t)pmt::MAX_PRODS) return false;
   const uint32_t *pr = T + T[pmt::H_OFF_PRODS] + pc.x;
-  for (uint32_t j = 0; j < pc.y; j++) {
+  int64_t *dst = slots + (P + A) * ss;
+  for (uint32_t j = 0; j < pc.y; j++, dst += ss) {
     const uint32_t w = pr[j];
-    const uint32_t src = w & 0xFF;
-    const int64_t v = (int64_t)vals[((w >> 8) & 0xFF) * vs];
-    prods[j * ps] = src == 0xFF ? v : (int64_t)((uint64_t)prods[src * ps] * (uint64_t)v);
+    *dst = (int64_t)((uint64_t)slots[(w & 31) * ss] * (uint64_t)slots[((w >> 8) & 31) * ss]);
   }
   const uint4 *en = (const uint4 *)(T + T[pmt::H_OFF_ENTRIES]) + pc.z;
-  int64_t h0 = 0, h1 = 0, h2 = 0, h3 = 0;
   uint64_t acc = 0;
   for (uint32_t e = 0; e < pc.w; e++) {
     const uint4 E = en[e];
-    const uint32_t p = (E.z >> 8) & 0xFF;
+    const uint32_t sl = (E.z >> 8) & 0xFF;
     const uint64_t coef = (uint64_t)E.x | ((uint64_t)E.y << 32);
-    acc += p == 0xFF ? coef : coef * (uint64_t)prods[p * ps];
+    const uint64_t x = (uint64_t)slots[(sl & 31) * ss];  // slot 31 is read (and ignored) for the constant
+    acc += sl == pmt::CONST_SLOT ? coef : coef * x;
     if (E.z & pmt::ENTRY_LAST) {
       const int64_t val = (int64_t)acc;
       const uint32_t hold = (E.z >> 16) & 0xF;
-      if (hold == 1) h0 = val;
-      else if (hold == 2) h1 = val;
-      else if (hold == 3) h2 = val;
-      else if (hold == 4) h3 = val;
+      if (hold) slots[(pmt::HOLD_SLOT + hold - 1) * ss] = val;
       emit((int)(E.z & 0xFF), val);
       acc = 0;
     }
@@ -102,10 +97,9 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
   const uint32_t npost = T[pmt::H_NPOST];
   const uint32_t *po = T + T[pmt::H_OFF_POST];
   for (uint32_t q = 0; q < npost; q++) {
-    uint32_t w = po[q];
-    uint32_t a = (w >> 8) & 0xFF, b = (w >> 16) & 0xFF;
-    int64_t va = a == 0 ? h0 : a == 1 ? h1 : a == 2 ? h2 : h3;
-    int64_t vb = b == 0 ? h0 : b == 1 ? h1 : b == 2 ? h2 : h3;
+    const uint32_t w = po[q];
+    const int64_t va = slots[(pmt::HOLD_SLOT + ((w >> 8) & 3)) * ss];
+    const int64_t vb = slots[(pmt::HOLD_SLOT + ((w >> 16) & 3)) * ss];
     post((int)(w & 0xFF), va < vb ? va : vb);
   }
   return true;

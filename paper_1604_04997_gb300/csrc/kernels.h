@@ -20,6 +20,7 @@ struct K2Args {
   const int32_t *var_off;      // [n_templates+1] CSR into tab_off
   const int32_t *tmpl_nparams; // [n_templates]
   const int32_t *tmpl_slices;  // [n_templates] variant slices S per point chunk (<= K2_MAX_SLICES)
+  const int4 *tmpl_box;        // [n_templates][2] parameter box (lo, hi) shared by the template's tables
   const int4 *chunks;          // [n_chunks] (template, first point, point count <= 32, first partial slot)
   const int4 *units;           // [n_units] (chunk, slice, first variant, end variant), schedule order
   int n_units;
@@ -36,6 +37,7 @@ struct K2Args {
 };
 cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st);
 int k2_max_blocks_per_sm(int nw);
+int k2_table_words();
 
 // predict.cu
 cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, int M, int precision, double *T,

@@ -76,6 +76,7 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   std::vector<int64_t> off(nv);
   std::vector<int32_t> nparams(T, 0);
   std::vector<double> tw(T, 0);
+  std::vector<int4> box(2 * T, make_int4(0, 0, 0, 0));
   for (int t = 0; t < T; t++) {
     for (int v = var_off[t]; v < var_off[t + 1]; v++) {
       int id = tables[v];
@@ -85,8 +86,16 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
       if (v == var_off[t]) nparams[t] = (int)w[pmt::H_NPARAMS];
       else if (nparams[t] != (int)w[pmt::H_NPARAMS])
         return pm_set_error(PM_ERR_INVALID_ARG, "variants of one template differ in parameter count");
-      if ((int)(w[pmt::H_NPARAMS] + w[pmt::H_NATOMS]) > 16)
-        return pm_set_error(PM_ERR_UNSUPPORTED, "fused ranking supports tables with at most 16 values");
+      if ((int)w[pmt::H_WORDS] > pmd::k2_table_words())
+        return pm_set_error(PM_ERR_UNSUPPORTED, "fused ranking needs tables of at most " +
+                                                    std::to_string(pmd::k2_table_words() * 4) + " bytes");
+      int4 lo = make_int4((int)w[pmt::H_BOX_LO], (int)w[pmt::H_BOX_LO + 1], (int)w[pmt::H_BOX_LO + 2],
+                          (int)w[pmt::H_BOX_LO + 3]);
+      int4 hi = make_int4((int)w[pmt::H_BOX_HI], (int)w[pmt::H_BOX_HI + 1], (int)w[pmt::H_BOX_HI + 2],
+                          (int)w[pmt::H_BOX_HI + 3]);
+      if (v == var_off[t]) { box[2 * t] = lo; box[2 * t + 1] = hi; }
+      else if (std::memcmp(&box[2 * t], &lo, sizeof lo) || std::memcmp(&box[2 * t + 1], &hi, sizeof hi))
+        return pm_set_error(PM_ERR_UNSUPPORTED, "variants of one template must share one parameter box");
       off[v] = (int64_t)((uint64_t)c->dev_off[id] | ((uint64_t)w[pmt::H_WORDS] << 40));
       tw[t] += table_work(w);
     }
@@ -144,6 +153,8 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   p->d_nparams = (const int32_t *)d;
   if ((s = alloc(slices.data(), sizeof(int32_t) * T, &d))) return s;
   p->d_slices = (const int32_t *)d;
+  if ((s = alloc(box.data(), sizeof(int4) * box.size(), &d))) return s;
+  p->d_box = (const int4 *)d;
   if ((s = alloc(chunks.data(), sizeof(int4) * chunks.size(), &d))) return s;
   p->d_chunks = (const int4 *)d;
   if ((s = alloc(hu.data(), sizeof(int4) * hu.size(), &d))) return s;
@@ -178,6 +189,7 @@ static pm_status launch_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double 
   a.var_off = p->d_var_off;
   a.tmpl_nparams = p->d_nparams;
   a.tmpl_slices = p->d_slices;
+  a.tmpl_box = p->d_box;
   a.chunks = p->d_chunks;
   a.units = p->d_units;
   a.n_units = p->n_units;

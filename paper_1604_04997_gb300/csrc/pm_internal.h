@@ -18,6 +18,7 @@ struct Plan {
   const int32_t *d_var_off = nullptr;
   const int32_t *d_nparams = nullptr;
   const int32_t *d_slices = nullptr;
+  const int4 *d_box = nullptr;              // [T][2] parameter box per template
   const int4 *d_chunks = nullptr;
   const int4 *d_units = nullptr;
   int *d_counter = nullptr;

@@ -7,8 +7,8 @@
 //      values v[P..P+A) = atoms floor((a . n + b) / c), c >= 2;
 //   2. bits: condition j holds iff const_j + sum_t coef_jt * v[idx_jt] >= 0;
 //   3. piece = lut[bits];
-//   4. the piece's products (distinct monomials prod v[f]) are formed once, then
-//      each column value = sum of integer coef * product over its entries (exact int64);
+//   4. the piece's products (monomials of degree >= 2) are formed once, then each
+//      column value = sum of integer coef * (value or product) over its entries (exact int64);
 //   5. post-ops: column = min(held value A, held value B)   (min(loads, stores)).
 // Columns that no segment names are zero.  Hidden columns (index >= k) only feed
 // post-ops.
@@ -32,7 +32,12 @@ enum Header {
   HEADER_WORDS = 28
 };
 
-constexpr int MAX_PRODS = 16;  // products per piece
+// Per-lane evaluation slots (int64): values 0..V-1 (parameters, then atoms), the
+// piece's products V..V+J-1, and four slots that hold post-op inputs.
+constexpr int MAX_SLOTS = 32;
+constexpr int HOLD_SLOT = 27;          // 27..30
+constexpr int MAX_PRODS = HOLD_SLOT;   // V + J <= 27
+constexpr uint32_t CONST_SLOT = 0xFF;  // "the constant 1" in entries
 
 // Atom: 8 words  a0 a1 a2 a3 b c magic packed
 //   packed: bits 0..7 shift1, 8..15 shift2, bit 16: numerator may be negative
@@ -40,12 +45,11 @@ constexpr int ATOM_WORDS = 8;
 // Condition: [n_terms, const_lo, const_hi, (idx, coef) * n_terms]
 // LUT: 2^n_conds bytes (piece ids), packed 4 per word.
 // Piece: 4 words [prod_begin, n_prods, entry_begin, n_entries]
-// Product: 1 word [src | value << 8]; product_j = (src == 0xFF ? 1 : product_src) * v[value],
-//   src < j, so products are computed in order (the distinct monomials of the piece
-//   and the prefixes they are built from).
+// Product: 1 word [a | b << 8]: slot V+j = slot a * slot b, with a, b < V+j (the
+//   monomials of degree >= 2 of the piece and the prefixes they are built from).
 // Entry: 4 words [coef_lo, coef_hi, packed, 0]; entries are sorted by column and
-//   column value = sum of coef * product over its entries (prod 0xFF = constant 1).
-//   packed: col (8) | prod << 8 | (hold+1) << 16 (4 bits) | last-of-column << 20
+//   column value = sum of coef * slot over its entries (slot 0xFF = the constant 1).
+//   packed: col (8) | slot << 8 | (hold+1) << 16 (4 bits) | last-of-column << 20
 constexpr int ENTRY_WORDS = 4;
 constexpr uint32_t ENTRY_LAST = 1u << 20;
 // Post-op: 1 word [out_col | holdA << 8 | holdB << 16]

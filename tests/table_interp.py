@@ -76,12 +76,13 @@ class Table:
         assert piece < w[H_NPIECES]
         pb = w[H_OFF_PIECES] + 4 * piece
         p0, n_prod, e0, n_ent = w[pb:pb + 4]
-        prods = []
+        slots = list(vals) + [None] * (32 - len(vals))
+        V = len(vals)
         for j in range(n_prod):
             x = w[w[H_OFF_PRODS] + p0 + j]
-            src, v = x & 0xFF, (x >> 8) & 0xFF
-            assert src == 0xFF or src < j
-            prods.append((1 if src == 0xFF else prods[src]) * vals[v])
+            a, b = x & 0xFF, (x >> 8) & 0xFF
+            assert a < V + j and b < V + j
+            slots[V + j] = slots[a] * slots[b]
         cols = [0] * (self.k + self.hidden)
         hold = [0, 0, 0, 0]
         acc = 0
@@ -89,8 +90,8 @@ class Table:
             eo = w[H_OFF_ENTRIES] + 4 * (e0 + e)
             coef = _s64(w[eo], w[eo + 1])
             pk = w[eo + 2]
-            pr = (pk >> 8) & 0xFF
-            acc += coef * (1 if pr == 0xFF else prods[pr])
+            sl = (pk >> 8) & 0xFF
+            acc += coef * (1 if sl == 0xFF else slots[sl])
             if pk & (1 << 20):
                 col, h = pk & 0xFF, (pk >> 16) & 0xF
                 cols[col] = acc
