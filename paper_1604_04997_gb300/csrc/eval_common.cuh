@@ -46,8 +46,10 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
   const int NC = (int)T[pmt::H_NCONDS];
   if (P > 4 || P + A > pmt::MAX_VALUES || NC > pmt::MAX_CONDS) return false;
 #pragma unroll
-  for (int p = 0; p < 4; p++)
+  for (int p = 0; p < 4; p++) {
     if (p < P) slots[p * ss] = n[p];
+    slots[(pmt::HOLD_SLOT + p) * ss] = 0;  // post-op inputs a piece does not produce are zero
+  }
   const uint32_t *at = T + T[pmt::H_OFF_ATOMS];
   for (int a = 0; a < A; a++, at += pmt::ATOM_WORDS) {
     const uint4 q0 = *(const uint4 *)at, q1 = *(const uint4 *)(at + 4);
