@@ -1357,7 +1357,7 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
       ent.back()[2] |= pmt::ENTRY_LAST;
       (void)first;
     }
-    if (V + (int)plist.size() > pmt::MAX_PRODS) fail(E_UNSUP, "more than 27 values and products in a piece");
+    if (V + (int)plist.size() > pmt::MAX_PRODS) fail(E_UNSUP, "more than 19 values and products in a piece");
     maxprod = std::max(maxprod, (int)plist.size());
     pw.push_back((uint32_t)prods.size());
     pw.push_back((uint32_t)plist.size());

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_eval_counts(const uint32_t *__re
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *sT = (uint32_t *)smem;                                   // table, <= 16 KB
   int64_t *stage = (int64_t *)(smem + pmt::MAX_TABLE_WORDS * 4);     // [threads][K+1]
-  int64_t *slots = stage + K1_THREADS * (K + 1);                     // [32][threads]
+  int64_t *slots = stage + K1_THREADS * (K + 1);                     // [24][threads]
   const int tid = threadIdx.x;
   const uint32_t *gT = arena + tab_off[blockIdx.y];
   const int words = (int)gT[pmt::H_WORDS];
@@ -88,7 +88,7 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
 // ------------------------------------------------------------------------------------ K2
 
 constexpr int K2_TOPK = 16;
-constexpr int TB_WORDS = 704;   // per-warp staging buffer (2.75 KB), double-buffered
+constexpr int TB_WORDS = 1024;  // per-warp staging buffer (4 KB), double-buffered
 constexpr uint64_t OFF_MASK = (1ull << 40) - 1;
 
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
@@ -165,7 +165,7 @@ template <int NW>
 __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *tbuf = (uint32_t *)smem;                                  // [NW][2][TB_WORDS]
-  int64_t *slots = (int64_t *)(tbuf + NW * 2 * TB_WORDS);             // [NW][32 slots][32 lanes]
+  int64_t *slots = (int64_t *)(tbuf + NW * 2 * TB_WORDS);             // [NW][24 slots][32 lanes]
   int64_t *mk = (int64_t *)smem;                                      // merge lists [NW][16][32] (alias tbuf, slots)
   int *mi = (int *)(mk + NW * K2_TOPK * 32);
   __shared__ int64_t s_W[pmt::MAX_COLS];

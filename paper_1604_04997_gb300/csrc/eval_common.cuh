@@ -50,6 +50,7 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
     if (p < P) slots[p * ss] = n[p];
     slots[(pmt::HOLD_SLOT + p) * ss] = 0;  // post-op inputs a piece does not produce are zero
   }
+  slots[pmt::CONST_SLOT * ss] = 1;
   const uint32_t *at = T + T[pmt::H_OFF_ATOMS];
   for (int a = 0; a < A; a++, at += pmt::ATOM_WORDS) {
     const uint4 q0 = *(const uint4 *)at, q1 = *(const uint4 *)(at + 4);
@@ -65,7 +66,7 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
   for (int c = 0; c < NC; c++) {
     const int nt = (int)cd[0];
     int64_t s = ld64(cd + 1);
-    for (int t = 0; t < nt; t++) s += (int64_t)(int32_t)cd[4 + 2 * t] * slots[(cd[3 + 2 * t] & 31) * ss];
+    for (int t = 0; t < nt; t++) s += (int64_t)(int32_t)cd[4 + 2 * t] * slots[min(cd[3 + 2 * t], (uint32_t)pmt::MAX_SLOTS - 1) * ss];
     bits |= (uint32_t)(s >= 0) << c;
     cd += 3 + 2 * nt;
   }
@@ -78,7 +79,8 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
   int64_t *dst = slots + (P + A) * ss;
   for (uint32_t j = 0; j < pc.y; j++, dst += ss) {
     const uint32_t w = pr[j];
-    *dst = (int64_t)((uint64_t)slots[(w & 31) * ss] * (uint64_t)slots[((w >> 8) & 31) * ss]);
+    *dst = (int64_t)((uint64_t)slots[min(w & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss] *
+                     (uint64_t)slots[min((w >> 8) & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
   }
   const uint4 *en = (const uint4 *)(T + T[pmt::H_OFF_ENTRIES]) + pc.z;
   uint64_t acc = 0;
@@ -86,8 +88,7 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
     const uint4 E = en[e];
     const uint32_t sl = (E.z >> 8) & 0xFF;
     const uint64_t coef = (uint64_t)E.x | ((uint64_t)E.y << 32);
-    const uint64_t x = (uint64_t)slots[(sl & 31) * ss];  // slot 31 is read (and ignored) for the constant
-    acc += sl == pmt::CONST_SLOT ? coef : coef * x;
+    acc += coef * (uint64_t)slots[min(sl, (uint32_t)pmt::MAX_SLOTS - 1) * ss];
     if (E.z & pmt::ENTRY_LAST) {
       const int64_t val = (int64_t)acc;
       const uint32_t hold = (E.z >> 16) & 0xF;

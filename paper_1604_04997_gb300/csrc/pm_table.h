@@ -33,11 +33,11 @@ enum Header {
 };
 
 // Per-lane evaluation slots (int64): values 0..V-1 (parameters, then atoms), the
-// piece's products V..V+J-1, and four slots that hold post-op inputs.
-constexpr int MAX_SLOTS = 32;
-constexpr int HOLD_SLOT = 27;          // 27..30
-constexpr int MAX_PRODS = HOLD_SLOT;   // V + J <= 27
-constexpr uint32_t CONST_SLOT = 0xFF;  // "the constant 1" in entries
+// piece's products V..V+J-1, four slots that hold post-op inputs, and the constant 1.
+constexpr int MAX_SLOTS = 24;
+constexpr int HOLD_SLOT = 19;          // 19..22
+constexpr int MAX_PRODS = HOLD_SLOT;   // V + J <= 19
+constexpr uint32_t CONST_SLOT = 23;    // always 1
 
 // Atom: 8 words  a0 a1 a2 a3 b c magic packed
 //   packed: bits 0..7 shift1, 8..15 shift2, bit 16: numerator may be negative
@@ -48,7 +48,7 @@ constexpr int ATOM_WORDS = 8;
 // Product: 1 word [a | b << 8]: slot V+j = slot a * slot b, with a, b < V+j (the
 //   monomials of degree >= 2 of the piece and the prefixes they are built from).
 // Entry: 4 words [coef_lo, coef_hi, packed, 0]; entries are sorted by column and
-//   column value = sum of coef * slot over its entries (slot 0xFF = the constant 1).
+//   column value = sum of coef * slot over its entries (slot 23 = the constant 1).
 //   packed: col (8) | slot << 8 | (hold+1) << 16 (4 bits) | last-of-column << 20
 constexpr int ENTRY_WORDS = 4;
 constexpr uint32_t ENTRY_LAST = 1u << 20;

@@ -76,7 +76,8 @@ class Table:
         assert piece < w[H_NPIECES]
         pb = w[H_OFF_PIECES] + 4 * piece
         p0, n_prod, e0, n_ent = w[pb:pb + 4]
-        slots = list(vals) + [None] * (32 - len(vals))
+        slots = list(vals) + [None] * (24 - len(vals))
+        slots[23] = 1
         V = len(vals)
         for j in range(n_prod):
             x = w[w[H_OFF_PRODS] + p0 + j]
@@ -91,7 +92,8 @@ class Table:
             coef = _s64(w[eo], w[eo + 1])
             pk = w[eo + 2]
             sl = (pk >> 8) & 0xFF
-            acc += coef * (1 if sl == 0xFF else slots[sl])
+            assert sl < V + n_prod or sl == 23
+            acc += coef * slots[sl]
             if pk & (1 << 20):
                 col, h = pk & 0xFF, (pk >> 16) & 0xF
                 cols[col] = acc
