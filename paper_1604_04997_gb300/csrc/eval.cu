@@ -152,29 +152,33 @@ __device__ __forceinline__ void merge_lists(const int64_t *ks, const int *is, in
   }
 }
 
-// Warp w of a CTA evaluates variants vb+w, vb+w+NW, ... < ve of the unit's template
-// for the unit's points (one point per lane; the table is shared by the warp and read
-// as broadcasts from shared memory).  Counts are exact; the predicted time is the
-// exact fixed-point sum S = sum_i count_i W_i (128-bit, integer pipes only), ranked by
-// a monotone 64-bit key.  Each lane keeps its point's 16 best (key, variant) pairs in
-// registers; a per-point threshold shared by the CTA's warps rejects most candidates.
-// The CTA merges its warps' lists; a point chunk split into S variant slices is
-// finished by the last of its S units (partial lists in a scratch buffer, a fence and
-// an atomic counter; no waiting).
+constexpr int K2_BUF = 8;  // buffered insertion candidates per lane
+
+// One CTA takes a work unit (a chunk of NW*32 points of one template, a slice of its
+// variants).  Each lane owns one point; all warps walk the slice's variants in order,
+// the CTA staging each table once into shared memory (double-buffered cp.async, one
+// barrier per variant) and reading it as warp-wide broadcasts.  Counts are exact; the
+// predicted time is the exact fixed-point sum S = sum_i count_i W_i (128-bit, integer
+// pipes only), ranked by a monotone 64-bit key.  Each lane keeps its point's 16 best
+// (key, variant) pairs in registers; candidates that beat the lane's 16th key are
+// buffered and inserted together when some lane's buffer fills, so the divergent
+// insertion path runs rarely.  A chunk split into S variant slices is finished by the
+// last of its S units (partial lists in a scratch buffer, a fence and an atomic
+// counter; no waiting).
 template <int NW>
 __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t *tbuf = (uint32_t *)smem;                                  // [NW][2][TB_WORDS]
-  int64_t *slots = (int64_t *)(tbuf + NW * 2 * TB_WORDS);             // [NW][24 slots][32 lanes]
-  int64_t *mk = (int64_t *)smem;                                      // merge lists [NW][16][32] (alias tbuf, slots)
-  int *mi = (int *)(mk + NW * K2_TOPK * 32);
+  uint32_t *tbuf = (uint32_t *)smem;                                  // [2][TB_WORDS]
+  int64_t *slots = (int64_t *)(tbuf + 2 * TB_WORDS);                  // [NW][24 slots][32 lanes]
+  int64_t *bk = slots + NW * pmt::MAX_SLOTS * 32;                     // [NW][K2_BUF][32] candidate keys
+  int *bi = (int *)(bk + NW * K2_BUF * 32);                           // [NW][K2_BUF][32] candidate variants
   __shared__ int64_t s_W[pmt::MAX_COLS];
-  __shared__ unsigned long long s_thr[32];
   __shared__ int s_E, s_unit;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t *mybuf = tbuf + warp * 2 * TB_WORDS;
   int64_t *myslots = slots + warp * pmt::MAX_SLOTS * 32 + lane;
+  int64_t *mybk = bk + warp * K2_BUF * 32 + lane;
+  int *mybi = bi + warp * K2_BUF * 32 + lane;
 
   if (threadIdx.x == 0) {
     const int E = weight_exponent(a.w, 32);
@@ -185,7 +189,6 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 
   while (true) {
     if (threadIdx.x == 0) s_unit = atomicAdd(a.unit_counter, 1);
-    if (threadIdx.x < 32) s_thr[threadIdx.x] = (unsigned long long)INT64_MAX;
     __syncthreads();
     const int u = s_unit;
     __syncthreads();
@@ -194,12 +197,12 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     const int4 C = a.chunks[U.x];       // template, first point, point count, first partial slot
     const int t = C.x;
     const int S = a.tmpl_slices[t];
-    const int64_t p = (int64_t)C.y + lane;
     const int P = a.tmpl_nparams[t];
-    // every table of a plan's template shares one parameter box: check the point once
+    const int pl = warp * 32 + lane;    // this lane's point within the chunk
+    const int64_t p = (int64_t)C.y + pl;
+    const bool live = pl < C.z;         // the lane has a point
+    bool valid = live;                  // ... inside the box (else its ranking stays empty)
     int32_t n[4] = {0, 0, 0, 0};
-    const bool live = lane < C.z;   // the lane has a point
-    bool valid = live;              // ... inside the box (else its ranking stays empty)
     if (live) {
       const int64_t *src = a.points + p * 4;
       const int4 lo = a.tmpl_box[2 * t], hi = a.tmpl_box[2 * t + 1];
@@ -217,88 +220,79 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     }
     TopK tk;
     tk.init();
+    int64_t thr = INT64_MAX;   // the list's 16th key
+    int nbuf = 0;
+    auto flush = [&]() {
+      for (int b = 0; b < nbuf; b++) tk.insert(mybk[b * 32], mybi[b * 32]);
+      nbuf = 0;
+      thr = tk.k[K2_TOPK - 1];
+    };
     const int v0 = a.var_off[t];
-    const int ve = U.w;
-    int v = U.z + warp;
-    auto stage = [&](uint64_t po, int slot) {
-      const int words = min((int)(po >> 40), TB_WORDS);
-      const uint32_t *g = a.arena + (po & OFF_MASK);
-      for (int i = lane; i < words / 4; i += 32) cp_async16(mybuf + slot * TB_WORDS + 4 * i, g + 4 * i);
+    const int vb = U.z, ve = U.w;
+    auto stage = [&](int vv, int buf) {
+      if (vv < ve) {
+        const uint64_t po = a.tab_off[vv];
+        const int words = min((int)(po >> 40), TB_WORDS);
+        const uint32_t *g = a.arena + (po & OFF_MASK);
+        for (int i = threadIdx.x; i < words / 4; i += NW * 32) cp_async16(tbuf + buf * TB_WORDS + 4 * i, g + 4 * i);
+      }
       cp_async_commit();
     };
-    uint64_t po_cur = v < ve ? a.tab_off[v] : 0;
-    uint64_t po_nxt = v + NW < ve ? a.tab_off[v + NW] : 0;
-    stage(po_cur, 0);
-    int slot = 0;
-    for (; v < ve; v += NW) {
-      const uint64_t po_nn = v + 2 * NW < ve ? a.tab_off[v + 2 * NW] : 0;  // used next iteration
-      stage(po_nxt, slot ^ 1);
-      cp_async_wait1();
-      __syncwarp();
-      const uint32_t *T = mybuf + slot * TB_WORDS;   // the plan admits only tables that fit
+    stage(vb, 0);
+    for (int v = vb; v < ve; v++) {
+      const int buf = (v - vb) & 1;
+      cp_async_wait0();
+      __syncthreads();                  // table v visible; table v-1 no longer read by any warp
+      stage(v + 1, buf ^ 1);            // overlaps with the evaluation of table v
       if (valid) {
         Acc128 acc;
         acc.zero();
         const bool ok = eval_table(
-            T, n, myslots, 32,
+            tbuf + buf * TB_WORDS, n, myslots, 32,
             [&](int col, int64_t val) { if (col < 32) acc.add_mul((uint64_t)val, s_W[col]); },
             [&](int col, int64_t val) { acc.add_mul((uint64_t)val, s_W[col]); });
         if (!ok) atomicOr(a.status, ST_BAD_TABLE);
         const int64_t key = acc_key(acc);
-        if (key < tk.k[K2_TOPK - 1] && key <= (int64_t)s_thr[lane]) {
-          tk.insert(key, v - v0);
-          if (tk.k[K2_TOPK - 1] != INT64_MAX) atomicMin(&s_thr[lane], (unsigned long long)tk.k[K2_TOPK - 1]);
+        if (key < thr) {                // strict: an equal key of a later variant ranks after
+          mybk[nbuf * 32] = key;
+          mybi[nbuf * 32] = v - v0;
+          nbuf++;
         }
       }
-      __syncwarp();
-      po_cur = po_nxt;
-      po_nxt = po_nn;
-      slot ^= 1;
+      if (__any_sync(0xffffffffu, nbuf == K2_BUF)) flush();
     }
+    flush();
     cp_async_wait0();
-    __syncthreads();  // table and slot buffers are reused as merge buffers below
+    bool write_out = S == 1;
+    if (S > 1) {
+      // publish this slice's lists, then the last slice of the chunk merges all of them
+      const int64_t slot0 = (int64_t)(C.w + U.y) * K2_TOPK * (NW * 32) + pl;
 #pragma unroll
-    for (int q = 0; q < K2_TOPK; q++) {
-      const int o = (warp * K2_TOPK + q) * 32 + lane;
-      mk[o] = tk.k[q];
-      mi[o] = tk.id[q];
-    }
-    __syncthreads();
-    if (warp == 0) {
-      TopK m;
-      merge_lists<NW, false>(mk + lane, mi + lane, NW, K2_TOPK * 32, 32, m);
-      bool write_out = S == 1;
-      if (S > 1) {
-        // publish this slice's list, then the last slice of the chunk merges all of them
-        const int64_t slot0 = (int64_t)(C.w + U.y) * K2_TOPK * 32 + lane;
-#pragma unroll
-        for (int q = 0; q < K2_TOPK; q++) {
-          a.part_k[slot0 + q * 32] = m.k[q];
-          a.part_i[slot0 + q * 32] = m.id[q];
-        }
-        __threadfence();
-        __syncwarp();
-        int last = 0;
-        if (lane == 0) last = atomicAdd(a.chunk_count + U.x, 1) == S - 1;
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-          __threadfence();
-          const int64_t b = (int64_t)C.w * K2_TOPK * 32 + lane;
-          merge_lists<K2_MAX_SLICES, true>(a.part_k + b, a.part_i + b, S, K2_TOPK * 32, 32, m);
-          write_out = true;
-        }
+      for (int q = 0; q < K2_TOPK; q++) {
+        a.part_k[slot0 + q * (NW * 32)] = tk.k[q];
+        a.part_i[slot0 + q * (NW * 32)] = tk.id[q];
       }
-      if (write_out && live) {
-        int32_t *oi = a.top_idx + p * a.topk;
-        double *ot = a.top_t + p * a.topk;
-        const int E = s_E;
+      __threadfence();
+      __syncthreads();
+      if (threadIdx.x == 0) s_unit = atomicAdd(a.chunk_count + U.x, 1) == S - 1;
+      __syncthreads();
+      if (s_unit) {
+        __threadfence();
+        const int64_t b = (int64_t)C.w * K2_TOPK * (NW * 32) + pl;
+        merge_lists<K2_MAX_SLICES, true>(a.part_k + b, a.part_i + b, S, K2_TOPK * (NW * 32), NW * 32, tk);
+        write_out = true;
+      }
+    }
+    if (write_out && live) {
+      int32_t *oi = a.top_idx + p * a.topk;
+      double *ot = a.top_t + p * a.topk;
+      const int E = s_E;
 #pragma unroll
-        for (int q = 0; q < K2_TOPK; q++) {
-          if (q < a.topk) {
-            const bool real = m.id[q] != 0x7fffffff;
-            oi[q] = real ? m.id[q] : -1;
-            ot[q] = real ? key_value(m.k[q], E) : __longlong_as_double(0x7ff0000000000000ll);
-          }
+      for (int q = 0; q < K2_TOPK; q++) {
+        if (q < a.topk) {
+          const bool real = tk.id[q] != 0x7fffffff;
+          oi[q] = real ? tk.id[q] : -1;
+          ot[q] = real ? key_value(tk.k[q], E) : __longlong_as_double(0x7ff0000000000000ll);
         }
       }
     }
@@ -309,10 +303,10 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 int k2_table_words() { return TB_WORDS; }
 
 size_t k2_smem_bytes(int nw) {
-  static_assert(K2_TOPK * 32 * 12 <= 2 * TB_WORDS * 4 + pmt::MAX_SLOTS * 32 * 8,
-                "merge lists must fit in the table and slot buffers");
-  return (size_t)nw * 2 * TB_WORDS * 4 + (size_t)nw * pmt::MAX_SLOTS * 32 * 8;
+  return (size_t)2 * TB_WORDS * 4 + (size_t)nw * pmt::MAX_SLOTS * 32 * 8 + (size_t)nw * K2_BUF * 32 * 12;
 }
+
+int k2_points_per_cta(int nw) { return nw * 32; }
 
 cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st) {
   size_t sm = k2_smem_bytes(nw);

@@ -21,13 +21,13 @@ struct K2Args {
   const int32_t *tmpl_nparams; // [n_templates]
   const int32_t *tmpl_slices;  // [n_templates] variant slices S per point chunk (<= K2_MAX_SLICES)
   const int4 *tmpl_box;        // [n_templates][2] parameter box (lo, hi) shared by the template's tables
-  const int4 *chunks;          // [n_chunks] (template, first point, point count <= 32, first partial slot)
+  const int4 *chunks;          // [n_chunks] (template, first point, point count <= 256, first partial slot)
   const int4 *units;           // [n_units] (chunk, slice, first variant, end variant), schedule order
   int n_units;
   int *unit_counter;           // reset to 0 before each launch
   int *chunk_count;            // [n_chunks] slices finished, reset to 0 before each launch
-  int64_t *part_k;             // [slots][16][32] partial lists (ranking keys) of chunks with S > 1
-  int *part_i;                 // [slots][16][32] their variant indices
+  int64_t *part_k;             // [slots][16][256] partial lists (ranking keys) of chunks with S > 1
+  int *part_i;                 // [slots][16][256] their variant indices
   const int64_t *points;       // [total][4]
   const double *w;             // [32]
   int topk;
@@ -38,6 +38,7 @@ struct K2Args {
 cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st);
 int k2_max_blocks_per_sm(int nw);
 int k2_table_words();
+int k2_points_per_cta(int nw);
 
 // predict.cu
 cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, int M, int precision, double *T,

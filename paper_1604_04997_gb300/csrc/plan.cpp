@@ -23,8 +23,9 @@
     if (e__ != cudaSuccess) return pm_set_error(PM_ERR_CUDA, std::string(#x) + ": " + cudaGetErrorString(e__)); \
   } while (0)
 
-static constexpr int UNIT_POINTS = 32;
-static constexpr int SLICE_VARIANTS = 400;
+static constexpr int K2_WARPS = 4;                  // warps per CTA of the fused kernel
+static constexpr int UNIT_POINTS = 32 * K2_WARPS;   // one point per lane
+static constexpr int SLICE_VARIANTS = 128;
 
 // Algorithmic lane operations of one evaluation of a table (average over its pieces):
 //   atom floor((a.n + b)/c):  P multiply-adds, 1 add, 5 for the magic division   P + 6
@@ -161,7 +162,7 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   p->d_units = (const int4 *)d;
   if ((s = alloc(nullptr, sizeof(int) * (chunks.size() + 1), &d))) return s;
   p->d_counter = (int *)d;  // [0] unit counter, [1..] per-chunk slice counters
-  const size_t part = (size_t)slots * 16 * 32;
+  const size_t part = (size_t)slots * 16 * UNIT_POINTS;
   if ((s = alloc(nullptr, part * 8, &d))) return s;
   p->d_part_k = (int64_t *)d;
   if ((s = alloc(nullptr, part * 4, &d))) return s;
@@ -172,7 +173,7 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   p->total_points = np;
   p->total_evals = evals;
   p->work_per_eval = evals ? total_work / (double)evals : 0;
-  p->nw = 8;
+  p->nw = K2_WARPS;
   int bps = pmd::k2_max_blocks_per_sm(p->nw);
   p->grid = std::max(1, c->n_sms * std::max(1, bps));
   c->plans[key] = p;
@@ -269,7 +270,7 @@ static pm_status tune_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w
   CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int bnw = p->nw, bgrid = p->grid, bbps = 1;
-  for (int cand_nw : {4, 8}) {
+  for (int cand_nw : {K2_WARPS}) {
     int mx = std::max(1, pmd::k2_max_blocks_per_sm(cand_nw));
     for (int cand_bps = 1; cand_bps <= mx; cand_bps++) {
       int grid = c->n_sms * cand_bps;
