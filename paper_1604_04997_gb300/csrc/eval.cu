@@ -172,7 +172,8 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   int64_t *slots = (int64_t *)(tbuf + 2 * TB_WORDS);                  // [NW][24 slots][32 lanes]
   int64_t *bk = slots + NW * pmt::MAX_SLOTS * 32;                     // [NW][K2_BUF][32] candidate keys
   int *bi = (int *)(bk + NW * K2_BUF * 32);                           // [NW][K2_BUF][32] candidate variants
-  __shared__ int64_t s_W[pmt::MAX_COLS];
+  __shared__ uint32_t s_w0[pmt::MAX_COLS];
+  __shared__ int32_t s_w1[pmt::MAX_COLS];
   __shared__ int s_E, s_unit;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -182,7 +183,11 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 
   if (threadIdx.x == 0) {
     const int E = weight_exponent(a.w, 32);
-    for (int c = 0; c < pmt::MAX_COLS; c++) s_W[c] = c < 32 ? llrint(ldexp(a.w[c], E)) : 0;
+    for (int c = 0; c < pmt::MAX_COLS; c++) {
+      const int64_t W = c < 32 ? llrint(ldexp(a.w[c], E)) : 0;   // |W| < 2^56
+      s_w0[c] = (uint32_t)(W & 0x0FFFFFFF);
+      s_w1[c] = (int32_t)(W >> 28);
+    }
     s_E = E;
   }
   __syncthreads();
@@ -220,12 +225,15 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     }
     TopK tk;
     tk.init();
-    int64_t thr = INT64_MAX;   // the list's 16th key
+    int64_t thr = INT64_MAX;                     // the list's 16th key
+    Acc128 thr_s = {~0ull, (uint64_t)INT64_MAX};  // S < thr_s  <=>  key(S) < thr (thr > 0)
     int nbuf = 0;
     auto flush = [&]() {
       for (int b = 0; b < nbuf; b++) tk.insert(mybk[b * 32], mybi[b * 32]);
       nbuf = 0;
       thr = tk.k[K2_TOPK - 1];
+      if (thr == INT64_MAX) { thr_s.lo = ~0ull; thr_s.hi = (uint64_t)INT64_MAX; }
+      else if (thr > 0) thr_s = key_floor(thr);
     };
     const int v0 = a.var_off[t];
     const int vb = U.z, ve = U.w;
@@ -245,16 +253,18 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       __syncthreads();                  // table v visible; table v-1 no longer read by any warp
       stage(v + 1, buf ^ 1);            // overlaps with the evaluation of table v
       if (valid) {
-        Acc128 acc;
-        acc.zero();
+        LimbAcc la;
+        la.zero();
         const bool ok = eval_table(
             tbuf + buf * TB_WORDS, n, myslots, 32,
-            [&](int col, int64_t val) { if (col < 32) acc.add_mul((uint64_t)val, s_W[col]); },
-            [&](int col, int64_t val) { acc.add_mul((uint64_t)val, s_W[col]); });
+            [&](int col, int64_t val) { if (col < 32) la.add((uint64_t)val, s_w0[col], s_w1[col]); },
+            [&](int col, int64_t val) { la.add((uint64_t)val, s_w0[col], s_w1[col]); });
         if (!ok) atomicOr(a.status, ST_BAD_TABLE);
-        const int64_t key = acc_key(acc);
-        if (key < thr) {                // strict: an equal key of a later variant ranks after
-          mybk[nbuf * 32] = key;
+        const Acc128 S = la.sum();
+        // strict: an equal key of a later variant ranks after the earlier one
+        const bool pass = thr > 0 ? acc_less(S, thr_s) : acc_key(S) < thr;
+        if (pass) {
+          mybk[nbuf * 32] = acc_key(S);
           mybi[nbuf * 32] = v - v0;
           nbuf++;
         }

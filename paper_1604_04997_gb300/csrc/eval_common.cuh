@@ -126,22 +126,58 @@ __device__ __forceinline__ bool point_in_box(const uint32_t *T, const int64_t *p
 }
 
 // ---- Exact fixed-point prediction on the integer pipes.
-// Weights become integers W = round(w * 2^E) (|W| < 2^58, one E per weight vector);
-// each exact count v >= 0 contributes v * W to a 128-bit accumulator, so the sum
-// S = sum_i v_i W_i is exact and T = S * 2^-E differs from sum_i v_i w_i by at most
-// 2^-(E+1) sum_i v_i, i.e. <= 2^-59 (max|w| / min|w|) of sum_i |v_i w_i|.
+// Weights become integers W = round(w * 2^E) (|W| < 2^56, one E per weight vector);
+// each exact count 0 <= v < 2^62 contributes v * W, so the sum S = sum_i v_i W_i is
+// exact and T = S * 2^-E differs from sum_i v_i w_i by at most 2^-(E+1) sum_i v_i,
+// i.e. <= 2^-57 (max|w| / min|w|) of sum_i |v_i w_i|.
+//
+// The products are formed from 28-bit limbs, v = v2 2^56 + v1 2^28 + v0 and
+// W = w1 2^28 + w0 (w1 signed), with one 32 x 32 -> 64 multiply-add per limb pair into
+// four 64-bit accumulators by power of 2^28 (each sums < 2^7 products below 2^56, so
+// none overflows); they are combined into 128 bits once per evaluation.
 struct Acc128 {
   uint64_t lo, hi;  // two's complement
   __device__ __forceinline__ void zero() { lo = hi = 0; }
-  __device__ __forceinline__ void add_mul(uint64_t v, int64_t W) {
-    const uint64_t w = (uint64_t)W;
-    const uint64_t plo = v * w;
-    const uint64_t phi = __umul64hi(v, w) - (W < 0 ? v : 0ull);
-    const uint64_t nl = lo + plo;
-    hi += phi + (nl < plo ? 1ull : 0ull);
-    lo = nl;
+};
+
+struct LimbAcc {
+  uint64_t l0;
+  int64_t l1, l2, l3;
+  __device__ __forceinline__ void zero() { l0 = 0; l1 = l2 = l3 = 0; }
+  __device__ __forceinline__ void add(uint64_t v, uint32_t w0, int32_t w1) {
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    const uint32_t v0 = lo & 0x0FFFFFFFu;
+    const uint32_t v1 = __funnelshift_r(lo, hi, 28) & 0x0FFFFFFFu;
+    const int32_t v2 = (int32_t)(hi >> 24);
+    l0 += (uint64_t)v0 * w0;
+    l1 += (int64_t)(int32_t)v0 * w1 + (int64_t)(int32_t)v1 * (int32_t)w0;
+    l2 += (int64_t)(int32_t)v1 * w1 + (int64_t)v2 * (int32_t)w0;
+    l3 += (int64_t)v2 * w1;
+  }
+  __device__ __forceinline__ Acc128 sum() const {
+    // S = l0 + l1 2^28 + l2 2^56 + l3 2^84, in 128-bit two's complement
+    Acc128 r;
+    r.lo = l0;
+    r.hi = 0;
+    auto add_shifted = [&](int64_t x, int sh) {  // r += x * 2^sh, 0 < sh < 128
+      uint64_t alo, ahi;
+      if (sh < 64) { alo = (uint64_t)x << sh; ahi = (uint64_t)(x >> (64 - sh)); }
+      else { alo = 0; ahi = (uint64_t)x << (sh - 64); }
+      const uint64_t nl = r.lo + alo;
+      r.hi += ahi + (nl < alo ? 1ull : 0ull);
+      r.lo = nl;
+    };
+    add_shifted(l1, 28);
+    add_shifted(l2, 56);
+    add_shifted(l3, 84);
+    return r;
   }
 };
+
+// signed 128-bit a < b
+__device__ __forceinline__ bool acc_less(const Acc128 &a, const Acc128 &b) {
+  return (int64_t)a.hi < (int64_t)b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
 
 // Monotone 64-bit key of a 128-bit signed value: sign, 7-bit exponent and the 56 bits
 // below the leading one (a float with a 56-bit mantissa; equal values give equal keys).
@@ -159,6 +195,25 @@ __device__ __forceinline__ int64_t acc_key(const Acc128 &a) {
   return neg ? -k : k;
 }
 
+// For a positive key k: the smallest 128-bit S with acc_key(S) >= k, so that
+// acc_key(S) < k  <=>  S < key_floor(k).  (Used to test candidates without a key.)
+__device__ __forceinline__ Acc128 key_floor(int64_t k) {
+  Acc128 r;
+  const int e = (int)(k >> 56) - 1;                 // exponent of the leading one
+  const uint64_t m = (1ull << 56) | ((uint64_t)k & ((1ull << 56) - 1));  // 57 bits
+  if (e >= 56) {
+    const int sh = e - 56;                          // 0..70
+    if (sh == 0) { r.lo = m; r.hi = 0; }
+    else if (sh < 64) { r.lo = m << sh; r.hi = m >> (64 - sh); }
+    else { r.lo = 0; r.hi = m << (sh - 64); }
+  } else {
+    const int sh = 56 - e;                          // 1..56: round the mantissa up
+    r.lo = (m + (1ull << sh) - 1) >> sh;
+    r.hi = 0;
+  }
+  return r;
+}
+
 // Inverse of acc_key times 2^-E, for output.
 __device__ __forceinline__ double key_value(int64_t k, int E) {
   if (k == 0) return 0.0;
@@ -170,13 +225,13 @@ __device__ __forceinline__ double key_value(int64_t k, int E) {
   return neg ? -v : v;
 }
 
-// Fixed-point weights: W_i = round(w_i * 2^E) with max |W_i| in [2^57, 2^58).
+// Fixed-point weights: W_i = round(w_i * 2^E) with max |W_i| in [2^55, 2^56).
 __device__ __forceinline__ int weight_exponent(const double *w, int k) {
   double mx = 0;
   for (int c = 0; c < k; c++) mx = fmax(mx, fabs(w[c]));
   int e = 0;
   if (mx > 0) frexp(mx, &e);  // mx in [2^(e-1), 2^e)
-  return 58 - e;
+  return 56 - e;
 }
 
 }  // namespace pmd
