@@ -1008,23 +1008,30 @@ static int qr_lstsq(double *A, int64_t m, int n, double *b, double *x, double *c
 int orc_fit(const int64_t *F, int64_t R, int k, const double *t, int objective,
             double *w_out, double *report) {
   if (k > 64 || R <= 0) return -1;
+  /* The matrix of the least-squares problem: each property row divided by the
+     kernel's measured time (relative objective, Sec. 4.3), or the properties
+     themselves (absolute).  Its all-zero columns are dropped; the others are scaled
+     by a power of two so that the largest entry of each lies in [1/2, 1). */
   int keep[64], nk = 0;
   double scale[64];
   for (int c = 0; c < k; c++) {
-    int64_t mx = 0;
-    for (int64_t i = 0; i < R; i++) { int64_t v = F[i * k + c] < 0 ? -F[i * k + c] : F[i * k + c]; if (v > mx) mx = v; }
+    double mx = 0;
+    for (int64_t i = 0; i < R; i++) {
+      double a = fabs((double)F[i * k + c]) / (objective == 0 ? t[i] : 1.0);
+      if (a > mx) mx = a;
+    }
     w_out[c] = 0;
-    if (!mx) continue;
+    if (!(mx > 0)) continue;
     int e;
-    frexp((double)mx, &e);
-    scale[nk] = ldexp(1.0, -e);            /* power-of-two column scaling */
+    frexp(mx, &e);
+    scale[nk] = ldexp(1.0, -e);
     keep[nk++] = c;
   }
   double *A = (double *)malloc(sizeof(double) * (size_t)R * nk);
   double *b = (double *)malloc(sizeof(double) * (size_t)R);
   for (int64_t i = 0; i < R; i++) {
     double ri = objective == 0 ? 1.0 / t[i] : 1.0;
-    for (int q = 0; q < nk; q++) A[(int64_t)q * R + i] = (double)F[i * k + keep[q]] * scale[q] * ri;
+    for (int q = 0; q < nk; q++) A[(int64_t)q * R + i] = (double)F[i * k + keep[q]] * ri * scale[q];
     b[i] = objective == 0 ? 1.0 : t[i];
   }
   double x[64], cond, res;
