@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -76,6 +77,7 @@ extern "C" void pm_destroy(pm_ctx *c) {
     cudaFree(c->d_status);
     cudaFree(c->scratch);
     cudaFreeHost(c->h_status);
+    if (c->fit_host) cudaFreeHost(c->fit_host);
   }
   delete c;
 }
@@ -91,6 +93,7 @@ extern "C" pm_status pm_sync_status(pm_ctx *c, void *stream) {
   if (s & pmd::ST_OUT_OF_BOX) return pm_set_error(PM_ERR_OUT_OF_BOX, "a parameter point lies outside its table's box");
   if (s & pmd::ST_BAD_TABLE) return pm_set_error(PM_ERR_INVALID_ARG, "malformed table reached the device");
   if (s & pmd::ST_TIMEOUT) return pm_set_error(PM_ERR_TIMEOUT, "a device wait ran out");
+  if (s & pmd::ST_BAD_INPUT) return pm_set_error(PM_ERR_INVALID_ARG, "a timing is not positive and finite");
   return PM_OK;
 }
 
@@ -268,4 +271,48 @@ extern "C" pm_status pm_eval_predict_topk(pm_ctx *c, const int32_t *tables, cons
   pm_status s = ctx_plan_k2(c, tables, var_off, n_templates, pt_off, &plan);
   if (s) return s;
   return ctx_run_k2(c, plan, d_points, d_w, topk, d_top_idx, d_top_t, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------------------------- fit (Sec. 4.3)
+
+extern "C" pm_status pm_fit_weights(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *T, int32_t M,
+                                    int32_t objective, int32_t precision, int32_t refine_steps, double *W_out,
+                                    pm_fit_report *rep, void *stream) {
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  if (R <= 0 || k <= 0 || k > 32 || M <= 0 || M > 64 || refine_steps < 0 || refine_steps > 50)
+    return pm_set_error(PM_ERR_INVALID_ARG, "need R > 0, 0 < k <= 32, 0 < M <= 64, 0 <= refine_steps <= 50");
+  if (!F || !T || !W_out || !rep) return pm_set_error(PM_ERR_INVALID_ARG, "null argument");
+  if (objective != PM_FIT_RELATIVE && objective != PM_FIT_ABSOLUTE) return pm_set_error(PM_ERR_INVALID_ARG, "objective");
+  if (precision != PM_PREC_FP64 && precision != PM_PREC_BF16X3) return pm_set_error(PM_ERR_INVALID_ARG, "precision");
+  void *scr = nullptr;
+  pm_status s = ctx_scratch(c, pmd::fit_scratch_bytes(R, k, M), &scr);
+  if (s) return s;
+  if (!c->fit_host) {
+    CU(cudaMallocHost(&c->fit_host, 64 * (16 + 8 * 4)));
+  }
+  pmd::FitHost h;
+  h.info = (int *)c->fit_host;
+  h.ratio = (double *)((char *)c->fit_host + 64 * 16);
+  h.upd = h.ratio + 64;
+  h.rr = h.upd + 64;
+  h.bb = h.rr + 64;
+  cudaStream_t st = (cudaStream_t)stream;
+  CU(pmd::launch_fit(F, R, k, T, M, objective, refine_steps, scr, W_out, &h, c->d_status, st));
+  CU(cudaStreamSynchronize(st));
+  s = pm_sync_status(c, stream);
+  if (s) return s;
+  bool deficient = false;
+  for (int m = 0; m < M; m++) {
+    pm_fit_report &r = rep[m];
+    r.rank = h.info[m * 4 + 0];
+    r.n_dropped = h.info[m * 4 + 1];
+    r.iters = refine_steps;
+    r.cond_est = h.ratio[m];
+    r.rel_resid = h.bb[m] > 0 ? std::sqrt(h.rr[m] / h.bb[m]) : 0.0;
+    r.last_update = h.upd[m];
+    r.status = h.info[m * 4 + 2] ? 1 : (refine_steps > 0 && !(r.last_update < 1e-6) ? 2 : 0);
+    deficient |= h.info[m * 4 + 2] != 0;
+  }
+  return deficient ? PM_WARN_RANK_DEFICIENT : PM_OK;
 }

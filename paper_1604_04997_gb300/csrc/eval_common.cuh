@@ -156,21 +156,13 @@ struct LimbAcc {
   }
   __device__ __forceinline__ Acc128 sum() const {
     // S = l0 + l1 2^28 + l2 2^56 + l3 2^84, in 128-bit two's complement
-    Acc128 r;
-    r.lo = l0;
-    r.hi = 0;
-    auto add_shifted = [&](int64_t x, int sh) {  // r += x * 2^sh, 0 < sh < 128
-      uint64_t alo, ahi;
-      if (sh < 64) { alo = (uint64_t)x << sh; ahi = (uint64_t)(x >> (64 - sh)); }
-      else { alo = 0; ahi = (uint64_t)x << (sh - 64); }
-      const uint64_t nl = r.lo + alo;
-      r.hi += ahi + (nl < alo ? 1ull : 0ull);
-      r.lo = nl;
-    };
-    add_shifted(l1, 28);
-    add_shifted(l2, 56);
-    add_shifted(l3, 84);
-    return r;
+    const uint64_t a1 = (uint64_t)l1 << 28, a2 = (uint64_t)l2 << 56;
+    const uint64_t h1 = (uint64_t)(l1 >> 36), h2 = (uint64_t)(l2 >> 8), h3 = (uint64_t)l3 << 20;
+    uint64_t lo = l0 + a1;
+    uint64_t hi = h1 + h2 + h3 + (lo < a1 ? 1ull : 0ull);
+    const uint64_t lo2 = lo + a2;
+    hi += lo2 < a2 ? 1ull : 0ull;
+    return Acc128{lo2, hi};
   }
 };
 

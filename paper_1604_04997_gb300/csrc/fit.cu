@@ -1,0 +1,417 @@
+// Weight fit (Sec. 4.3): for every device model m, find w_m minimising
+//   relative objective  sum_j (1 - F_j w_m / t_jm)^2     (the paper's)
+//   absolute objective  sum_j (t_jm - F_j w_m)^2
+// The least-squares matrix of model m is A_m = diag(1/t_m) F (relative) or F
+// (absolute); its columns are scaled by powers of two so that max_r |A_rc| lies in
+// [1/2, 1).  The normal equations A^T A x = A^T b (b = 1, or b = t_m) are formed
+// with FP32 products and compensated FP32 sums per row chunk, chunks summed in FP64;
+// the k x k systems are factored by FP64 Cholesky.  Iterative refinement then
+// recovers the accuracy: r = b - A x is formed from the exact fixed-point product
+// F w (the prediction kernel's arithmetic) and an FP64 division, the correction
+// solves G d = A^T r with the same factor, and x += d.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "eval_common.cuh"
+#include "kernels.h"
+#include "pm.h"
+
+namespace pmd {
+
+constexpr int FIT_MAXK = 32;
+constexpr int FIT_ROWS = 64;      // rows staged per batch
+constexpr int FIT_THREADS = 256;
+
+// ---- column maxima of |F| (as unsigned bit patterns, for atomicMax)
+__global__ void k_colmax(const int64_t *__restrict__ F, int64_t R, int k, unsigned long long *cmax) {
+  __shared__ unsigned long long s[FIT_MAXK];
+  if (threadIdx.x < FIT_MAXK) s[threadIdx.x] = 0;
+  __syncthreads();
+  const int c = threadIdx.x % k;
+  const int rstep = blockDim.x / k;
+  unsigned long long m = 0;
+  if (threadIdx.x < rstep * k) {
+    for (int64_t r = (int64_t)blockIdx.x * rstep + threadIdx.x / k; r < R; r += (int64_t)gridDim.x * rstep) {
+      const int64_t v = F[r * k + c];
+      const unsigned long long a = (unsigned long long)(v < 0 ? -v : v);
+      m = a > m ? a : m;
+    }
+    atomicMax(&s[c], m);
+  }
+  __syncthreads();
+  if (threadIdx.x < k) atomicMax(&cmax[threadIdx.x], s[threadIdx.x]);
+}
+
+// exponent e_c with max |F_c| in [2^(e-1), 2^e) (0 for an all-zero column)
+__device__ __forceinline__ int col_exp(unsigned long long mx) { return mx ? 64 - __clzll((long long)mx) : 0; }
+
+// ---- U = F diag(2^-e) in FP32 (64-bit integer -> float via two 32-bit halves)
+__global__ void k_scale(const int64_t *__restrict__ F, int64_t R, int k, const unsigned long long *cmax,
+                        float *__restrict__ U) {
+  const int64_t n = R * k;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(i % k);
+    const int64_t v = F[i];
+    const float hi = (float)(int32_t)(v >> 32), lo = (float)(uint32_t)v;
+    const float x = __fmaf_rn(hi, 4294967296.0f, lo);
+    U[i] = ldexpf(x, -col_exp(cmax[c]));
+  }
+}
+
+// ---- per (model, column) maxima of |A_rc| = |U_rc| * rowfactor_rm (float bits, atomicMax)
+__global__ void k_acolmax(const float *__restrict__ U, const double *__restrict__ T, int64_t R, int k, int M,
+                          int objective, int64_t rows_per_chunk, unsigned *__restrict__ amax) {
+  const int m = blockIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t r1 = min(R, r0 + rows_per_chunk);
+  const int c = threadIdx.x % 32, lr = threadIdx.x / 32;
+  float mx = 0.f;
+  if (c < k)
+    for (int64_t r = r0 + lr; r < r1; r += FIT_THREADS / 32) {
+      float x = fabsf(U[r * k + c]);
+      if (objective == PM_FIT_RELATIVE) x = __fdiv_rn(x, (float)T[r * M + m]);
+      mx = fmaxf(mx, x);
+    }
+  __shared__ float red[FIT_THREADS];
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32 && c < k) {
+    float t = 0.f;
+    for (int q = 0; q < FIT_THREADS / 32; q++) t = fmaxf(t, red[q * 32 + threadIdx.x]);
+    atomicMax(&amax[m * FIT_MAXK + c], __float_as_uint(t));   // non-negative floats order as integers
+  }
+}
+
+// power-of-two exponent f with max |A_c| * 2^-f in [1/2, 1) (0 for an all-zero column)
+__device__ __forceinline__ int acol_exp(unsigned bits) {
+  if (!bits) return 0;
+  int e;
+  frexpf(__uint_as_float(bits), &e);
+  return e;
+}
+
+// ---- Gram matrices and right-hand sides.
+// Grid (row chunks, models).  Each CTA accumulates, for its model, the upper triangle
+// of sum_r v_r v_r^T and sum_r v_r * beta_r over its rows, where
+// relative: v = u / t, beta = 1;   absolute: v = u, beta = t.
+// Each thread owns up to 3 of the (k(k+1)/2 + k) sums, accumulated with TwoSum
+// compensation; the chunk result is added to the FP64 totals with atomics.
+__global__ void __launch_bounds__(FIT_THREADS) k_gram(const float *__restrict__ U, const double *__restrict__ T,
+                                                      int64_t R, int k, int M, int objective, int64_t rows_per_chunk,
+                                                      const unsigned *__restrict__ amax, double *__restrict__ G,
+                                                      double *__restrict__ rhs) {
+  __shared__ float v[FIT_ROWS][FIT_MAXK + 1];
+  __shared__ float beta[FIT_ROWS];
+  __shared__ int f[FIT_MAXK];
+  const int m = blockIdx.y;
+  if (threadIdx.x < FIT_MAXK) f[threadIdx.x] = threadIdx.x < k ? acol_exp(amax[m * FIT_MAXK + threadIdx.x]) : 0;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t r1 = min(R, r0 + rows_per_chunk);
+  const int npairs = k * (k + 1) / 2, nsums = npairs + k;
+  int pa[3], pb[3];
+  float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    int id = threadIdx.x + q * FIT_THREADS;
+    pa[q] = pb[q] = -1;
+    if (id < npairs) {
+      int a = 0;
+      while (id >= k - a) { id -= k - a; a++; }
+      pa[q] = a;
+      pb[q] = a + id;
+    } else if (id < nsums) {
+      pa[q] = id - npairs;
+      pb[q] = -2;  // right-hand side
+    }
+  }
+  for (int64_t rb = r0; rb < r1; rb += FIT_ROWS) {
+    __syncthreads();
+    const int nr = (int)min((int64_t)FIT_ROWS, r1 - rb);
+    for (int i = threadIdx.x; i < FIT_ROWS * k; i += FIT_THREADS) {
+      const int rr = i / k, cc = i - rr * k;
+      float x = 0.f;
+      if (rr < nr) {
+        x = U[(rb + rr) * k + cc];
+        if (objective == PM_FIT_RELATIVE) x = __fdiv_rn(x, (float)T[(rb + rr) * M + m]);
+        x = ldexpf(x, -f[cc]);
+      }
+      v[rr][cc] = x;
+    }
+    for (int rr = threadIdx.x; rr < FIT_ROWS; rr += FIT_THREADS)
+      beta[rr] = rr < nr ? (objective == PM_FIT_RELATIVE ? 1.f : (float)T[(rb + rr) * M + m]) : 0.f;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      if (pa[q] < 0) continue;
+      for (int rr = 0; rr < nr; rr++) {
+        const float p = pb[q] >= 0 ? __fmul_rn(v[rr][pa[q]], v[rr][pb[q]]) : __fmul_rn(v[rr][pa[q]], beta[rr]);
+        const float t = __fadd_rn(s[q], p);
+        const float z = __fsub_rn(t, s[q]);
+        c[q] = __fadd_rn(c[q], __fadd_rn(__fsub_rn(s[q], __fsub_rn(t, z)), __fsub_rn(p, z)));
+        s[q] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    if (pa[q] < 0) continue;
+    const double val = (double)s[q] + (double)c[q];
+    if (pb[q] >= 0) atomicAdd(&G[((int64_t)m * FIT_MAXK + pa[q]) * FIT_MAXK + pb[q]], val);
+    else atomicAdd(&rhs[(int64_t)m * FIT_MAXK + pa[q]], val);
+  }
+}
+
+// ---- Cholesky of each model's Gram (one warp per model), FP64.
+// Columns whose scale exponent marks them all-zero are replaced by identity rows
+// (weight 0).  A pivot below tol * (largest diagonal) marks the model rank deficient
+// and its direction is dropped likewise.  Writes L (lower) and the first solution.
+__global__ void k_chol_solve(double *__restrict__ G, const double *__restrict__ rhs, int k, int M,
+                             const unsigned long long *cmax, double *__restrict__ x, int *__restrict__ info,
+                             double *__restrict__ diag_ratio) {
+  const int m = blockIdx.x;
+  if (m >= M) return;
+  __shared__ double L[FIT_MAXK][FIT_MAXK + 1];
+  __shared__ double y[FIT_MAXK];
+  __shared__ int dead[FIT_MAXK];
+  const int lane = threadIdx.x;
+  double *Gm = G + (int64_t)m * FIT_MAXK * FIT_MAXK;
+  for (int i = lane; i < k * k; i += 32) {
+    const int a = i / k, b = i - a * k;
+    L[a][b] = a <= b ? Gm[a * FIT_MAXK + b] : Gm[b * FIT_MAXK + a];   // symmetric from the upper triangle
+  }
+  if (lane < k) dead[lane] = cmax[lane] == 0;
+  __syncwarp();
+  double dmax = 0;
+  for (int a = 0; a < k; a++) if (!dead[a]) dmax = fmax(dmax, L[a][a]);
+  const double tol = dmax * 1e-13;
+  int rank = 0;
+  double pmin = 1e300, pmax = 0;
+  for (int j = 0; j < k; j++) {
+    // L[j][j] = sqrt(G[j][j] - sum_{p<j} L[j][p]^2)
+    double d = L[j][j];
+    for (int p = 0; p < j; p++) d -= L[j][p] * L[j][p];
+    const bool drop = dead[j] || !(d > tol);
+    __syncwarp();
+    if (drop) {
+      if (lane == 0) { dead[j] = 1; L[j][j] = 1.0; }
+      if (lane < k && lane > j) L[lane][j] = 0.0;
+      if (lane < j) L[j][lane] = 0.0;
+      __syncwarp();
+      continue;
+    }
+    const double ljj = sqrt(d);
+    rank++;
+    pmin = fmin(pmin, ljj);
+    pmax = fmax(pmax, ljj);
+    if (lane > j && lane < k) {
+      double s = L[lane][j];
+      for (int p = 0; p < j; p++) s -= L[lane][p] * L[j][p];
+      L[lane][j] = s / ljj;
+    }
+    __syncwarp();
+    if (lane == 0) L[j][j] = ljj;
+    __syncwarp();
+  }
+  // forward and back substitution (one lane), dead directions get 0
+  if (lane == 0) {
+    for (int a = 0; a < k; a++) {
+      double s = dead[a] ? 0.0 : rhs[(int64_t)m * FIT_MAXK + a];
+      for (int p = 0; p < a; p++) s -= L[a][p] * y[p];
+      y[a] = dead[a] ? 0.0 : s / L[a][a];
+    }
+    for (int a = k - 1; a >= 0; a--) {
+      double s = y[a];
+      for (int p = a + 1; p < k; p++) s -= L[p][a] * x[(int64_t)m * FIT_MAXK + p];
+      x[(int64_t)m * FIT_MAXK + a] = dead[a] ? 0.0 : s / L[a][a];
+    }
+    int nz = 0;
+    for (int a = 0; a < k; a++) nz += cmax[a] == 0;
+    unsigned mask = 0;
+    for (int a = 0; a < k; a++) mask |= (unsigned)dead[a] << a;
+    info[m * 4 + 0] = rank;
+    info[m * 4 + 1] = nz;
+    info[m * 4 + 2] = rank < k - nz ? 1 : 0;
+    info[m * 4 + 3] = (int)mask;
+    diag_ratio[m] = pmin > 0 ? (pmax / pmin) * (pmax / pmin) : 1e300;
+  }
+  __syncwarp();
+  for (int i = lane; i < k * k; i += 32) {
+    const int a = i / k, b = i - a * k;
+    Gm[a * FIT_MAXK + b] = b <= a ? L[a][b] : 0.0;   // keep L for the refinement solves
+  }
+  if (lane < k) Gm[lane * FIT_MAXK + lane] = L[lane][lane];
+}
+
+// ---- weights from scaled coordinates: w_c = x_c * 2^-e_c
+__global__ void k_unscale(const double *__restrict__ x, int k, int M, const unsigned long long *cmax,
+                          const unsigned *__restrict__ amax, double *__restrict__ W) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= k * M) return;
+  const int m = i / k, c = i - m * k;
+  W[i] = cmax[c] ? ldexp(x[(int64_t)m * FIT_MAXK + c], -col_exp(cmax[c]) - acol_exp(amax[m * FIT_MAXK + c])) : 0.0;
+}
+
+// ---- residual q = (b - A x) scaled for A^T q, from the exact product p = F w:
+// relative: r = 1 - p / t, q = r / t;   absolute: r = t - p, q = r.  Also sums r^2 and b^2.
+__global__ void k_residual(const double *__restrict__ P, const double *__restrict__ T, int64_t R, int M,
+                           int objective, float *__restrict__ Q, double *__restrict__ rr, double *__restrict__ bb,
+                           int *status) {
+  __shared__ double s_r[64], s_b[64];
+  if (threadIdx.x < 64) { s_r[threadIdx.x] = 0; s_b[threadIdx.x] = 0; }
+  __syncthreads();
+  const int64_t n = R * M;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i % M);
+    const double t = T[i], p = P[i];
+    if (!(t > 0.0) || t > 1e300) atomicOr(status, ST_BAD_INPUT);
+    double r, q, b;
+    if (objective == PM_FIT_RELATIVE) { r = 1.0 - p / t; q = r / t; b = 1.0; }
+    else { r = t - p; q = r; b = t; }
+    Q[i] = (float)q;
+    atomicAdd(&s_r[m], r * r);
+    atomicAdd(&s_b[m], b * b);
+  }
+  __syncthreads();
+  if (threadIdx.x < M && threadIdx.x < 64) {
+    atomicAdd(&rr[threadIdx.x], s_r[threadIdx.x]);
+    atomicAdd(&bb[threadIdx.x], s_b[threadIdx.x]);
+  }
+}
+
+// ---- g_m = U^T q_m  (compensated FP32 per chunk, FP64 totals); grid (row chunks, models)
+__global__ void __launch_bounds__(FIT_THREADS) k_atq(const float *__restrict__ U, const float *__restrict__ Q,
+                                                     int64_t R, int k, int M, int64_t rows_per_chunk,
+                                                     const unsigned *__restrict__ amax, double *__restrict__ g) {
+  const int m = blockIdx.y;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
+  const int64_t r1 = min(R, r0 + rows_per_chunk);
+  const int c = threadIdx.x % 32, lane_r = threadIdx.x / 32;   // 8 row lanes x 32 columns
+  float s = 0.f, cc = 0.f;
+  if (c < k) {
+    for (int64_t r = r0 + lane_r; r < r1; r += FIT_THREADS / 32) {
+      const float p = __fmul_rn(U[r * k + c], Q[r * M + m]);
+      const float t = __fadd_rn(s, p);
+      const float z = __fsub_rn(t, s);
+      cc = __fadd_rn(cc, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)));
+      s = t;
+    }
+  }
+  __shared__ double red[FIT_THREADS];
+  red[threadIdx.x] = (double)s + (double)cc;
+  __syncthreads();
+  if (threadIdx.x < 32 && c < k) {
+    double tot = 0;
+    for (int q = 0; q < FIT_THREADS / 32; q++) tot += red[q * 32 + threadIdx.x];
+    atomicAdd(&g[(int64_t)m * FIT_MAXK + c], ldexp(tot, -acol_exp(amax[m * FIT_MAXK + c])));
+  }
+}
+
+// ---- x += L^-T L^-1 g per model; records |d| / |x|
+__global__ void k_refine_update(const double *__restrict__ Lall, const double *__restrict__ g, int k, int M,
+                                const int *__restrict__ info, double *__restrict__ x, double *__restrict__ upd) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const unsigned dead = (unsigned)info[m * 4 + 3];
+  const double *L = Lall + (int64_t)m * FIT_MAXK * FIT_MAXK;
+  double y[FIT_MAXK], d[FIT_MAXK];
+  for (int a = 0; a < k; a++) {
+    double s = (dead >> a) & 1 ? 0.0 : g[(int64_t)m * FIT_MAXK + a];
+    for (int p = 0; p < a; p++) s -= L[a * FIT_MAXK + p] * y[p];
+    y[a] = s / L[a * FIT_MAXK + a];
+  }
+  double dn = 0, xn = 0;
+  for (int a = k - 1; a >= 0; a--) {
+    double s = y[a];
+    for (int p = a + 1; p < k; p++) s -= L[p * FIT_MAXK + a] * d[p];
+    d[a] = s / L[a * FIT_MAXK + a];
+  }
+  for (int a = 0; a < k; a++) {
+    if ((dead >> a) & 1) d[a] = 0;
+    x[(int64_t)m * FIT_MAXK + a] += d[a];
+    dn += d[a] * d[a];
+    xn += x[(int64_t)m * FIT_MAXK + a] * x[(int64_t)m * FIT_MAXK + a];
+  }
+  upd[m] = xn > 0 ? sqrt(dn / xn) : 0.0;
+}
+
+// ------------------------------------------------------------------------------------ host side
+
+size_t fit_scratch_bytes(int64_t R, int k, int M) {
+  size_t b = 0;
+  b += 256;                                        // cmax
+  b += (size_t)M * FIT_MAXK * 4;                   // amax
+  b += (size_t)R * k * 4;                          // U
+  b += (size_t)R * M * 4;                          // Q
+  b += (size_t)R * M * 8;                          // P
+  b += (size_t)M * FIT_MAXK * FIT_MAXK * 8;        // G / L
+  b += (size_t)M * FIT_MAXK * 8 * 3;               // rhs, x, g
+  b += (size_t)M * (4 * 4 + 8 * 4);                // info, ratio, upd, rr, bb
+  return b + 16 * 64;
+}
+
+static char *carve(char *&p, size_t bytes) {
+  char *r = p;
+  p += (bytes + 255) & ~(size_t)255;
+  return r;
+}
+
+cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int steps,
+                       void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st) {
+  char *p = (char *)scratch;
+  unsigned long long *cmax = (unsigned long long *)carve(p, 256);
+  unsigned *amax = (unsigned *)carve(p, (size_t)M * FIT_MAXK * 4);
+  float *U = (float *)carve(p, (size_t)R * k * 4);
+  float *Q = (float *)carve(p, (size_t)R * M * 4);
+  double *P = (double *)carve(p, (size_t)R * M * 8);
+  double *G = (double *)carve(p, (size_t)M * FIT_MAXK * FIT_MAXK * 8);
+  double *rhs = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
+  double *x = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
+  double *g = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
+  int *info = (int *)carve(p, (size_t)M * 16);
+  double *ratio = (double *)carve(p, (size_t)M * 8);
+  double *upd = (double *)carve(p, (size_t)M * 8);
+  double *rr = (double *)carve(p, (size_t)M * 8);
+  double *bb = (double *)carve(p, (size_t)M * 8);
+  cudaError_t e;
+  cudaMemsetAsync(cmax, 0, 256, st);
+  cudaMemsetAsync(amax, 0, (size_t)M * FIT_MAXK * 4, st);
+  cudaMemsetAsync(G, 0, (size_t)M * FIT_MAXK * FIT_MAXK * 8, st);
+  cudaMemsetAsync(rhs, 0, (size_t)M * FIT_MAXK * 8, st);
+  cudaMemsetAsync(upd, 0, (size_t)M * 8, st);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_colmax<<<sms * 2, 256, 0, st>>>(F, R, k, cmax);
+  k_scale<<<sms * 8, 256, 0, st>>>(F, R, k, cmax, U);
+  const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / std::max(1, M) + 1, (R + 255) / 256));
+  const int64_t rpc = (R + chunks - 1) / chunks;
+  k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, T, R, k, M, objective, rpc, amax);
+  k_gram<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, T, R, k, M, objective, rpc, amax, G, rhs);
+  k_chol_solve<<<M, 32, 0, st>>>(G, rhs, k, M, cmax, x, info, ratio);
+  for (int it = 0; it < steps; it++) {
+    k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
+    if ((e = launch_predict(F, R, k, W_out, M, PM_PREC_FP64, P, st)) != cudaSuccess) return e;
+    cudaMemsetAsync(rr, 0, (size_t)M * 8, st);
+    cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
+    cudaMemsetAsync(g, 0, (size_t)M * FIT_MAXK * 8, st);
+    k_residual<<<sms * 4, 256, 0, st>>>(P, T, R, M, objective, Q, rr, bb, status);
+    k_atq<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Q, R, k, M, rpc, amax, g);
+    k_refine_update<<<(M + 31) / 32, 32, 0, st>>>(G, g, k, M, info, x, upd);
+  }
+  k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
+  // final residual for the report
+  if ((e = launch_predict(F, R, k, W_out, M, PM_PREC_FP64, P, st)) != cudaSuccess) return e;
+  cudaMemsetAsync(rr, 0, (size_t)M * 8, st);
+  cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
+  k_residual<<<sms * 4, 256, 0, st>>>(P, T, R, M, objective, Q, rr, bb, status);
+  cudaMemcpyAsync(host->info, info, (size_t)M * 16, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(host->ratio, ratio, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(host->upd, upd, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(host->rr, rr, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(host->bb, bb, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
+  return cudaGetLastError();
+}
+
+}  // namespace pmd

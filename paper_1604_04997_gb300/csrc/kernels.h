@@ -6,7 +6,7 @@
 namespace pmd {
 
 // bits of the device status word
-enum StatusBits { ST_OUT_OF_BOX = 1, ST_BAD_TABLE = 2, ST_TIMEOUT = 4 };
+enum StatusBits { ST_OUT_OF_BOX = 1, ST_BAD_TABLE = 2, ST_TIMEOUT = 4, ST_BAD_INPUT = 8 };
 
 // K1 (eval.cu)
 cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, int n_tables, const int64_t *points,
@@ -48,5 +48,14 @@ size_t argmin_scratch_bytes(int M, int n_part);
 int argmin_parts();
 cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
                                   void *scratch, int64_t *arg, double *mn, cudaStream_t st);
+
+// fit.cu
+struct FitHost {            // pinned host buffers filled by the fit (per model)
+  int *info;                // [M][4] rank, zero columns, rank deficient, dropped-direction mask
+  double *ratio, *upd, *rr, *bb;
+};
+size_t fit_scratch_bytes(int64_t R, int k, int M);
+cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int steps,
+                       void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st);
 
 }  // namespace pmd

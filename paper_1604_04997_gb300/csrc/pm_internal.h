@@ -54,6 +54,7 @@ struct pm_ctx {
   std::string tune_path;
   ServeState *serve = nullptr;
   double *d_models = nullptr;                 // resident weights [n_models][32]
+  void *fit_host = nullptr;                   // pinned report buffers of the fit
   int n_models = 0;
 };
 

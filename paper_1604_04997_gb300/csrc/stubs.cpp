@@ -6,10 +6,6 @@ pm_status pm_predict_bf16x3(pm_ctx *, const int64_t *, int64_t, int, const doubl
                             double *, void *) {
   return pm_set_error(PM_ERR_UNSUPPORTED, "PM_PREC_BF16X3 is not available in this build");
 }
-extern "C" pm_status pm_fit_weights(pm_ctx *, const int64_t *, int64_t, int32_t, const double *, int32_t, int32_t,
-                                    int32_t, int32_t, double *, pm_fit_report *, void *) {
-  return pm_set_error(PM_ERR_UNSUPPORTED, "pm_fit_weights is not available in this build");
-}
 extern "C" pm_status pm_serve_set_weights(pm_ctx *, const double *, int32_t) {
   return pm_set_error(PM_ERR_UNSUPPORTED, "serving is not available in this build");
 }
