@@ -313,6 +313,112 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _clocks_and_time(fn, steps, warmup, stream, flush=None):
+    """Warm up, then time `steps` calls of fn with CUDA events on `stream` (L2 flushed
+    before each); returns (mean ms, clock summary)."""
+    import torch
+    for _ in range(max(3, warmup)):
+        fn()
+    torch.cuda.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ck = Clocks(torch.cuda.current_device())
+    ck.start()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            if flush is not None:
+                flush.zero_()
+            ev0[i].record(stream)
+            fn()
+            ev1[i].record(stream)
+    torch.cuda.synchronize()
+    c = ck.stop()
+    return sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / steps, c
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_other(args):
+    """Secondary workloads (one JSON line each): materialised counts, cross-model
+    prediction, weight fit."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_1604_04997_gb300 import binding as B
+    from paper_1604_04997_gb300 import tuning
+    from paper_1604_04997_gb300 import workloads as W
+    __graft_entry__.build()
+    dev = torch.device("cuda:0")
+    ctx = B.Context(0)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)
+    hbm = float(_peaks().get("hbm_gbs", 6790.0))
+    base = {"n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "scaling": "weak",
+            "vs_baseline": None, "data": "synthetic", "gpu_launches": None}
+    if args.workload == "eval":
+        bp = tuning.build(ctx, args.variants, args.points)
+        outs, calls = [], []
+        for t in range(len(bp.templates)):
+            ids = bp.tables[bp.var_off[t]:bp.var_off[t + 1]]
+            P = len(W.TEMPLATE_PARAMS[bp.templates[t]])
+            pts = torch.from_numpy(np.ascontiguousarray(bp.points[bp.pt_off[t]:bp.pt_off[t + 1], :P])).to(dev)
+            out = torch.empty((len(ids), pts.shape[0], 32), dtype=torch.int64, device=dev)
+            calls.append((ids, pts, out))
+        def fn():
+            for ids, pts, out in calls:
+                ctx.eval_counts(ids, pts, out, stream=stream)
+        ms, ck = _clocks_and_time(fn, args.steps, args.warmup, stream, flush)
+        ctx.sync_status(stream)
+        evals = bp.total_evals
+        nbytes = evals * 32 * 8 + sum(int(c[1].numel()) * 8 * len(c[0]) for c in calls)
+        line = dict(base, metric="materialised count evaluations/s (pm_eval_counts, int64 [tables][points][32])",
+                    value=evals / (ms / 1e3), unit="evals/s", ms_per_step=ms, higher_is_better=True, dtype="int64",
+                    config={"workload": "10,000 variants x 4,096 points per template, all 32 counts written",
+                            "bytes_per_step": nbytes, "l2": "flushed before every timed step"},
+                    roofline={"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": nbytes / (ms / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_eval_counts",
+                              "algorithmic_bytes": "256 B of counts written per evaluation + 8 B per parameter read"},
+                    clocks=ck, gpu_launches=len(calls) * args.steps)
+    elif args.workload == "predict":
+        R, M = 1_000_000, 64
+        F = torch.from_numpy(W.fit_features(R, 32, 7)).to(dev)
+        Wm = torch.from_numpy(W.draw_weights(32, M, 8)).to(dev)
+        T = torch.empty((R, M), dtype=torch.float64, device=dev)
+        fn = lambda: ctx.predict(F, Wm, T, B.PREC_FP64, stream=stream)
+        ms, ck = _clocks_and_time(fn, args.steps, args.warmup, stream, flush)
+        nbytes = R * 32 * 8 + R * M * 8
+        line = dict(base, metric="cross-model predictions/s (1e6 rows x 32 features x 64 models, FP64-accurate)",
+                    value=R * M / (ms / 1e3), unit="predictions/s", ms_per_step=ms, higher_is_better=True,
+                    dtype="int64 x fixed-point int (exact, 128-bit sums)",
+                    config={"workload": "1,000,000 feature rows x 32 int64 features x 64 weight vectors",
+                            "bytes_per_step": nbytes},
+                    roofline={"bound": "alu", "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_peak": hbm,
+                              "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm, "kernel": "k_predict_ff"},
+                    clocks=ck, gpu_launches=args.steps)
+    elif args.workload == "fit":
+        R, M = 200_000, 64
+        Fh = W.fit_features(R, 32, 5)
+        Th = W.synth_timings(Fh, W.draw_weights(32, M, 6), 6)
+        F = torch.from_numpy(Fh).to(dev)
+        T = torch.from_numpy(Th).to(dev)
+        Wo = torch.empty((M, 32), dtype=torch.float64, device=dev)
+        fn = lambda: ctx.fit_weights(F, T, Wo, B.FIT_RELATIVE, B.PREC_BF16X3, 3, stream=stream)
+        ms, ck = _clocks_and_time(fn, args.steps, args.warmup, stream, None)
+        line = dict(base, metric="weight fits/s (200,000 rows x 32 features, 64 models, 3 refinement steps)",
+                    value=M / (ms / 1e3), unit="model fits/s", ms_per_step=ms, higher_is_better=True,
+                    dtype="float-float Gram, FP64 Cholesky, exact residual products",
+                    config={"workload": "200,000 x 32 int64 features, 64 device models, relative objective"},
+                    clocks=ck, gpu_launches=None)
+    print(json.dumps(line))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,10 +430,13 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=8.0)
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-tune", action="store_true", help="use the default launch shape (8 warps, 2 CTAs/SM)")
+    ap.add_argument("--no-tune", action="store_true", help="use the default launch shape")
+    ap.add_argument("--workload", default="batched", choices=["batched", "eval", "predict", "fit"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "batched":
+        run_other(args)
     else:
         run_ours(args)
 

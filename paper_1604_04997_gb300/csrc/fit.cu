@@ -4,7 +4,9 @@
 // The least-squares matrix of model m is A_m = diag(1/t_m) F (relative) or F
 // (absolute); its columns are scaled by powers of two so that max_r |A_rc| lies in
 // [1/2, 1).  The normal equations A^T A x = A^T b (b = 1, or b = t_m) are formed
-// with FP32 products and compensated FP32 sums per row chunk, chunks summed in FP64;
+// in float-float arithmetic on the FP32 pipes (entries split exactly into hi + lo
+// pairs, error-free products by FMA, compensated sums; about 2^-44 relative) per row
+// chunk, chunks summed in FP64;
 // the k x k systems are factored by FP64 Cholesky.  Iterative refinement then
 // recovers the accuracy: r = b - A x is formed from the exact fixed-point product
 // F w (the prediction kernel's arithmetic) and an FP64 division, the correction
@@ -47,22 +49,52 @@ __global__ void k_colmax(const int64_t *__restrict__ F, int64_t R, int k, unsign
 // exponent e_c with max |F_c| in [2^(e-1), 2^e) (0 for an all-zero column)
 __device__ __forceinline__ int col_exp(unsigned long long mx) { return mx ? 64 - __clzll((long long)mx) : 0; }
 
-// ---- U = F diag(2^-e) in FP32 (64-bit integer -> float via two 32-bit halves)
+// ---- U = F diag(2^-e) as float-float pairs: Uh = rn(F), Ul = rn(F - Uh), scaled exactly
 __global__ void k_scale(const int64_t *__restrict__ F, int64_t R, int k, const unsigned long long *cmax,
-                        float *__restrict__ U) {
+                        float *__restrict__ Uh, float *__restrict__ Ul) {
   const int64_t n = R * k;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(i % k);
     const int64_t v = F[i];
-    const float hi = (float)(int32_t)(v >> 32), lo = (float)(uint32_t)v;
-    const float x = __fmaf_rn(hi, 4294967296.0f, lo);
-    U[i] = ldexpf(x, -col_exp(cmax[c]));
+    const float h = __ll2float_rn(v);
+    const float l = __ll2float_rn(v - (int64_t)h);
+    const int e = col_exp(cmax[c]);
+    Uh[i] = ldexpf(h, -e);
+    Ul[i] = ldexpf(l, -e);
   }
 }
 
+// ---- row factors as float-float: 1/t (relative) or 1 (absolute); beta = 1 or t
+__global__ void k_rowfac(const double *__restrict__ T, int64_t n, int objective, float2 *__restrict__ rf,
+                         float2 *__restrict__ beta) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double t = T[i];
+    const double r = objective == PM_FIT_RELATIVE ? 1.0 / t : 1.0;
+    const double b = objective == PM_FIT_RELATIVE ? 1.0 : t;
+    const float rh = __double2float_rn(r), bh = __double2float_rn(b);
+    rf[i] = make_float2(rh, __double2float_rn(r - (double)rh));
+    beta[i] = make_float2(bh, __double2float_rn(b - (double)bh));
+  }
+}
+
+// float-float helpers: error-free product by FMA, compensated accumulation
+__device__ __forceinline__ float2 ff_mul(float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  return make_float2(p, e);
+}
+__device__ __forceinline__ void ff_acc(float &s, float &c, float2 p) {
+  const float t = __fadd_rn(s, p.x);
+  const float z = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p.x, z)), p.y));
+  s = t;
+}
+
 // ---- per (model, column) maxima of |A_rc| = |U_rc| * rowfactor_rm (float bits, atomicMax)
-__global__ void k_acolmax(const float *__restrict__ U, const double *__restrict__ T, int64_t R, int k, int M,
-                          int objective, int64_t rows_per_chunk, unsigned *__restrict__ amax) {
+__global__ void k_acolmax(const float *__restrict__ U, const float2 *__restrict__ rf, int64_t R, int k, int M,
+                          int64_t rows_per_chunk, unsigned *__restrict__ amax) {
   const int m = blockIdx.y;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r1 = min(R, r0 + rows_per_chunk);
@@ -70,9 +102,7 @@ __global__ void k_acolmax(const float *__restrict__ U, const double *__restrict_
   float mx = 0.f;
   if (c < k)
     for (int64_t r = r0 + lr; r < r1; r += FIT_THREADS / 32) {
-      float x = fabsf(U[r * k + c]);
-      if (objective == PM_FIT_RELATIVE) x = __fdiv_rn(x, (float)T[r * M + m]);
-      mx = fmaxf(mx, x);
+      mx = fmaxf(mx, fabsf(__fmul_rn(U[r * k + c], rf[r * M + m].x)));
     }
   __shared__ float red[FIT_THREADS];
   red[threadIdx.x] = mx;
@@ -98,12 +128,13 @@ __device__ __forceinline__ int acol_exp(unsigned bits) {
 // relative: v = u / t, beta = 1;   absolute: v = u, beta = t.
 // Each thread owns up to 3 of the (k(k+1)/2 + k) sums, accumulated with TwoSum
 // compensation; the chunk result is added to the FP64 totals with atomics.
-__global__ void __launch_bounds__(FIT_THREADS) k_gram(const float *__restrict__ U, const double *__restrict__ T,
-                                                      int64_t R, int k, int M, int objective, int64_t rows_per_chunk,
+__global__ void __launch_bounds__(FIT_THREADS) k_gram(const float *__restrict__ Uh, const float *__restrict__ Ul,
+                                                      const float2 *__restrict__ rf, const float2 *__restrict__ bt,
+                                                      int64_t R, int k, int M, int64_t rows_per_chunk,
                                                       const unsigned *__restrict__ amax, double *__restrict__ G,
                                                       double *__restrict__ rhs) {
-  __shared__ float v[FIT_ROWS][FIT_MAXK + 1];
-  __shared__ float beta[FIT_ROWS];
+  __shared__ float vh[FIT_ROWS][FIT_MAXK + 1], vl[FIT_ROWS][FIT_MAXK + 1];
+  __shared__ float2 beta[FIT_ROWS];
   __shared__ int f[FIT_MAXK];
   const int m = blockIdx.y;
   if (threadIdx.x < FIT_MAXK) f[threadIdx.x] = threadIdx.x < k ? acol_exp(amax[m * FIT_MAXK + threadIdx.x]) : 0;
@@ -131,26 +162,28 @@ __global__ void __launch_bounds__(FIT_THREADS) k_gram(const float *__restrict__ 
     const int nr = (int)min((int64_t)FIT_ROWS, r1 - rb);
     for (int i = threadIdx.x; i < FIT_ROWS * k; i += FIT_THREADS) {
       const int rr = i / k, cc = i - rr * k;
-      float x = 0.f;
+      float2 v = make_float2(0.f, 0.f);
       if (rr < nr) {
-        x = U[(rb + rr) * k + cc];
-        if (objective == PM_FIT_RELATIVE) x = __fdiv_rn(x, (float)T[(rb + rr) * M + m]);
-        x = ldexpf(x, -f[cc]);
+        const int64_t o = (rb + rr) * k + cc;
+        const float2 r = rf[(rb + rr) * M + m];
+        v = ff_mul(Uh[o], Ul[o], r.x, r.y);
+        v.x = ldexpf(v.x, -f[cc]);
+        v.y = ldexpf(v.y, -f[cc]);
       }
-      v[rr][cc] = x;
+      vh[rr][cc] = v.x;
+      vl[rr][cc] = v.y;
     }
     for (int rr = threadIdx.x; rr < FIT_ROWS; rr += FIT_THREADS)
-      beta[rr] = rr < nr ? (objective == PM_FIT_RELATIVE ? 1.f : (float)T[(rb + rr) * M + m]) : 0.f;
+      beta[rr] = rr < nr ? bt[(rb + rr) * M + m] : make_float2(0.f, 0.f);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < 3; q++) {
       if (pa[q] < 0) continue;
+      const int a = pa[q], b = pb[q];
       for (int rr = 0; rr < nr; rr++) {
-        const float p = pb[q] >= 0 ? __fmul_rn(v[rr][pa[q]], v[rr][pb[q]]) : __fmul_rn(v[rr][pa[q]], beta[rr]);
-        const float t = __fadd_rn(s[q], p);
-        const float z = __fsub_rn(t, s[q]);
-        c[q] = __fadd_rn(c[q], __fadd_rn(__fsub_rn(s[q], __fsub_rn(t, z)), __fsub_rn(p, z)));
-        s[q] = t;
+        const float2 p = b >= 0 ? ff_mul(vh[rr][a], vl[rr][a], vh[rr][b], vl[rr][b])
+                                : ff_mul(vh[rr][a], vl[rr][a], beta[rr].x, beta[rr].y);
+        ff_acc(s[q], c[q], p);
       }
     }
   }
@@ -342,7 +375,8 @@ size_t fit_scratch_bytes(int64_t R, int k, int M) {
   size_t b = 0;
   b += 256;                                        // cmax
   b += (size_t)M * FIT_MAXK * 4;                   // amax
-  b += (size_t)R * k * 4;                          // U
+  b += (size_t)R * k * 8;                          // Uh, Ul
+  b += (size_t)R * M * 16;                         // row factors, beta
   b += (size_t)R * M * 4;                          // Q
   b += (size_t)R * M * 8;                          // P
   b += (size_t)M * FIT_MAXK * FIT_MAXK * 8;        // G / L
@@ -363,6 +397,9 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   unsigned long long *cmax = (unsigned long long *)carve(p, 256);
   unsigned *amax = (unsigned *)carve(p, (size_t)M * FIT_MAXK * 4);
   float *U = (float *)carve(p, (size_t)R * k * 4);
+  float *Ul = (float *)carve(p, (size_t)R * k * 4);
+  float2 *rf = (float2 *)carve(p, (size_t)R * M * 8);
+  float2 *bt = (float2 *)carve(p, (size_t)R * M * 8);
   float *Q = (float *)carve(p, (size_t)R * M * 4);
   double *P = (double *)carve(p, (size_t)R * M * 8);
   double *G = (double *)carve(p, (size_t)M * FIT_MAXK * FIT_MAXK * 8);
@@ -384,11 +421,12 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   k_colmax<<<sms * 2, 256, 0, st>>>(F, R, k, cmax);
-  k_scale<<<sms * 8, 256, 0, st>>>(F, R, k, cmax, U);
+  k_scale<<<sms * 8, 256, 0, st>>>(F, R, k, cmax, U, Ul);
+  k_rowfac<<<sms * 8, 256, 0, st>>>(T, R * M, objective, rf, bt);
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / std::max(1, M) + 1, (R + 255) / 256));
   const int64_t rpc = (R + chunks - 1) / chunks;
-  k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, T, R, k, M, objective, rpc, amax);
-  k_gram<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, T, R, k, M, objective, rpc, amax, G, rhs);
+  k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, rf, R, k, M, rpc, amax);
+  k_gram<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Ul, rf, bt, R, k, M, rpc, amax, G, rhs);
   k_chol_solve<<<M, 32, 0, st>>>(G, rhs, k, M, cmax, x, info, ratio);
   for (int it = 0; it < steps; it++) {
     k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
