@@ -289,7 +289,7 @@ __global__ void k_unscale(const double *__restrict__ x, int k, int M, const unsi
 // ---- residual q = (b - A x) scaled for A^T q, from the exact product p = F w:
 // relative: r = 1 - p / t, q = r / t;   absolute: r = t - p, q = r.  Also sums r^2 and b^2.
 __global__ void k_residual(const double *__restrict__ P, const double *__restrict__ T, int64_t R, int M,
-                           int objective, float *__restrict__ Q, double *__restrict__ rr, double *__restrict__ bb,
+                           int objective, float2 *__restrict__ Q, double *__restrict__ rr, double *__restrict__ bb,
                            int *status) {
   __shared__ double s_r[64], s_b[64];
   if (threadIdx.x < 64) { s_r[threadIdx.x] = 0; s_b[threadIdx.x] = 0; }
@@ -302,7 +302,8 @@ __global__ void k_residual(const double *__restrict__ P, const double *__restric
     double r, q, b;
     if (objective == PM_FIT_RELATIVE) { r = 1.0 - p / t; q = r / t; b = 1.0; }
     else { r = t - p; q = r; b = t; }
-    Q[i] = (float)q;
+    const float qh = __double2float_rn(q);
+    Q[i] = make_float2(qh, __double2float_rn(q - (double)qh));
     atomicAdd(&s_r[m], r * r);
     atomicAdd(&s_b[m], b * b);
   }
@@ -313,10 +314,11 @@ __global__ void k_residual(const double *__restrict__ P, const double *__restric
   }
 }
 
-// ---- g_m = U^T q_m  (compensated FP32 per chunk, FP64 totals); grid (row chunks, models)
-__global__ void __launch_bounds__(FIT_THREADS) k_atq(const float *__restrict__ U, const float *__restrict__ Q,
-                                                     int64_t R, int k, int M, int64_t rows_per_chunk,
-                                                     const unsigned *__restrict__ amax, double *__restrict__ g) {
+// ---- g_m = U^T q_m  (float-float products and sums per chunk, FP64 totals); grid (row chunks, models)
+__global__ void __launch_bounds__(FIT_THREADS) k_atq(const float *__restrict__ Uh, const float *__restrict__ Ul,
+                                                     const float2 *__restrict__ Q, int64_t R, int k, int M,
+                                                     int64_t rows_per_chunk, const unsigned *__restrict__ amax,
+                                                     double *__restrict__ g) {
   const int m = blockIdx.y;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r1 = min(R, r0 + rows_per_chunk);
@@ -324,11 +326,8 @@ __global__ void __launch_bounds__(FIT_THREADS) k_atq(const float *__restrict__ U
   float s = 0.f, cc = 0.f;
   if (c < k) {
     for (int64_t r = r0 + lane_r; r < r1; r += FIT_THREADS / 32) {
-      const float p = __fmul_rn(U[r * k + c], Q[r * M + m]);
-      const float t = __fadd_rn(s, p);
-      const float z = __fsub_rn(t, s);
-      cc = __fadd_rn(cc, __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z)));
-      s = t;
+      const float2 q = Q[r * M + m];
+      ff_acc(s, cc, ff_mul(Uh[r * k + c], Ul[r * k + c], q.x, q.y));
     }
   }
   __shared__ double red[FIT_THREADS];
@@ -377,7 +376,7 @@ size_t fit_scratch_bytes(int64_t R, int k, int M) {
   b += (size_t)M * FIT_MAXK * 4;                   // amax
   b += (size_t)R * k * 8;                          // Uh, Ul
   b += (size_t)R * M * 16;                         // row factors, beta
-  b += (size_t)R * M * 4;                          // Q
+  b += (size_t)R * M * 8;                          // Q
   b += (size_t)R * M * 8;                          // P
   b += (size_t)M * FIT_MAXK * FIT_MAXK * 8;        // G / L
   b += (size_t)M * FIT_MAXK * 8 * 3;               // rhs, x, g
@@ -400,7 +399,7 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   float *Ul = (float *)carve(p, (size_t)R * k * 4);
   float2 *rf = (float2 *)carve(p, (size_t)R * M * 8);
   float2 *bt = (float2 *)carve(p, (size_t)R * M * 8);
-  float *Q = (float *)carve(p, (size_t)R * M * 4);
+  float2 *Q = (float2 *)carve(p, (size_t)R * M * 8);
   double *P = (double *)carve(p, (size_t)R * M * 8);
   double *G = (double *)carve(p, (size_t)M * FIT_MAXK * FIT_MAXK * 8);
   double *rhs = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
@@ -435,7 +434,7 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
     cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
     cudaMemsetAsync(g, 0, (size_t)M * FIT_MAXK * 8, st);
     k_residual<<<sms * 4, 256, 0, st>>>(P, T, R, M, objective, Q, rr, bb, status);
-    k_atq<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Q, R, k, M, rpc, amax, g);
+    k_atq<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Ul, Q, R, k, M, rpc, amax, g);
     k_refine_update<<<(M + 31) / 32, 32, 0, st>>>(G, g, k, M, info, x, upd);
   }
   k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
