@@ -130,6 +130,24 @@ pm_status pm_predict_argmin(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t 
                             const double *d_W, int32_t M, int32_t precision, int64_t *d_arg,
                             double *d_min, void *stream);
 
+/* Allocation-free variant of pm_predict_argmin (PM_PREC_FP64), for callers that
+ * cannot allocate device memory: code running while another allocator owns the
+ * GPU's memory, latency-critical loops that must not trigger cudaMalloc's implicit
+ * synchronisation, or callers that have no pm_ctx (creating one allocates).  The
+ * paper has no counterpart; this is a deployment convenience.
+ * Its partial results live in a fixed 1 MiB device array inside the library, held
+ * by every GPU that loads the library until the process exits; it needs no context
+ * and calls no allocating routine.  d_F, d_W, d_arg, d_min as in pm_predict_argmin
+ * (device pointers of the current device); k <= 40, M <= 64 (larger M is rejected
+ * with PM_ERR_INVALID_ARG).  The first call on each device looks up the array's
+ * device address with that device current, so make that first call before any
+ * stream capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race and must be serialised by
+ * the caller.  Each launch writes every partial entry before reading it, so no
+ * clearing is needed between calls. */
+pm_status pm_predict_argmin_static(const int64_t *d_F, int64_t R, int32_t k, const double *d_W, int32_t M,
+                                   int64_t *d_arg, double *d_min, void *stream);
+
 /* Batched tuning evaluation: for each template t (0..n_templates-1), its
  * variants are the tables h_tables[h_var_off[t] .. h_var_off[t+1]) and its
  * points are rows h_pt_off[t] .. h_pt_off[t+1] of d_points (int64 [total][4],

@@ -74,6 +74,7 @@ def lib():
             "pm_eval_counts": ([vp, vp, i32, vp, i64, vp, vp], i32),
             "pm_predict": ([vp, vp, i64, i32, vp, i32, i32, vp, vp], i32),
             "pm_predict_argmin": ([vp, vp, i64, i32, vp, i32, i32, vp, vp, vp], i32),
+            "pm_predict_argmin_static": ([vp, i64, i32, vp, i32, vp, vp, vp], i32),
             "pm_eval_predict_topk": ([vp, vp, vp, i32, vp, vp, vp, i32, vp, vp, vp], i32),
             "pm_tune": ([vp, i32, ctypes.c_char_p], i32),
             "pm_plan_info": ([vp, vp, vp, i32, vp, vp], i32),
@@ -94,7 +95,8 @@ def lib():
 
 def exported_symbols() -> Sequence[str]:
     return ("pm_create", "pm_destroy", "pm_last_error", "pm_sync_status", "pm_compile_counts", "pm_table_image",
-            "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_eval_predict_topk", "pm_tune",
+            "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
+            "pm_eval_predict_topk", "pm_tune",
             "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
             "pm_serve_poll", "pm_serve_stop")
 
@@ -229,3 +231,9 @@ class Context:
 
     def serve_stop(self):
         _check(lib().pm_serve_stop(self.h))
+
+
+def predict_argmin_static(F, W, arg, mn, stream=None):
+    """pm_predict_argmin_static: needs no context and allocates no device memory."""
+    _check(lib().pm_predict_argmin_static(_ptr(F), F.shape[0], F.shape[1], _ptr(W), W.shape[0], _ptr(arg),
+                                          _ptr(mn), _stream(stream)))

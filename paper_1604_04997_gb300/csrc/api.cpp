@@ -18,14 +18,19 @@
 int pm_compile_table(const char *ir, size_t len, int layout, const int64_t *plo, const int64_t *phi,
                      std::vector<uint32_t> &words, int info[8], std::string &msg);
 
-static thread_local std::string g_err;
+// Last error of the calling thread, in a fixed buffer (reporting an error allocates nothing).
+static thread_local char g_err[512];
 
-pm_status pm_set_error(pm_status code, const std::string &m) {
-  g_err = m;
+pm_status pm_set_error_c(pm_status code, const char *m) {
+  size_t n = 0;
+  while (m[n] && n < sizeof(g_err) - 1) { g_err[n] = m[n]; n++; }
+  g_err[n] = 0;
   return code;
 }
 
-extern "C" const char *pm_last_error(void) { return g_err.c_str(); }
+pm_status pm_set_error(pm_status code, const std::string &m) { return pm_set_error_c(code, m.c_str()); }
+
+extern "C" const char *pm_last_error(void) { return g_err; }
 
 #define CU(x)                                                                                          \
   do {                                                                                                 \

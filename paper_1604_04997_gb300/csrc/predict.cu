@@ -11,10 +11,12 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "eval_common.cuh"
 #include "kernels.h"
 #include "pm.h"
+#include "pm_internal.h"
 
 namespace pmd {
 
@@ -204,15 +206,57 @@ __global__ void k_argmin_reduce(const ArgPart *__restrict__ part, int n_part, in
 int argmin_parts() { return num_sms() * 4; }
 size_t argmin_scratch_bytes(int M, int n_part) { return (size_t)M * n_part * sizeof(ArgPart); }
 
-cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
-                                  void *scratch, int64_t *arg, double *mn, cudaStream_t st) {
-  if (k > PR_MAXK || M > PR_MAXM || precision != PM_PREC_FP64) return cudaErrorInvalidValue;
+static cudaError_t launch_argmin_parts(const int64_t *F, int64_t R, int k, const double *W, int M, void *scratch,
+                                       int np, int64_t *arg, double *mn, cudaStream_t st) {
   size_t sm = sizeof(PredictSmem);
   cudaFuncSetAttribute(k_predict_argmin_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int np = argmin_parts();
   k_predict_argmin_part<<<np, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, (ArgPart *)scratch);
   k_argmin_reduce<<<(M + 63) / 64, 64, 0, st>>>((const ArgPart *)scratch, np, M, arg, mn);
   return cudaGetLastError();
 }
 
+cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
+                                  void *scratch, int64_t *arg, double *mn, cudaStream_t st) {
+  if (k > PR_MAXK || M > PR_MAXM || precision != PM_PREC_FP64) return cudaErrorInvalidValue;
+  return launch_argmin_parts(F, R, k, W, M, scratch, argmin_parts(), arg, mn, st);
+}
+
+// ---------------------------------------------------------------- allocation-free argmin
+
+// Partial results of pm_predict_argmin_static live in this fixed device array instead
+// of memory from cudaMalloc.  Every GPU that loads the library holds it until exit.
+constexpr size_t STATIC_ARGMIN_BYTES = size_t(1) << 20;
+static __device__ __align__(256) unsigned char g_argmin_scratch[STATIC_ARGMIN_BYTES];
+
+// Device address of g_argmin_scratch per device, looked up on the first call made
+// with that device current (host code may not use the symbol itself as a pointer).
+constexpr int STATIC_MAX_DEVICES = 64;
+static std::atomic<void *> g_argmin_addr[STATIC_MAX_DEVICES];
+
 }  // namespace pmd
+
+extern "C" pm_status pm_predict_argmin_static(const int64_t *d_F, int64_t R, int32_t k, const double *d_W,
+                                              int32_t M, int64_t *d_arg, double *d_min, void *stream) {
+  using namespace pmd;
+  if (R < 0 || k <= 0 || k > PR_MAXK || M <= 0 || M > PR_MAXM)
+    return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: need R >= 0, 0 < k <= 40, 0 < M <= 64");
+  if (!d_F || !d_W || !d_arg || !d_min) return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: null pointer");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES)
+    return pm_set_error_c(PM_ERR_CUDA, "pm_predict_argmin_static: no usable current device");
+  void *scratch = g_argmin_addr[dev].load();
+  if (!scratch) {
+    if (cudaGetSymbolAddress(&scratch, g_argmin_scratch) != cudaSuccess || !scratch)
+      return pm_set_error_c(PM_ERR_CUDA, "pm_predict_argmin_static: cudaGetSymbolAddress of the scratch array failed");
+    g_argmin_addr[dev].store(scratch);
+  }
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+    return pm_set_error_c(PM_ERR_CUDA, "pm_predict_argmin_static: cannot read the SM count");
+  // one partial result per (CTA, model); fewer CTAs if the fixed array would overflow
+  const int cap = (int)(STATIC_ARGMIN_BYTES / ((size_t)M * sizeof(ArgPart)));
+  const int np = std::min(4 * sms, cap);
+  if (np < 1) return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: M too large for the scratch array");
+  if (launch_argmin_parts(d_F, R, k, d_W, M, scratch, np, d_arg, d_min, (cudaStream_t)stream) != cudaSuccess)
+    return pm_set_error_c(PM_ERR_CUDA, "pm_predict_argmin_static: kernel launch failed");
+  return PM_OK;
+}
