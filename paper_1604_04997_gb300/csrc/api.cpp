@@ -261,6 +261,19 @@ extern "C" pm_status pm_predict_argmin(pm_ctx *c, const int64_t *F, int64_t R, i
   return PM_OK;
 }
 
+// Tensor-core path (three-term bf16 split, FP32 accumulation): T, or per-model argmin.
+pm_status pm_predict_bf16x3(pm_ctx *c, const int64_t *F, int64_t R, int k, const double *W, int M, double *T,
+                            int64_t *arg, double *mn, void *stream) {
+  if (k != 32 || M > 64) return pm_set_error(PM_ERR_INVALID_ARG, "PM_PREC_BF16X3 needs k == 32 and M <= 64");
+  void *scr = nullptr;
+  if (arg) {
+    pm_status s = ctx_scratch(c, pmd::tc_argmin_scratch_bytes(M, c->n_sms), &scr);
+    if (s) return s;
+  }
+  CU(pmd::launch_predict_tc(F, R, k, W, M, T, arg, mn, scr, c->n_sms, c->d_status, (cudaStream_t)stream));
+  return PM_OK;
+}
+
 // ------------------------------------------------------------------------------------- batched eval+predict+top-k
 
 extern "C" pm_status pm_eval_predict_topk(pm_ctx *c, const int32_t *tables, const int32_t *var_off,

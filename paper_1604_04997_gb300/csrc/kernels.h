@@ -49,6 +49,12 @@ int argmin_parts();
 cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
                                   void *scratch, int64_t *arg, double *mn, cudaStream_t st);
 
+// predict_tc.cu (tensor cores, three-term bf16 split)
+int tc_parts(int sms);
+size_t tc_argmin_scratch_bytes(int M, int sms);
+cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *W, int M, double *T, int64_t *arg,
+                              double *mn, void *scratch, int sms, int *status, cudaStream_t st);
+
 // fit.cu
 struct FitHost {            // pinned host buffers filled by the fit (per model)
   int *info;                // [M][4] rank, zero columns, rank deficient, dropped-direction mask

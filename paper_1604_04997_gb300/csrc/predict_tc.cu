@@ -1,0 +1,327 @@
+// Reduced-precision prediction on the fifth-generation tensor cores:
+//   T = F W^T   (F int64 [R][32] counts, W fp64 [M <= 64][32] weights)   (Sec. 2)
+//
+// Each count and each weight is rounded to FP32 (24 bits) and split exactly into
+// three bf16 parts, x = x1 + x2 + x3.  The six products x1 y1, x1 y2, x2 y1, x1 y3,
+// x2 y2, x3 y1 carry every term down to 2^-24 of |x y|; they are issued as 12
+// tcgen05.mma instructions (M = 128 rows, N = 64 models, K = 16) accumulating in
+// FP32 in tensor memory.  Relative error <= ~2^-21 of sum_i |F_ri W_mi|.
+//
+// One CTA (4 warps) owns a 128-row tile at a time (persistent over tiles).  The
+// int64 -> float conversion uses integer operations and FP32 adds only (the
+// 64-bit conversion instructions run on the FP64 pipe of this GPU).  Operands are
+// written to shared memory in the no-swizzle K-major core-matrix layout (8 rows x
+// 16 bytes per core matrix), made visible to the tensor core with a proxy fence,
+// and the MMAs are issued by one thread and committed to an mbarrier.  Every
+// mbarrier wait is bounded; on timeout the kernel records ST_TIMEOUT and stops.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "eval_common.cuh"
+#include "kernels.h"
+
+namespace pmd {
+
+constexpr int TC_ROWS = 128;      // MMA M
+constexpr int TC_N = 64;          // MMA N (models, padded)
+constexpr int TC_K = 32;          // features
+constexpr int TC_THREADS = 128;
+constexpr uint32_t TC_A_BYTES = TC_ROWS * TC_K * 2;   // one bf16 split of a row tile: 8 KB
+constexpr uint32_t TC_B_BYTES = TC_N * TC_K * 2;      // one bf16 split of the weights: 4 KB
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // give up an mbarrier wait after 2 s
+
+// instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, N = 64, M = 128
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                              ((uint32_t)(TC_ROWS >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, k) in the no-swizzle K-major layout: core matrices of
+// 8 rows x 8 elements (128 B), the 4 k-groups of a row group contiguous (LBO = 128 B),
+// row groups 512 B apart (SBO = 512 B)
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 512 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor (no swizzle)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((128u >> 4) & 0x3FFFu) << 16;   // leading (K) byte offset
+  d |= (uint64_t)((512u >> 4) & 0x3FFFu) << 32;   // stride (M/N) byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Exact float -> double bit pattern with integer operations (the conversion
+// instruction would run on the FP64 pipe).
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint64_t sign = (uint64_t)(u >> 31) << 63;
+  const uint32_t e = (u >> 23) & 0xFF, m = u & 0x7FFFFF;
+  uint64_t bits;
+  if (e == 0xFF) bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);          // inf / nan
+  else if (e != 0) bits = sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)m << 29);  // normal: 1023 - 127 = 896
+  else if (m == 0) bits = sign;                                                   // zero
+  else {                                                                           // subnormal float
+    const int lz = __clz(m) - 8;                                                   // leading zeros in 23 bits
+    bits = sign | ((uint64_t)(897 - lz - 1) << 52) | ((uint64_t)((m << (lz + 1)) & 0x7FFFFF) << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// 32 consecutive fp32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Exact 23-bit chunks to float without conversion instructions: (2^23 + x) as float minus 2^23.
+__device__ __forceinline__ float chunk_to_float(uint32_t x) {
+  return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.0f);
+}
+
+// int64 -> nearest-ish float (|error| <= 2^-23 relative) using integer ops and FP32 adds.
+__device__ __forceinline__ float i64_to_float(int64_t v) {
+  const bool neg = v < 0;
+  const uint64_t a = neg ? (uint64_t)(-v) : (uint64_t)v;
+  const float c0 = chunk_to_float((uint32_t)(a & 0x7FFFFFu));
+  const float c1 = chunk_to_float((uint32_t)((a >> 23) & 0x7FFFFFu));
+  const float c2 = chunk_to_float((uint32_t)((a >> 46) & 0x7FFFFFu));
+  const float f = __fmaf_rn(c2, 70368744177664.0f, __fmaf_rn(c1, 8388608.0f, c0));   // 2^46, 2^23
+  return neg ? -f : f;
+}
+
+// x = x1 + x2 + x3 exactly for a 24-bit float x
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &b1, __nv_bfloat16 &b2, __nv_bfloat16 &b3) {
+  b1 = __float2bfloat16_rn(x);
+  const float r1 = __fsub_rn(x, __bfloat162float(b1));
+  b2 = __float2bfloat16_rn(r1);
+  const float r2 = __fsub_rn(r1, __bfloat162float(b2));
+  b3 = __float2bfloat16_rn(r2);
+}
+
+// mode 0: write T (fp64 [R][M]);  mode 1: per-model running argmin -> part[blockIdx][M]
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__restrict__ F, int64_t R,
+                                                            const double *__restrict__ W, int M,
+                                                            double *__restrict__ T, double *__restrict__ part_t,
+                                                            int64_t *__restrict__ part_r, int *status) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *sA = smem;                              // 3 splits x 8 KB
+  uint8_t *sB = smem + 3 * TC_A_BYTES;             // 3 splits x 4 KB
+  float *stage = (float *)(sB + 3 * TC_B_BYTES);   // [128 rows][64 + 1] for the argmin epilogue
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights: three bf16 splits, K-major, models >= M are zero
+  for (int i = tid; i < TC_N * TC_K; i += TC_THREADS) {
+    const int n = i / TC_K, k = i - n * TC_K;
+    const float w = n < M ? __double2float_rn(W[(int64_t)n * TC_K + k]) : 0.f;
+    __nv_bfloat16 b1, b2, b3;
+    split3(w, b1, b2, b3);
+    const uint32_t o = kmajor_off(n, k);
+    *(__nv_bfloat16 *)(sB + o) = b1;
+    *(__nv_bfloat16 *)(sB + TC_B_BYTES + o) = b2;
+    *(__nv_bfloat16 *)(sB + 2 * TC_B_BYTES + o) = b3;
+  }
+  if (tid == 0) {
+    s_abort = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
+                 "r"(TC_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+  const uint32_t tmem = tmem_base;
+
+  float best_t = __int_as_float(0x7f800000);   // argmin mode: model tid % 64, rows of half tid / 64
+  int64_t best_r = INT64_MAX;
+  uint32_t phase = 0;
+  const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * TC_ROWS;
+    // operands: counts -> float -> three exact bf16 splits, K-major core matrices
+    for (int j = 0; j < TC_ROWS * TC_K / TC_THREADS; j++) {
+      const int e = tid + j * TC_THREADS;
+      const int row = e / TC_K, k = e - row * TC_K;
+      const int64_t v = r0 + row < R ? F[(r0 + row) * TC_K + k] : 0;
+      __nv_bfloat16 b1, b2, b3;
+      split3(i64_to_float(v), b1, b2, b3);
+      const uint32_t o = kmajor_off(row, k);
+      *(__nv_bfloat16 *)(sA + o) = b1;
+      *(__nv_bfloat16 *)(sA + TC_A_BYTES + o) = b2;
+      *(__nv_bfloat16 *)(sA + 2 * TC_A_BYTES + o) = b3;
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+      // products x1y1, x1y2, x2y1, x1y3, x2y2, x3y1, each over K = 32 in two K = 16 steps
+      const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+      uint32_t acc = 0;
+#pragma unroll
+      for (int p = 0; p < 6; p++)
+#pragma unroll
+        for (int kc = 0; kc < 2; kc++) {
+          const uint64_t ad = sdesc(smem_addr(sA + pa[p] * TC_A_BYTES + kc * 256));
+          const uint64_t bd = sdesc(smem_addr(sB + pb[p] * TC_B_BYTES + kc * 256));
+          tc_mma(tmem, ad, bd, acc);
+          acc = 1;
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+          smem_addr(&mbar)));
+    }
+    // bounded wait for the MMAs of this tile; the give-up decision is taken by the whole CTA
+    int timed_out = 0;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try(smem_addr(&mbar), phase)) {
+      if (globaltimer() - t0 > TC_WAIT_NS) { timed_out = 1; break; }
+    }
+    phase ^= 1;
+    if (__syncthreads_or(timed_out)) { if (tid == 0) s_abort = 1; break; }
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows 32w + lane of the tile
+    float acc[64];
+    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+    tmem_ld32(ta, acc);
+    tmem_ld32(ta + 32, acc + 32);
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+    const int64_t row = r0 + warp * 32 + lane;
+    if (MODE == 0) {
+      if (row < R) {
+        double *out = T + row * M;
+        if (M == TC_N) {
+#pragma unroll
+          for (int m = 0; m < TC_N; m += 2) *(double2 *)(out + m) = make_double2(f32_to_f64(acc[m]), f32_to_f64(acc[m + 1]));
+        } else {
+#pragma unroll
+          for (int m = 0; m < TC_N; m++)
+            if (m < M) out[m] = f32_to_f64(acc[m]);
+        }
+      }
+    } else {
+      float *srow = stage + (warp * 32 + lane) * (TC_N + 1);
+#pragma unroll
+      for (int m = 0; m < TC_N; m++) srow[m] = acc[m];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+    __syncthreads();   // TMEM read and (argmin) staging complete before the next tile
+    if (MODE == 1) {
+      const int m = tid % TC_N, half = tid / TC_N;
+      for (int rr = half * 64; rr < half * 64 + 64; rr++) {
+        if (r0 + rr >= R) break;
+        const float x = stage[rr * (TC_N + 1) + m];
+        if (x < best_t) { best_t = x; best_r = r0 + rr; }   // rows visited in increasing order
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  if (s_abort && tid == 0) atomicOr(status, ST_TIMEOUT);
+  if (MODE == 1) {
+    // combine the two halves of each model, then publish this CTA's partial result
+    float *st = stage;
+    __syncthreads();
+    if (tid >= TC_N) { st[2 * (tid - TC_N)] = best_t; ((int64_t *)(st + 2 * TC_N))[tid - TC_N] = best_r; }
+    __syncthreads();
+    if (tid < TC_N && tid < M) {
+      const float ot = st[2 * tid];
+      const int64_t orr = ((int64_t *)(st + 2 * TC_N))[tid];
+      if (ot < best_t || (ot == best_t && orr < best_r)) { best_t = ot; best_r = orr; }
+      part_t[(int64_t)blockIdx.x * M + tid] = (double)best_t;
+      part_r[(int64_t)blockIdx.x * M + tid] = best_r;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N));
+}
+
+__global__ void k_argmin_tc_reduce(const double *__restrict__ pt, const int64_t *__restrict__ pr, int n_part, int M,
+                                   int64_t *arg, double *mn) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  double bt = pt[m];
+  int64_t br = pr[m];
+  for (int p = 1; p < n_part; p++) {
+    const double t = pt[(int64_t)p * M + m];
+    const int64_t r = pr[(int64_t)p * M + m];
+    if (t < bt || (t == bt && r < br)) { bt = t; br = r; }
+  }
+  arg[m] = br == INT64_MAX ? -1 : br;
+  mn[m] = bt;
+}
+
+static size_t tc_smem(int mode) {
+  return 3 * TC_A_BYTES + 3 * TC_B_BYTES + (mode == 1 ? (size_t)TC_ROWS * (TC_N + 1) * 4 : 0) + 1024;
+}
+
+int tc_parts(int sms) { return sms * 2; }
+size_t tc_argmin_scratch_bytes(int M, int sms) { return (size_t)tc_parts(sms) * M * 16; }
+
+cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *W, int M, double *T, int64_t *arg,
+                              double *mn, void *scratch, int sms, int *status, cudaStream_t st) {
+  if (k != TC_K || M > TC_N || M <= 0) return cudaErrorInvalidValue;
+  const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)tc_parts(sms)));
+  if (!arg) {
+    const size_t sm = tc_smem(0);
+    cudaFuncSetAttribute(k_predict_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_predict_tc<0><<<grid, TC_THREADS, sm, st>>>(F, R, W, M, T, nullptr, nullptr, status);
+  } else {
+    const size_t sm = tc_smem(1);
+    double *pt = (double *)scratch;
+    int64_t *pr = (int64_t *)((char *)scratch + (size_t)tc_parts(sms) * M * 8);
+    cudaFuncSetAttribute(k_predict_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_predict_tc<1><<<grid, TC_THREADS, sm, st>>>(F, R, W, M, nullptr, pt, pr, status);
+    k_argmin_tc_reduce<<<(M + 63) / 64, 64, 0, st>>>(pt, pr, grid, M, arg, mn);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pmd

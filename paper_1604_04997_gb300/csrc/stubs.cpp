@@ -2,10 +2,6 @@
 #include "pm.h"
 #include "pm_internal.h"
 
-pm_status pm_predict_bf16x3(pm_ctx *, const int64_t *, int64_t, int, const double *, int, double *, int64_t *,
-                            double *, void *) {
-  return pm_set_error(PM_ERR_UNSUPPORTED, "PM_PREC_BF16X3 is not available in this build");
-}
 extern "C" pm_status pm_serve_set_weights(pm_ctx *, const double *, int32_t) {
   return pm_set_error(PM_ERR_UNSUPPORTED, "serving is not available in this build");
 }
