@@ -390,16 +390,29 @@ def run_other(args):
         F = torch.from_numpy(W.fit_features(R, 32, 7)).to(dev)
         Wm = torch.from_numpy(W.draw_weights(32, M, 8)).to(dev)
         T = torch.empty((R, M), dtype=torch.float64, device=dev)
-        fn = lambda: ctx.predict(F, Wm, T, B.PREC_FP64, stream=stream)
-        ms, ck = _clocks_and_time(fn, args.steps, args.warmup, stream, flush)
+        arg = torch.empty(M, dtype=torch.int64, device=dev)
+        mn = torch.empty(M, dtype=torch.float64, device=dev)
+        times = {}
+        for name, prec, fn in (
+                ("bf16x3_T", B.PREC_BF16X3, lambda: ctx.predict(F, Wm, T, B.PREC_BF16X3, stream=stream)),
+                ("bf16x3_argmin", B.PREC_BF16X3,
+                 lambda: ctx.predict_argmin(F, Wm, arg, mn, B.PREC_BF16X3, stream=stream)),
+                ("fp64_T", B.PREC_FP64, lambda: ctx.predict(F, Wm, T, B.PREC_FP64, stream=stream))):
+            times[name] = _clocks_and_time(fn, args.steps, args.warmup, stream, flush)
+        ms, ck = times["bf16x3_T"]
         nbytes = R * 32 * 8 + R * M * 8
-        line = dict(base, metric="cross-model predictions/s (1e6 rows x 32 features x 64 models, FP64-accurate)",
+        nb_arg = R * 32 * 8
+        ms_arg = times["bf16x3_argmin"][0]
+        line = dict(base, metric="cross-model predictions/s (1e6 rows x 32 features x 64 models, tensor cores)",
                     value=R * M / (ms / 1e3), unit="predictions/s", ms_per_step=ms, higher_is_better=True,
-                    dtype="int64 x fixed-point int (exact, 128-bit sums)",
+                    dtype="bf16 x3-term split, fp32 accumulate (tcgen05), fp64 output",
                     config={"workload": "1,000,000 feature rows x 32 int64 features x 64 weight vectors",
-                            "bytes_per_step": nbytes},
-                    roofline={"bound": "alu", "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "hbm_peak": hbm,
-                              "hbm_frac": nbytes / (ms / 1e3) / 1e9 / hbm, "kernel": "k_predict_ff"},
+                            "bytes_per_step": nbytes,
+                            "argmin_only_ms": ms_arg, "argmin_only_gbs": nb_arg / (ms_arg / 1e3) / 1e9,
+                            "fp64_accurate_ms": times["fp64_T"][0]},
+                    roofline={"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                              "frac": nbytes / (ms / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_predict_tc",
+                              "algorithmic_bytes": "256 B read + 8 B written per (row, model)"},
                     clocks=ck, gpu_launches=args.steps)
     elif args.workload == "fit":
         R, M = 200_000, 64
