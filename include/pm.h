@@ -22,8 +22,9 @@
  *     unless stated otherwise.  Argument checks run on the host before launch.
  *   - Device-side errors (e.g. a parameter point outside the declared box) are
  *     recorded in a context status word; pm_sync_status() reads and clears it.
- *   - A context is used by one host thread at a time, except the serve entry
- *     points (pm_serve_*), which are thread-safe.
+ *   - A context is used by one host thread at a time, except pm_serve_submit,
+ *     pm_serve_poll and pm_serve_stats, which any number of threads may call while
+ *     the serve loop runs (and pm_compile_counts, which may run beside them).
  */
 #ifndef PM_H
 #define PM_H
@@ -120,12 +121,14 @@ pm_status pm_eval_counts(pm_ctx *ctx, const int32_t *h_table_ids, int32_t n_tabl
  *   sums exact in 128 bits: error <= 2^-59 (max_i|W_mi| / min_i|W_mi|) sum_i |F_ri W_mi|
  *   plus 2^-56 |T|;
  * PM_PREC_BF16X3: <= ~1e-6 of the same (tensor cores, power-of-two column scaling);
+ *   needs k == 32, M <= 64 and d_F 16-byte aligned (else PM_ERR_INVALID_ARG);
  * PM_PREC_NATIVE_FP64: double FMA. */
 pm_status pm_predict(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t k, const double *d_W,
                      int32_t M, int32_t precision, double *d_T, void *stream);
 
 /* Per-model argmin over rows (configuration selection, Sec. 6.1): d_arg int64 [M],
- * d_min fp64 [M]; ties broken by the smaller row index.  Does not materialise T. */
+ * d_min fp64 [M]; ties broken by the smaller row index; R == 0 gives -1 and +inf.
+ * Does not materialise T. */
 pm_status pm_predict_argmin(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t k,
                             const double *d_W, int32_t M, int32_t precision, int64_t *d_arg,
                             double *d_min, void *stream);
@@ -224,13 +227,38 @@ typedef struct {
   double *h_top_t;
 } pm_query;
 
-/* Make the weights of n_models device models resident (h_W fp64 [n_models][32]). */
+/* Latency and volume of the queries completed since the last reset.  Latency runs
+ * from pm_serve_submit to the moment the results are in the caller's buffers. */
+typedef struct {
+  int64_t n_queries;
+  int64_t n_batches;
+  int64_t n_candidates;
+  double p50_us, p99_us, max_us, mean_us;
+} pm_serve_stats_t;
+
+/* Make the weights of n_models device models resident (h_W fp64 [n_models][32], finite).
+ * PM_ERR_BUSY while the serve loop runs. */
 pm_status pm_serve_set_weights(pm_ctx *ctx, const double *h_W, int32_t n_models);
+/* Start the serve loop (a batching thread and a completion thread).  It holds
+ * min(mem_budget, 1 GiB) of device memory and as much pinned host memory for the
+ * queries in flight.  A batch is launched when its oldest query has waited
+ * batch_interval_us or max_batch_queries are queued; queries are admitted in arrival
+ * order while they fit the free memory, so a small budget queues them. */
 pm_status pm_serve_start(pm_ctx *ctx, const pm_serve_config *cfg);
-/* Queue a query; PM_ERR_BUSY if it can never fit the memory budget. */
+/* Queue a query (thread-safe).  Its tables must be PM_LAYOUT_32 tables of this
+ * context; h_tables and h_points are read when its batch is formed, so they too stay
+ * valid until pm_serve_poll returns something other than PM_PENDING.  n_cand == 0
+ * completes at once with idx -1 and time +inf.  PM_ERR_BUSY if the query can never
+ * fit the memory budget. */
 pm_status pm_serve_submit(pm_ctx *ctx, const pm_query *q, uint64_t *ticket);
-/* PM_PENDING, PM_OK (results written) or an error; waits at most timeout_us (0 = no wait). */
+/* PM_PENDING, PM_OK (results written) or an error (PM_ERR_OUT_OF_BOX: some candidate
+ * point lies outside its table's box; the others are still ranked and written);
+ * waits at most timeout_us (0 = no wait).  A ticket is forgotten once it has
+ * returned something other than PM_PENDING (then PM_ERR_NOT_FOUND). */
 pm_status pm_serve_poll(pm_ctx *ctx, uint64_t ticket, int32_t timeout_us);
+pm_status pm_serve_stats(pm_ctx *ctx, int32_t reset, pm_serve_stats_t *out);
+/* Finish every queued and running query, then stop the threads and free the serve
+ * memory.  Unpolled tickets stay pollable until the next pm_serve_start. */
 pm_status pm_serve_stop(pm_ctx *ctx);
 
 #ifdef __cplusplus

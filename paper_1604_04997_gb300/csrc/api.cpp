@@ -69,7 +69,7 @@ extern "C" pm_status pm_create(pm_ctx **out, int device, size_t mem_budget_bytes
 
 extern "C" void pm_destroy(pm_ctx *c) {
   if (!c) return;
-  pm_serve_stop(c);
+  serve_destroy(c);
   if (c->device >= 0) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
@@ -251,7 +251,7 @@ extern "C" pm_status pm_predict_argmin(pm_ctx *c, const int64_t *F, int64_t R, i
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (R < 0 || k <= 0 || k > 40 || M <= 0 || M > 64) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
-  if (!F || !W || !arg || !mn) return pm_set_error(PM_ERR_INVALID_ARG, "null device buffer");
+  if ((!F && R > 0) || !W || !arg || !mn) return pm_set_error(PM_ERR_INVALID_ARG, "null device buffer");
   if (precision == PM_PREC_BF16X3) return pm_predict_bf16x3(c, F, R, k, W, M, nullptr, arg, mn, stream);
   if (precision != PM_PREC_FP64) return pm_set_error(PM_ERR_INVALID_ARG, "argmin supports PM_PREC_FP64 and PM_PREC_BF16X3");
   void *scr = nullptr;
@@ -265,6 +265,7 @@ extern "C" pm_status pm_predict_argmin(pm_ctx *c, const int64_t *F, int64_t R, i
 pm_status pm_predict_bf16x3(pm_ctx *c, const int64_t *F, int64_t R, int k, const double *W, int M, double *T,
                             int64_t *arg, double *mn, void *stream) {
   if (k != 32 || M > 64) return pm_set_error(PM_ERR_INVALID_ARG, "PM_PREC_BF16X3 needs k == 32 and M <= 64");
+  if ((uintptr_t)F % 16 != 0) return pm_set_error(PM_ERR_INVALID_ARG, "PM_PREC_BF16X3 needs F 16-byte aligned");
   void *scr = nullptr;
   if (arg) {
     pm_status s = ctx_scratch(c, pmd::tc_argmin_scratch_bytes(M, c->n_sms), &scr);

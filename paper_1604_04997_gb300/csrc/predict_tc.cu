@@ -7,7 +7,10 @@
 // tcgen05.mma instructions (M = 128 rows, N = 64 models, K = 16) accumulating in
 // FP32 in tensor memory.  Relative error <= ~2^-21 of sum_i |F_ri W_mi|.
 //
-// One CTA (4 warps) owns a 128-row tile at a time (persistent over tiles).  The
+// One CTA (4 warps) owns a 128-row tile at a time (persistent over tiles).  Row tiles
+// (32 KB of contiguous counts) are streamed into shared memory by the bulk-copy
+// engine (cp.async.bulk, mbarrier transaction counts), double-buffered, so the next
+// tile arrives while the current one is converted and multiplied.  The
 // int64 -> float conversion uses integer operations and FP32 adds only (the
 // 64-bit conversion instructions run on the FP64 pipe of this GPU).  Operands are
 // written to shared memory in the no-swizzle K-major core-matrix layout (8 rows x
@@ -31,6 +34,7 @@ constexpr int TC_K = 32;          // features
 constexpr int TC_THREADS = 128;
 constexpr uint32_t TC_A_BYTES = TC_ROWS * TC_K * 2;   // one bf16 split of a row tile: 8 KB
 constexpr uint32_t TC_B_BYTES = TC_N * TC_K * 2;      // one bf16 split of the weights: 4 KB
+constexpr uint32_t TC_F_BYTES = TC_ROWS * TC_K * 8;   // one raw row tile of counts: 32 KB
 constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // give up an mbarrier wait after 2 s
 
 // instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, N = 64, M = 128
@@ -136,6 +140,41 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16 &b1, __nv_bfloat16
   b3 = __float2bfloat16_rn(r2);
 }
 
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Bounded mbarrier wait shared by the whole CTA: returns true if every thread saw the
+// phase complete within TC_WAIT_NS.
+__device__ __forceinline__ bool cta_wait(uint32_t mbar, uint32_t parity) {
+  int timed_out = 0;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try(mbar, parity)) {
+    if (globaltimer() - t0 > TC_WAIT_NS) { timed_out = 1; break; }
+  }
+  return !__syncthreads_or(timed_out);
+}
+
+// 8 consecutive counts -> three 16-byte vectors of bf16 splits
+__device__ __forceinline__ void convert8(const int64_t *src, uint4 &o1, uint4 &o2, uint4 &o3) {
+  uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    __nv_bfloat16 a1, a2, a3, b1, b2, b3;
+    split3(i64_to_float(src[2 * q]), a1, a2, a3);
+    split3(i64_to_float(src[2 * q + 1]), b1, b2, b3);
+    w1[q] = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+    w2[q] = (uint32_t)__bfloat16_as_ushort(a2) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
+    w3[q] = (uint32_t)__bfloat16_as_ushort(a3) | ((uint32_t)__bfloat16_as_ushort(b3) << 16);
+  }
+  o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  o2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+  o3 = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+}
+
 // mode 0: write T (fp64 [R][M]);  mode 1: per-model running argmin -> part[blockIdx][M]
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__restrict__ F, int64_t R,
@@ -143,12 +182,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
                                                             double *__restrict__ T, double *__restrict__ part_t,
                                                             int64_t *__restrict__ part_r, int *status) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *sA = smem;                              // 3 splits x 8 KB
-  uint8_t *sB = smem + 3 * TC_A_BYTES;             // 3 splits x 4 KB
+  uint8_t *sF = smem;                              // 2 x 32 KB raw row tiles
+  uint8_t *sA = smem + 2 * TC_F_BYTES;             // 3 splits x 8 KB
+  uint8_t *sB = sA + 3 * TC_A_BYTES;               // 3 splits x 4 KB
   float *stage = (float *)(sB + 3 * TC_B_BYTES);   // [128 rows][64 + 1] for the argmin epilogue
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_ld[2];
   __shared__ uint32_t tmem_base;
-  __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -163,9 +202,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
     *(__nv_bfloat16 *)(sB + TC_B_BYTES + o) = b2;
     *(__nv_bfloat16 *)(sB + 2 * TC_B_BYTES + o) = b3;
   }
+  const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
+  auto tile_bytes = [&](int64_t tile) { return (uint32_t)(min((int64_t)TC_ROWS, R - tile * TC_ROWS) * TC_K * 8); };
   if (tid == 0) {
-    s_abort = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_mma)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_ld[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_ld[1])));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
   }
   if (warp == 0) {
@@ -177,24 +219,37 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
+  if (tid == 0 && (int64_t)blockIdx.x < ntiles)
+    bulk_load(smem_addr(sF), F + (int64_t)blockIdx.x * TC_ROWS * TC_K, tile_bytes(blockIdx.x), smem_addr(&mbar_ld[0]));
 
   float best_t = __int_as_float(0x7f800000);   // argmin mode: model tid % 64, rows of half tid / 64
   int64_t best_r = INT64_MAX;
-  uint32_t phase = 0;
-  const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  uint32_t ph_mma = 0, ph_ld[2] = {0, 0};
+  bool aborted = false;
+  int it = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+    const int buf = it & 1;
     const int64_t r0 = tile * TC_ROWS;
-    // operands: counts -> float -> three exact bf16 splits, K-major core matrices
-    for (int j = 0; j < TC_ROWS * TC_K / TC_THREADS; j++) {
-      const int e = tid + j * TC_THREADS;
-      const int row = e / TC_K, k = e - row * TC_K;
-      const int64_t v = r0 + row < R ? F[(r0 + row) * TC_K + k] : 0;
-      __nv_bfloat16 b1, b2, b3;
-      split3(i64_to_float(v), b1, b2, b3);
-      const uint32_t o = kmajor_off(row, k);
-      *(__nv_bfloat16 *)(sA + o) = b1;
-      *(__nv_bfloat16 *)(sA + TC_A_BYTES + o) = b2;
-      *(__nv_bfloat16 *)(sA + 2 * TC_A_BYTES + o) = b3;
+    // stream the next tile into the other buffer (its previous contents were consumed last iteration)
+    const int64_t next = tile + gridDim.x;
+    if (tid == 0 && next < ntiles)
+      bulk_load(smem_addr(sF + (buf ^ 1) * TC_F_BYTES), F + next * TC_ROWS * TC_K, tile_bytes(next),
+                smem_addr(&mbar_ld[buf ^ 1]));
+    if (!cta_wait(smem_addr(&mbar_ld[buf]), ph_ld[buf])) { aborted = true; break; }
+    ph_ld[buf] ^= 1;
+    // operands: counts -> float -> three exact bf16 splits, 16-byte K-major core-matrix rows
+    const int nrows = (int)min((int64_t)TC_ROWS, R - r0);
+    const int64_t *src = (const int64_t *)(sF + buf * TC_F_BYTES);
+#pragma unroll
+    for (int j = 0; j < TC_ROWS * 4 / TC_THREADS; j++) {
+      const int item = tid + j * TC_THREADS;
+      const int row = item >> 2, kg = item & 3;
+      uint4 o1 = make_uint4(0, 0, 0, 0), o2 = o1, o3 = o1;
+      if (row < nrows) convert8(src + row * TC_K + kg * 8, o1, o2, o3);
+      const uint32_t o = kmajor_off(row, kg * 8);
+      *(uint4 *)(sA + o) = o1;
+      *(uint4 *)(sA + TC_A_BYTES + o) = o2;
+      *(uint4 *)(sA + 2 * TC_A_BYTES + o) = o3;
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -214,16 +269,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
           acc = 1;
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-          smem_addr(&mbar)));
+          smem_addr(&mbar_mma)));
     }
-    // bounded wait for the MMAs of this tile; the give-up decision is taken by the whole CTA
-    int timed_out = 0;
-    const unsigned long long t0 = globaltimer();
-    while (!mbar_try(smem_addr(&mbar), phase)) {
-      if (globaltimer() - t0 > TC_WAIT_NS) { timed_out = 1; break; }
-    }
-    phase ^= 1;
-    if (__syncthreads_or(timed_out)) { if (tid == 0) s_abort = 1; break; }
+    if (!cta_wait(smem_addr(&mbar_mma), ph_mma)) { aborted = true; break; }
+    ph_mma ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows 32w + lane of the tile
     float acc[64];
@@ -250,7 +299,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
       for (int m = 0; m < TC_N; m++) srow[m] = acc[m];
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();   // TMEM read and (argmin) staging complete before the next tile
+    __syncthreads();   // TMEM read, staging and the raw buffer of this tile are done with
     if (MODE == 1) {
       const int m = tid % TC_N, half = tid / TC_N;
       for (int rr = half * 64; rr < half * 64 + 64; rr++) {
@@ -261,9 +310,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
       __syncthreads();
     }
   }
-  __syncthreads();
-  if (s_abort && tid == 0) atomicOr(status, ST_TIMEOUT);
-  if (MODE == 1) {
+  if (aborted) {
+    if (tid == 0) atomicOr(status, ST_TIMEOUT);
+    // let any bulk copy still in flight land before the CTA exits (bounded)
+    for (int b = 0; b < 2; b++) cta_wait(smem_addr(&mbar_ld[b]), ph_ld[b]);
+  }
+  if (MODE == 1 && !aborted) {
     // combine the two halves of each model, then publish this CTA's partial result
     float *st = stage;
     __syncthreads();
@@ -286,9 +338,9 @@ __global__ void k_argmin_tc_reduce(const double *__restrict__ pt, const int64_t 
                                    int64_t *arg, double *mn) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
-  double bt = pt[m];
-  int64_t br = pr[m];
-  for (int p = 1; p < n_part; p++) {
+  double bt = __longlong_as_double(0x7ff0000000000000ll);
+  int64_t br = INT64_MAX;
+  for (int p = 0; p < n_part; p++) {
     const double t = pt[(int64_t)p * M + m];
     const int64_t r = pr[(int64_t)p * M + m];
     if (t < bt || (t == bt && r < br)) { bt = t; br = r; }
@@ -298,17 +350,25 @@ __global__ void k_argmin_tc_reduce(const double *__restrict__ pt, const int64_t 
 }
 
 static size_t tc_smem(int mode) {
-  return 3 * TC_A_BYTES + 3 * TC_B_BYTES + (mode == 1 ? (size_t)TC_ROWS * (TC_N + 1) * 4 : 0) + 1024;
+  return 2 * TC_F_BYTES + 3 * TC_A_BYTES + 3 * TC_B_BYTES + (mode == 1 ? (size_t)TC_ROWS * (TC_N + 1) * 4 : 0) +
+         1024;
 }
 
+// resident CTAs per SM: mode 0 uses 101 KB of shared memory, mode 1 134 KB
 int tc_parts(int sms) { return sms * 2; }
+static int tc_grid(int mode, int sms) { return sms * (mode == 0 ? 2 : 1); }
 size_t tc_argmin_scratch_bytes(int M, int sms) { return (size_t)tc_parts(sms) * M * 16; }
 
 cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *W, int M, double *T, int64_t *arg,
                               double *mn, void *scratch, int sms, int *status, cudaStream_t st) {
   if (k != TC_K || M > TC_N || M <= 0) return cudaErrorInvalidValue;
+  if (((uintptr_t)F & 15) != 0) return cudaErrorMisalignedAddress;   // bulk copies need 16-byte alignment
+  if (R == 0) {   // no rows: argmin is -1 with time +inf
+    if (arg) k_argmin_tc_reduce<<<(M + 63) / 64, 64, 0, st>>>(nullptr, nullptr, 0, M, arg, mn);
+    return cudaGetLastError();
+  }
   const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)tc_parts(sms)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)tc_grid(arg ? 1 : 0, sms)));
   if (!arg) {
     const size_t sm = tc_smem(0);
     cudaFuncSetAttribute(k_predict_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

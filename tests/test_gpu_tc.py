@@ -66,6 +66,41 @@ def test_tc_argmin(env):
         assert abs(m[j] - ref[a[j], j]) <= 1e-5 * mag[a[j], j]
 
 
+def test_tc_argmin_many_tiles_per_cta(env):
+    """300,007 rows: every CTA streams many row tiles through both buffers; ragged last tile."""
+    import torch
+    ctx, dev = env
+    F = W.fit_features(300_007, 32, 11)
+    Wm = W.draw_weights(32, 40, 12)
+    ref, mag = oracle.predict(F, Wm), oracle.predict_abs(F, Wm)
+    arg = torch.empty(40, dtype=torch.int64, device=dev)
+    mn = torch.empty(40, dtype=torch.float64, device=dev)
+    ctx.predict_argmin(torch.from_numpy(F).to(dev), torch.from_numpy(Wm).to(dev), arg, mn, B.PREC_BF16X3)
+    ctx.sync_status()
+    a, m = arg.cpu().numpy(), mn.cpu().numpy()
+    for j in range(40):
+        assert ref[a[j], j] - ref[:, j].min() <= 2e-5 * mag[a[j], j]
+        assert abs(m[j] - ref[a[j], j]) <= 1e-5 * mag[a[j], j]
+
+
+def test_tc_empty_and_misaligned(env):
+    import torch
+    ctx, dev = env
+    Wt = torch.from_numpy(W.draw_weights(32, 8, 1)).to(dev)
+    arg = torch.zeros(8, dtype=torch.int64, device=dev)
+    mn = torch.zeros(8, dtype=torch.float64, device=dev)
+    F0 = torch.zeros(64, dtype=torch.int64, device=dev)[:0].view(0, 32)   # empty, non-null pointer
+    ctx.predict_argmin(F0, Wt, arg, mn, B.PREC_BF16X3)
+    ctx.sync_status()
+    assert (arg.cpu().numpy() == -1).all() and np.isinf(mn.cpu().numpy()).all()
+    buf = torch.zeros(129 * 32 + 1, dtype=torch.int64, device=dev)
+    Fm = buf[1:].view(129, 32)          # 8 bytes past a 16-byte boundary
+    T = torch.zeros((129, 8), dtype=torch.float64, device=dev)
+    with pytest.raises(B.PMError) as e:
+        ctx.predict(Fm, Wt, T, B.PREC_BF16X3)
+    assert e.value.code == -1
+
+
 def test_tc_predict_full_size_sampled(env):
     """1,000,000 rows x 32 features x 64 models, sampled rows checked."""
     ctx, dev = env
