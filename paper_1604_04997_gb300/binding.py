@@ -56,6 +56,12 @@ class Query(ctypes.Structure):
                 ("h_top_idx", ctypes.c_void_p), ("h_top_t", ctypes.c_void_p)]
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("n_queries", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -83,6 +89,7 @@ def lib():
             "pm_serve_start": ([vp, ctypes.POINTER(ServeConfig)], i32),
             "pm_serve_submit": ([vp, ctypes.POINTER(Query), ctypes.POINTER(ctypes.c_uint64)], i32),
             "pm_serve_poll": ([vp, ctypes.c_uint64, i32], i32),
+            "pm_serve_stats": ([vp, i32, ctypes.POINTER(ServeStats)], i32),
             "pm_serve_stop": ([vp], i32),
         }
         for name, (args, res) in sig.items():
@@ -98,7 +105,7 @@ def exported_symbols() -> Sequence[str]:
             "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
             "pm_eval_predict_topk", "pm_tune",
             "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
-            "pm_serve_poll", "pm_serve_stop")
+            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop")
 
 
 def _check(rc: int, ok=(PM_OK,)) -> int:
@@ -229,8 +236,22 @@ class Context:
     def serve_poll(self, ticket: int, timeout_us: int = 0) -> int:
         return _check(lib().pm_serve_poll(self.h, ticket, timeout_us), ok=(PM_OK, PM_PENDING))
 
+    def serve_stats(self, reset: bool = False) -> dict:
+        st = ServeStats()
+        _check(lib().pm_serve_stats(self.h, int(reset), ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServeStats._fields_}
+
     def serve_stop(self):
         _check(lib().pm_serve_stop(self.h))
+
+
+def make_query(model: int, topk: int, tables: np.ndarray, points: np.ndarray, top_idx: np.ndarray,
+               top_t: np.ndarray) -> Query:
+    """A pm_query over host arrays; the caller keeps the arrays alive until the poll."""
+    assert tables.dtype == np.int32 and points.dtype == np.int64 and points.shape[1:] == (4,)
+    assert top_idx.dtype == np.int32 and top_t.dtype == np.float64 and len(top_idx) >= topk
+    return Query(model, topk, len(tables), tables.ctypes.data if len(tables) else None,
+                 points.ctypes.data if len(tables) else None, top_idx.ctypes.data, top_t.ctypes.data)
 
 
 def predict_argmin_static(F, W, arg, mn, stream=None):

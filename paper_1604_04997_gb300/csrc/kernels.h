@@ -55,6 +55,30 @@ size_t tc_argmin_scratch_bytes(int M, int sms);
 cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *W, int M, double *T, int64_t *arg,
                               double *mn, void *scratch, int sms, int *status, cudaStream_t st);
 
+// serve.cu: one batch of queries, all arrays inside one device region
+constexpr int SV_MAX_TOPK = 16;
+struct SQuery {               // 24 bytes
+  int64_t begin;              // first candidate of the query in the batch
+  int32_t n;                  // candidates
+  int32_t model;              // row of models
+  int32_t topk;               // 1..16
+  int32_t pad;
+};
+struct ServeArgs {
+  const uint32_t *arena;      // compiled tables
+  const SQuery *queries;
+  int n_queries;
+  const int2 *blocks;         // per k_serve_eval CTA: (query, chunk of 128 candidates)
+  const uint32_t *cand_off;   // [N] arena word offset of each candidate's table
+  const int64_t *points;      // [N][4]
+  const double *models;       // [n_models][32]
+  int64_t *keys;              // [N] scratch
+  int32_t *q_status;          // [n_queries] status bits
+  int32_t *out_idx;           // [n_queries][16]
+  double *out_t;              // [n_queries][16]
+};
+cudaError_t launch_serve(const ServeArgs &a, int n_blocks, cudaStream_t st);
+
 // fit.cu
 struct FitHost {            // pinned host buffers filled by the fit (per model)
   int *info;                // [M][4] rank, zero columns, rank deficient, dropped-direction mask

@@ -59,6 +59,7 @@ struct pm_ctx {
 };
 
 pm_status pm_set_error(pm_status code, const std::string &m);
+void serve_destroy(pm_ctx *c);   // stops the serve loop and frees its state and resident weights
 pm_status pm_set_error_c(pm_status code, const char *m);
 pm_status ctx_device_guard(pm_ctx *c);
 pm_status ctx_dcopy(pm_ctx *c, const void *h, size_t bytes, void **d);

@@ -7,7 +7,7 @@
 // tcgen05.mma instructions (M = 128 rows, N = 64 models, K = 16) accumulating in
 // FP32 in tensor memory.  Relative error <= ~2^-21 of sum_i |F_ri W_mi|.
 //
-// One CTA (4 warps) owns a 128-row tile at a time (persistent over tiles).  Row tiles
+// One CTA (8 warps) owns a 128-row tile at a time (persistent over tiles).  Row tiles
 // (32 KB of contiguous counts) are streamed into shared memory by the bulk-copy
 // engine (cp.async.bulk, mbarrier transaction counts), double-buffered, so the next
 // tile arrives while the current one is converted and multiplied.  The
@@ -31,7 +31,7 @@ namespace pmd {
 constexpr int TC_ROWS = 128;      // MMA M
 constexpr int TC_N = 64;          // MMA N (models, padded)
 constexpr int TC_K = 32;          // features
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;
 constexpr uint32_t TC_A_BYTES = TC_ROWS * TC_K * 2;   // one bf16 split of a row tile: 8 KB
 constexpr uint32_t TC_B_BYTES = TC_N * TC_K * 2;      // one bf16 split of the weights: 4 KB
 constexpr uint32_t TC_F_BYTES = TC_ROWS * TC_K * 8;   // one raw row tile of counts: 32 KB
@@ -131,15 +131,6 @@ __device__ __forceinline__ float i64_to_float(int64_t v) {
   return neg ? -f : f;
 }
 
-// x = x1 + x2 + x3 exactly for a 24-bit float x
-__device__ __forceinline__ void split3(float x, __nv_bfloat16 &b1, __nv_bfloat16 &b2, __nv_bfloat16 &b3) {
-  b1 = __float2bfloat16_rn(x);
-  const float r1 = __fsub_rn(x, __bfloat162float(b1));
-  b2 = __float2bfloat16_rn(r1);
-  const float r2 = __fsub_rn(r1, __bfloat162float(b2));
-  b3 = __float2bfloat16_rn(r2);
-}
-
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
@@ -158,17 +149,27 @@ __device__ __forceinline__ bool cta_wait(uint32_t mbar, uint32_t parity) {
   return !__syncthreads_or(timed_out);
 }
 
-// 8 consecutive counts -> three 16-byte vectors of bf16 splits
+// packed bf16 pair -> the two floats (low half, high half)
+__device__ __forceinline__ float bf_lo(uint32_t p) { return __uint_as_float(p << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t p) { return __uint_as_float(p & 0xFFFF0000u); }
+
+// two floats -> packed bf16 pair (round to nearest even), x in the low half
+__device__ __forceinline__ uint32_t pack_bf2(float x, float y) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  return *(const uint32_t *)&h;
+}
+
+// 8 consecutive counts -> three 16-byte vectors of exact bf16 splits (x = x1 + x2 + x3)
 __device__ __forceinline__ void convert8(const int64_t *src, uint4 &o1, uint4 &o2, uint4 &o3) {
   uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
   for (int q = 0; q < 4; q++) {
-    __nv_bfloat16 a1, a2, a3, b1, b2, b3;
-    split3(i64_to_float(src[2 * q]), a1, a2, a3);
-    split3(i64_to_float(src[2 * q + 1]), b1, b2, b3);
-    w1[q] = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-    w2[q] = (uint32_t)__bfloat16_as_ushort(a2) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
-    w3[q] = (uint32_t)__bfloat16_as_ushort(a3) | ((uint32_t)__bfloat16_as_ushort(b3) << 16);
+    const longlong2 v = *(const longlong2 *)(src + 2 * q);
+    const float x = i64_to_float(v.x), y = i64_to_float(v.y);
+    w1[q] = pack_bf2(x, y);
+    const float rx = __fsub_rn(x, bf_lo(w1[q])), ry = __fsub_rn(y, bf_hi(w1[q]));
+    w2[q] = pack_bf2(rx, ry);
+    w3[q] = pack_bf2(__fsub_rn(rx, bf_lo(w2[q])), __fsub_rn(ry, bf_hi(w2[q])));
   }
   o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
   o2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
@@ -176,6 +177,9 @@ __device__ __forceinline__ void convert8(const int64_t *src, uint4 &o1, uint4 &o
 }
 
 // mode 0: write T (fp64 [R][M]);  mode 1: per-model running argmin -> part[blockIdx][M]
+//
+// Warps w and w + 4 share TMEM lanes 32 (w % 4) .. +31 (rows of the tile); warp w < 4
+// reads accumulator columns 0..31 (models), warp w + 4 columns 32..63.
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__restrict__ F, int64_t R,
                                                             const double *__restrict__ W, int M,
@@ -185,22 +189,26 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
   uint8_t *sF = smem;                              // 2 x 32 KB raw row tiles
   uint8_t *sA = smem + 2 * TC_F_BYTES;             // 3 splits x 8 KB
   uint8_t *sB = sA + 3 * TC_A_BYTES;               // 3 splits x 4 KB
-  float *stage = (float *)(sB + 3 * TC_B_BYTES);   // [128 rows][64 + 1] for the argmin epilogue
   __shared__ __align__(8) uint64_t mbar_mma, mbar_ld[2];
   __shared__ uint32_t tmem_base;
+  __shared__ float fin_t[TC_THREADS];
+  __shared__ int64_t fin_r[TC_THREADS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // weights: three bf16 splits, K-major, models >= M are zero
-  for (int i = tid; i < TC_N * TC_K; i += TC_THREADS) {
-    const int n = i / TC_K, k = i - n * TC_K;
-    const float w = n < M ? __double2float_rn(W[(int64_t)n * TC_K + k]) : 0.f;
-    __nv_bfloat16 b1, b2, b3;
-    split3(w, b1, b2, b3);
+  for (int i = tid; i < TC_N * TC_K / 2; i += TC_THREADS) {
+    const int n = i / (TC_K / 2), k = 2 * (i - n * (TC_K / 2));
+    const float w0 = n < M ? __double2float_rn(W[(int64_t)n * TC_K + k]) : 0.f;
+    const float w1 = n < M ? __double2float_rn(W[(int64_t)n * TC_K + k + 1]) : 0.f;
+    const uint32_t p1 = pack_bf2(w0, w1);
+    const float r0 = __fsub_rn(w0, bf_lo(p1)), r1 = __fsub_rn(w1, bf_hi(p1));
+    const uint32_t p2 = pack_bf2(r0, r1);
+    const uint32_t p3 = pack_bf2(__fsub_rn(r0, bf_lo(p2)), __fsub_rn(r1, bf_hi(p2)));
     const uint32_t o = kmajor_off(n, k);
-    *(__nv_bfloat16 *)(sB + o) = b1;
-    *(__nv_bfloat16 *)(sB + TC_B_BYTES + o) = b2;
-    *(__nv_bfloat16 *)(sB + 2 * TC_B_BYTES + o) = b3;
+    *(uint32_t *)(sB + o) = p1;
+    *(uint32_t *)(sB + TC_B_BYTES + o) = p2;
+    *(uint32_t *)(sB + 2 * TC_B_BYTES + o) = p3;
   }
   const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
   auto tile_bytes = [&](int64_t tile) { return (uint32_t)(min((int64_t)TC_ROWS, R - tile * TC_ROWS) * TC_K * 8); };
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
   if (tid == 0 && (int64_t)blockIdx.x < ntiles)
     bulk_load(smem_addr(sF), F + (int64_t)blockIdx.x * TC_ROWS * TC_K, tile_bytes(blockIdx.x), smem_addr(&mbar_ld[0]));
 
-  float best_t = __int_as_float(0x7f800000);   // argmin mode: model tid % 64, rows of half tid / 64
+  float best_t = __int_as_float(0x7f800000);   // argmin mode: model tid % 64, rows 32 (tid / 64) .. +31
   int64_t best_r = INT64_MAX;
   uint32_t ph_mma = 0, ph_ld[2] = {0, 0};
   bool aborted = false;
@@ -274,39 +282,43 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
     if (!cta_wait(smem_addr(&mbar_mma), ph_mma)) { aborted = true; break; }
     ph_mma ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 = rows 32w + lane of the tile
-    float acc[64];
-    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
-    tmem_ld32(ta, acc);
-    tmem_ld32(ta + 32, acc + 32);
+    // epilogue: this thread's row and half of the models
+    const int lrow = (warp & 3) * 32 + lane, half = warp >> 2;
+    float acc[32];
+    tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * 32, acc);
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-    const int64_t row = r0 + warp * 32 + lane;
+    const int64_t row = r0 + lrow;
     if (MODE == 0) {
       if (row < R) {
-        double *out = T + row * M;
+        double *out = T + row * M + half * 32;
         if (M == TC_N) {
 #pragma unroll
-          for (int m = 0; m < TC_N; m += 2) *(double2 *)(out + m) = make_double2(f32_to_f64(acc[m]), f32_to_f64(acc[m + 1]));
+          for (int m = 0; m < 32; m += 2) *(double2 *)(out + m) = make_double2(f32_to_f64(acc[m]), f32_to_f64(acc[m + 1]));
         } else {
 #pragma unroll
-          for (int m = 0; m < TC_N; m++)
-            if (m < M) out[m] = f32_to_f64(acc[m]);
+          for (int m = 0; m < 32; m++)
+            if (half * 32 + m < M) out[m] = f32_to_f64(acc[m]);
         }
       }
     } else {
-      float *srow = stage + (warp * 32 + lane) * (TC_N + 1);
+      // stage [128 rows][64 models] in the raw buffer of this tile (consumed), columns
+      // XOR-swizzled by the row so that row-wise writes and column-wise reads are conflict-free
+      float *stage = (float *)(sF + buf * TC_F_BYTES);
 #pragma unroll
-      for (int m = 0; m < TC_N; m++) srow[m] = acc[m];
+      for (int m = 0; m < 32; m++) stage[lrow * TC_N + ((half * 32 + m) ^ (lrow & 31))] = acc[m];
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();   // TMEM read, staging and the raw buffer of this tile are done with
+    __syncthreads();   // TMEM read and staging done
     if (MODE == 1) {
-      const int m = tid % TC_N, half = tid / TC_N;
-      for (int rr = half * 64; rr < half * 64 + 64; rr++) {
-        if (r0 + rr >= R) break;
-        const float x = stage[rr * (TC_N + 1) + m];
-        if (x < best_t) { best_t = x; best_r = r0 + rr; }   // rows visited in increasing order
+      const float *stage = (const float *)(sF + buf * TC_F_BYTES);
+      const int m = tid % TC_N, q = tid / TC_N;
+      const int rend = min(q * 32 + 32, nrows);
+      for (int rr = q * 32; rr < rend; rr++) {   // rows in increasing order
+        const float x = stage[rr * TC_N + (m ^ (rr & 31))];
+        if (x < best_t) { best_t = x; best_r = r0 + rr; }
       }
+      // the raw buffer is refilled by the bulk-copy engine next iteration
+      asm volatile("fence.proxy.async.shared::cta;\n" ::);
       __syncthreads();
     }
   }
@@ -316,15 +328,16 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
     for (int b = 0; b < 2; b++) cta_wait(smem_addr(&mbar_ld[b]), ph_ld[b]);
   }
   if (MODE == 1 && !aborted) {
-    // combine the two halves of each model, then publish this CTA's partial result
-    float *st = stage;
-    __syncthreads();
-    if (tid >= TC_N) { st[2 * (tid - TC_N)] = best_t; ((int64_t *)(st + 2 * TC_N))[tid - TC_N] = best_r; }
+    // combine the four row ranges of each model, then publish this CTA's partial result
+    fin_t[tid] = best_t;
+    fin_r[tid] = best_r;
     __syncthreads();
     if (tid < TC_N && tid < M) {
-      const float ot = st[2 * tid];
-      const int64_t orr = ((int64_t *)(st + 2 * TC_N))[tid];
-      if (ot < best_t || (ot == best_t && orr < best_r)) { best_t = ot; best_r = orr; }
+      for (int q = 1; q < TC_THREADS / TC_N; q++) {
+        const float ot = fin_t[q * TC_N + tid];
+        const int64_t orr = fin_r[q * TC_N + tid];
+        if (ot < best_t || (ot == best_t && orr < best_r)) { best_t = ot; best_r = orr; }
+      }
       part_t[(int64_t)blockIdx.x * M + tid] = (double)best_t;
       part_r[(int64_t)blockIdx.x * M + tid] = best_r;
     }
@@ -349,14 +362,11 @@ __global__ void k_argmin_tc_reduce(const double *__restrict__ pt, const int64_t 
   mn[m] = bt;
 }
 
-static size_t tc_smem(int mode) {
-  return 2 * TC_F_BYTES + 3 * TC_A_BYTES + 3 * TC_B_BYTES + (mode == 1 ? (size_t)TC_ROWS * (TC_N + 1) * 4 : 0) +
-         1024;
-}
+static size_t tc_smem(int) { return 2 * TC_F_BYTES + 3 * TC_A_BYTES + 3 * TC_B_BYTES + 1024; }
 
-// resident CTAs per SM: mode 0 uses 101 KB of shared memory, mode 1 134 KB
+// two resident CTAs per SM (101 KB of shared memory each)
 int tc_parts(int sms) { return sms * 2; }
-static int tc_grid(int mode, int sms) { return sms * (mode == 0 ? 2 : 1); }
+static int tc_grid(int, int sms) { return sms * 2; }
 size_t tc_argmin_scratch_bytes(int M, int sms) { return (size_t)tc_parts(sms) * M * 16; }
 
 cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *W, int M, double *T, int64_t *arg,

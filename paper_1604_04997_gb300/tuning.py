@@ -59,3 +59,11 @@ def build(ctx: B.Context, n_variants: int = 10000, n_points: int = 4096, variant
         pt_off.append(pt_off[-1] + n_points)
     return Batched(list(W.TEMPLATES), variants, np.array(tables, dtype=np.int32), np.array(var_off, dtype=np.int32),
                    np.concatenate(pt_rows), np.array(pt_off, dtype=np.int64), len(cache))
+
+
+def query_arrays(b: Batched, q: W.QueryDraw):
+    """Candidate tables (int32 [n]) and points (int64 [n][4]) of one drawn query."""
+    t = q.template
+    tables = np.ascontiguousarray(b.tables[b.var_off[t] + q.variant], dtype=np.int32)
+    points = np.ascontiguousarray(b.points[b.pt_off[t] + q.point], dtype=np.int64)
+    return tables, points

@@ -385,6 +385,36 @@ def draw_weights(k: int, n_models: int, seed: int, lo: float = 1e-12, hi: float 
     return rng.uniform(lo, hi, size=(n_models, k))
 
 
+@dataclasses.dataclass
+class QueryDraw:
+    arrival_s: float          # arrival time from the start of the stream
+    template: int             # index into TEMPLATES
+    model: int
+    variant: np.ndarray       # int64 [n] variant index within the template's list
+    point: np.ndarray         # int64 [n] point index within the template's point set
+
+
+def draw_queries(n_queries: int, rate_per_s: float, n_variants: Sequence[int], n_points: int, n_models: int = 64,
+                 seed: int = 9, max_cand: int = 50000) -> List[QueryDraw]:
+    """Autotuner query stream: Poisson arrivals at rate_per_s; each query picks a
+    template and a model uniformly and n candidates log-uniform in [1, max_cand],
+    each a (variant, point) pair drawn uniformly from that template's variants
+    (n_variants[t] of them) and its n_points points."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate_per_s, size=n_queries)
+    live = [t for t in range(len(n_variants)) if n_variants[t] > 0]
+    out = []
+    t_arr = 0.0
+    for i in range(n_queries):
+        t_arr += float(gaps[i])
+        t = live[int(rng.integers(len(live)))]
+        n = int(min(max_cand, math.floor(math.exp(rng.uniform(0.0, math.log(max_cand + 1))))))
+        n = max(1, n)
+        out.append(QueryDraw(t_arr, t, int(rng.integers(n_models)), rng.integers(n_variants[t], size=n),
+                             rng.integers(n_points, size=n)))
+    return out
+
+
 # --------------------------------------------------------------------------- small workload
 
 POW2_SMALL = (64, 128, 256)
