@@ -120,15 +120,18 @@ __device__ __forceinline__ float chunk_to_float(uint32_t x) {
   return __fsub_rn(__uint_as_float(0x4B000000u | x), 8388608.0f);
 }
 
-// int64 -> nearest-ish float (|error| <= 2^-23 relative) using integer ops and FP32 adds.
+// int64 -> float with |error| <= 2^-23 |v|, using integer ops and FP32 arithmetic only.
+// v = c2 2^46 + c1 2^23 + c0 with c0, c1 in [0, 2^23) and c2 = v >> 46 signed; each part
+// converts exactly.  s = c2 2^23 + c1 is exact whenever |s| < 2^24, which covers every
+// case where the final sum s 2^23 + c0 cancels (s in {-1, 0}); otherwise both roundings
+// are relative to a value >= 2^47.
 __device__ __forceinline__ float i64_to_float(int64_t v) {
-  const bool neg = v < 0;
-  const uint64_t a = neg ? (uint64_t)(-v) : (uint64_t)v;
-  const float c0 = chunk_to_float((uint32_t)(a & 0x7FFFFFu));
-  const float c1 = chunk_to_float((uint32_t)((a >> 23) & 0x7FFFFFu));
-  const float c2 = chunk_to_float((uint32_t)((a >> 46) & 0x7FFFFFu));
-  const float f = __fmaf_rn(c2, 70368744177664.0f, __fmaf_rn(c1, 8388608.0f, c0));   // 2^46, 2^23
-  return neg ? -f : f;
+  const uint32_t lo = (uint32_t)v;
+  const int32_t hi = (int32_t)(v >> 32);
+  const float c0 = chunk_to_float(lo & 0x7FFFFFu);
+  const float c1 = chunk_to_float(__funnelshift_r(lo, (uint32_t)hi, 23) & 0x7FFFFFu);
+  const float c2 = __fsub_rn(__int_as_float(0x4B400000 + (hi >> 14)), 12582912.0f);   // 1.5 * 2^23
+  return __fmaf_rn(__fmaf_rn(c2, 8388608.0f, c1), 8388608.0f, c0);
 }
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
@@ -283,44 +286,62 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
     ph_mma ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     // epilogue: this thread's row and half of the models
-    const int lrow = (warp & 3) * 32 + lane, half = warp >> 2;
+    const int half = warp >> 2;
     float acc[32];
     tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * 32, acc);
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-    const int64_t row = r0 + lrow;
+    // per-warp 32 x 32 float block in the raw buffer of this tile (consumed), columns
+    // XOR-swizzled by the row: row-wise writes and column-wise reads are conflict-free
+    float *blk = (float *)(sF + buf * TC_F_BYTES) + warp * 1024;
+#pragma unroll
+    for (int c = 0; c < 32; c++) blk[lane * 32 + (c ^ lane)] = acc[c];
+    __syncwarp();
+    const int64_t wrow = r0 + (warp & 3) * 32;   // first row of this warp's block
     if (MODE == 0) {
-      if (row < R) {
-        double *out = T + row * M + half * 32;
-        if (M == TC_N) {
-#pragma unroll
-          for (int m = 0; m < 32; m += 2) *(double2 *)(out + m) = make_double2(f32_to_f64(acc[m]), f32_to_f64(acc[m + 1]));
-        } else {
-#pragma unroll
-          for (int m = 0; m < 32; m++)
-            if (half * 32 + m < M) out[m] = f32_to_f64(acc[m]);
+      // coalesced T rows: half-warps write one 256-byte half row each
+      if (M == TC_N) {
+        const int cp = (lane & 15) * 2;
+#pragma unroll 4
+        for (int it = 0; it < 16; it++) {
+          const int j = 2 * it + (lane >> 4);
+          const float x = blk[j * 32 + (cp ^ j)], y = blk[j * 32 + ((cp + 1) ^ j)];
+          if (wrow + j < R) *(double2 *)(T + (wrow + j) * TC_N + half * 32 + cp) = make_double2(f32_to_f64(x), f32_to_f64(y));
         }
+      } else {
+        const int col = half * 32 + lane;
+#pragma unroll 4
+        for (int j = 0; j < 32; j++)
+          if (wrow + j < R && col < M) T[(wrow + j) * M + col] = f32_to_f64(blk[j * 32 + (lane ^ j)]);
       }
-    } else {
-      // stage [128 rows][64 models] in the raw buffer of this tile (consumed), columns
-      // XOR-swizzled by the row so that row-wise writes and column-wise reads are conflict-free
-      float *stage = (float *)(sF + buf * TC_F_BYTES);
-#pragma unroll
-      for (int m = 0; m < 32; m++) stage[lrow * TC_N + ((half * 32 + m) ^ (lrow & 31))] = acc[m];
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();   // TMEM read and staging done
+    __syncthreads();   // TMEM read; blocks complete
     if (MODE == 1) {
-      const float *stage = (const float *)(sF + buf * TC_F_BYTES);
+      // model m = tid % 64 scans rows 32 q .. 32 q + 31 (the block of warp (q, m / 32))
       const int m = tid % TC_N, q = tid / TC_N;
-      const int rend = min(q * 32 + 32, nrows);
-      for (int rr = q * 32; rr < rend; rr++) {   // rows in increasing order
-        const float x = stage[rr * TC_N + (m ^ (rr & 31))];
-        if (x < best_t) { best_t = x; best_r = r0 + rr; }
+      const float *col = (const float *)(sF + buf * TC_F_BYTES) + ((m >> 5) * 4 + q) * 1024;
+      const int mc = m & 31, rb = q * 32;
+      float bt = __int_as_float(0x7f800000);
+      int bi = 0;
+      if (rb + 32 <= nrows) {
+#pragma unroll
+        for (int j = 0; j < 32; j++) {   // rows in increasing order: the first minimum wins
+          const float x = col[j * 32 + (mc ^ j)];
+          const bool p = x < bt;
+          bt = p ? x : bt;
+          bi = p ? j : bi;
+        }
+      } else {
+        for (int j = 0; j < nrows - rb; j++) {
+          const float x = col[j * 32 + (mc ^ j)];
+          if (x < bt) { bt = x; bi = j; }
+        }
       }
-      // the raw buffer is refilled by the bulk-copy engine next iteration
-      asm volatile("fence.proxy.async.shared::cta;\n" ::);
-      __syncthreads();
+      if (bt < best_t) { best_t = bt; best_r = r0 + rb + bi; }
     }
+    // the raw buffer is refilled by the bulk-copy engine next iteration
+    asm volatile("fence.proxy.async.shared::cta;\n" ::);
+    __syncthreads();
   }
   if (aborted) {
     if (tid == 0) atomicOr(status, ST_TIMEOUT);
