@@ -17,11 +17,14 @@
 // 16 bytes per core matrix), made visible to the tensor core with a proxy fence,
 // and the MMAs are issued by one thread and committed to an mbarrier.  Every
 // mbarrier wait is bounded; on timeout the kernel records ST_TIMEOUT and stops.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "eval_common.cuh"
 #include "kernels.h"
@@ -85,19 +88,41 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 
 // Exact float -> double bit pattern with integer operations (the conversion
 // instruction would run on the FP64 pipe).
-__device__ __forceinline__ double f32_to_f64(float f) {
+__device__ __noinline__ double f32_to_f64_rare(float f) {   // zero, subnormal, inf, nan
   const uint32_t u = __float_as_uint(f);
   const uint64_t sign = (uint64_t)(u >> 31) << 63;
   const uint32_t e = (u >> 23) & 0xFF, m = u & 0x7FFFFF;
   uint64_t bits;
-  if (e == 0xFF) bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);          // inf / nan
-  else if (e != 0) bits = sign | ((uint64_t)(e + 896) << 52) | ((uint64_t)m << 29);  // normal: 1023 - 127 = 896
-  else if (m == 0) bits = sign;                                                   // zero
-  else {                                                                           // subnormal float
-    const int lz = __clz(m) - 8;                                                   // leading zeros in 23 bits
+  if (e == 0xFF) bits = sign | (0x7FFull << 52) | ((uint64_t)m << 29);   // inf / nan
+  else if (m == 0) bits = sign;                                          // zero
+  else {                                                                  // subnormal float
+    const int lz = __clz(m) - 8;                                          // leading zeros in 23 bits
     bits = sign | ((uint64_t)(897 - lz - 1) << 52) | ((uint64_t)((m << (lz + 1)) & 0x7FFFFF) << 29);
   }
   return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f), mag = u & 0x7FFFFFFFu;
+  if (mag - 0x00800000u < 0x7F000000u) {   // normal: exponent rebias 1023 - 127 = 896
+    const uint32_t hi = (u & 0x80000000u) | ((mag >> 3) + 0x38000000u);
+    return __hiloint2double((int)hi, (int)(u << 29));
+  }
+  return f32_to_f64_rare(f);
+}
+
+// TMEM 16 lanes x 256 bits, 4 repetitions along the columns: thread t holds lanes
+// t/4 and t/4 + 8, columns 8 j + 2 (t%4) and 8 j + 2 (t%4) + 1 of repetition j as
+// v[4 j + {0, 1}] (lane t/4) and v[4 j + {2, 3}] (lane t/4 + 8).
+__device__ __forceinline__ void tmem_ld16x256(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
 }
 
 // 32 consecutive fp32 columns of this thread's TMEM lane
@@ -134,11 +159,23 @@ __device__ __forceinline__ float i64_to_float(int64_t v) {
   return __fmaf_rn(__fmaf_rn(c2, 8388608.0f, c1), 8388608.0f, c0);
 }
 
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
+// Tiled tensor copy of one 128-row tile of counts (box 16 x 2 x 128 int64 over the view
+// F[R][2][16]) with the 128-byte swizzle; rows past R are zero-filled, and the
+// transaction count is always the full box.
+__device__ __forceinline__ void tile_load(uint32_t dst, const CUtensorMap *map, int32_t row0, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(TC_F_BYTES) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(dst),
+      "l"((uint64_t)map), "r"(0), "r"(0), "r"(row0), "r"(mbar)
+      : "memory");
+}
+
+// Byte offset of 16-byte chunk c (0..15) of row r in a swizzled tile: each 128-byte
+// line (half row) has its chunk index XORed with the line index mod 8.
+__device__ __forceinline__ uint32_t swz_chunk(int r, int c) {
+  const int line = 2 * r + (c >> 3);
+  return (uint32_t)(line * 128 + (((c & 7) ^ (line & 7)) << 4));
 }
 
 // Bounded mbarrier wait shared by the whole CTA: returns true if every thread saw the
@@ -162,43 +199,51 @@ __device__ __forceinline__ uint32_t pack_bf2(float x, float y) {
   return *(const uint32_t *)&h;
 }
 
-// 8 consecutive counts -> three 16-byte vectors of exact bf16 splits (x = x1 + x2 + x3)
-__device__ __forceinline__ void convert8(const int64_t *src, uint4 &o1, uint4 &o2, uint4 &o3) {
-  uint32_t w1[4], w2[4], w3[4];
-#pragma unroll
-  for (int q = 0; q < 4; q++) {
-    const longlong2 v = *(const longlong2 *)(src + 2 * q);
-    const float x = i64_to_float(v.x), y = i64_to_float(v.y);
-    w1[q] = pack_bf2(x, y);
-    const float rx = __fsub_rn(x, bf_lo(w1[q])), ry = __fsub_rn(y, bf_hi(w1[q]));
-    w2[q] = pack_bf2(rx, ry);
-    w3[q] = pack_bf2(__fsub_rn(rx, bf_lo(w2[q])), __fsub_rn(ry, bf_hi(w2[q])));
-  }
-  o1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-  o2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-  o3 = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+// Two counts -> three packed bf16 pairs, exact splits x = x1 + x2 + x3 of their floats.
+__device__ __forceinline__ void split_pair(longlong2 v, uint32_t &p1, uint32_t &p2, uint32_t &p3) {
+  const float x = i64_to_float(v.x), y = i64_to_float(v.y);
+  p1 = pack_bf2(x, y);
+  const float rx = __fsub_rn(x, bf_lo(p1)), ry = __fsub_rn(y, bf_hi(p1));
+  p2 = pack_bf2(rx, ry);
+  p3 = pack_bf2(__fsub_rn(rx, bf_lo(p2)), __fsub_rn(ry, bf_hi(p2)));
 }
+
+// (value, row) pairs: the smaller value, the smaller row on ties
+__device__ __forceinline__ bool vr_less(float a, int ra, float b, int rb) { return a < b || (a == b && ra < rb); }
 
 // mode 0: write T (fp64 [R][M]);  mode 1: per-model running argmin -> part[blockIdx][M]
 //
-// Warps w and w + 4 share TMEM lanes 32 (w % 4) .. +31 (rows of the tile); warp w < 4
-// reads accumulator columns 0..31 (models), warp w + 4 columns 32..63.
+// Per tile: wait for the tile's counts, convert them into the three bf16 operand
+// splits, issue the MMAs and the load of the CTA's next tile (the raw buffer is free
+// once converted), wait for the MMAs, then the epilogue.  Several CTAs per SM overlap
+// one another's loads, conversions and epilogues.  Warps w and w + 4 share TMEM lanes
+// 32 (w % 4) .. +31 (rows of the tile); warp w < 4 takes accumulator columns (models)
+// 0..31, warp w + 4 columns 32..63.
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__restrict__ F, int64_t R,
+__global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant__ CUtensorMap fmap, int64_t R,
                                                             const double *__restrict__ W, int M,
                                                             double *__restrict__ T, double *__restrict__ part_t,
                                                             int64_t *__restrict__ part_r, int *status) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *sF = smem;                              // 2 x 32 KB raw row tiles
-  uint8_t *sA = smem + 2 * TC_F_BYTES;             // 3 splits x 8 KB
+  extern __shared__ uint8_t smem_raw[];
+  // the swizzled tile needs a 1024-byte aligned destination
+  uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  uint8_t *sF = smem;                              // 32 KB raw row tile (swizzled)
+  uint8_t *sA = smem + TC_F_BYTES;                 // 3 splits x 8 KB
   uint8_t *sB = sA + 3 * TC_A_BYTES;               // 3 splits x 4 KB
-  __shared__ __align__(8) uint64_t mbar_mma, mbar_ld[2];
+  __shared__ __align__(8) uint64_t mbar_mma, mbar_ld;
   __shared__ uint32_t tmem_base;
   __shared__ float fin_t[TC_THREADS];
   __shared__ int64_t fin_r[TC_THREADS];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
 
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_mma)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_ld)));
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
+    asm volatile("prefetch.tensormap [%0];\n" ::"l"((uint64_t)&fmap) : "memory");
+  }
   // weights: three bf16 splits, K-major, models >= M are zero
   for (int i = tid; i < TC_N * TC_K / 2; i += TC_THREADS) {
     const int n = i / (TC_K / 2), k = 2 * (i - n * (TC_K / 2));
@@ -213,14 +258,6 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
     *(uint32_t *)(sB + TC_B_BYTES + o) = p2;
     *(uint32_t *)(sB + 2 * TC_B_BYTES + o) = p3;
   }
-  const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
-  auto tile_bytes = [&](int64_t tile) { return (uint32_t)(min((int64_t)TC_ROWS, R - tile * TC_ROWS) * TC_K * 8); };
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_mma)));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_ld[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar_ld[1])));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::);
-  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
                  "r"(TC_N));
@@ -231,36 +268,30 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
   const uint32_t tmem = tmem_base;
   if (tid == 0 && (int64_t)blockIdx.x < ntiles)
-    bulk_load(smem_addr(sF), F + (int64_t)blockIdx.x * TC_ROWS * TC_K, tile_bytes(blockIdx.x), smem_addr(&mbar_ld[0]));
+    tile_load(smem_addr(sF), &fmap, (int32_t)(blockIdx.x * TC_ROWS), smem_addr(&mbar_ld));
 
-  float best_t = __int_as_float(0x7f800000);   // argmin mode: model tid % 64, rows 32 (tid / 64) .. +31
+  const int half = warp >> 2, quarter = warp & 3;
+  float best_t = __int_as_float(0x7f800000);   // argmin mode: model 32 half + lane over rows 32 quarter .. +31
   int64_t best_r = INT64_MAX;
-  uint32_t ph_mma = 0, ph_ld[2] = {0, 0};
+  uint32_t ph_mma = 0, ph_ld = 0;
   bool aborted = false;
-  int it = 0;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
-    const int buf = it & 1;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * TC_ROWS;
-    // stream the next tile into the other buffer (its previous contents were consumed last iteration)
-    const int64_t next = tile + gridDim.x;
-    if (tid == 0 && next < ntiles)
-      bulk_load(smem_addr(sF + (buf ^ 1) * TC_F_BYTES), F + next * TC_ROWS * TC_K, tile_bytes(next),
-                smem_addr(&mbar_ld[buf ^ 1]));
-    if (!cta_wait(smem_addr(&mbar_ld[buf]), ph_ld[buf])) { aborted = true; break; }
-    ph_ld[buf] ^= 1;
+    if (!cta_wait(smem_addr(&mbar_ld), ph_ld)) { aborted = true; break; }
+    ph_ld ^= 1;
     // operands: counts -> float -> three exact bf16 splits, 16-byte K-major core-matrix rows
-    const int nrows = (int)min((int64_t)TC_ROWS, R - r0);
-    const int64_t *src = (const int64_t *)(sF + buf * TC_F_BYTES);
 #pragma unroll
     for (int j = 0; j < TC_ROWS * 4 / TC_THREADS; j++) {
       const int item = tid + j * TC_THREADS;
-      const int row = item >> 2, kg = item & 3;
-      uint4 o1 = make_uint4(0, 0, 0, 0), o2 = o1, o3 = o1;
-      if (row < nrows) convert8(src + row * TC_K + kg * 8, o1, o2, o3);
+      const int row = item >> 2, kg = item & 3;   // 8 counts: chunks 4 kg .. 4 kg + 3 of the row
+      uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        split_pair(*(const longlong2 *)(sF + swz_chunk(row, 4 * kg + q)), w1[q], w2[q], w3[q]);
       const uint32_t o = kmajor_off(row, kg * 8);
-      *(uint4 *)(sA + o) = o1;
-      *(uint4 *)(sA + TC_A_BYTES + o) = o2;
-      *(uint4 *)(sA + 2 * TC_A_BYTES + o) = o3;
+      *(uint4 *)(sA + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+      *(uint4 *)(sA + TC_A_BYTES + o) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      *(uint4 *)(sA + 2 * TC_A_BYTES + o) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::);
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -268,99 +299,118 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const int64_t *__rest
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
       // products x1y1, x1y2, x2y1, x1y3, x2y2, x3y1, each over K = 32 in two K = 16 steps
-      const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
-      uint32_t acc = 0;
 #pragma unroll
-      for (int p = 0; p < 6; p++)
+      for (int p = 0; p < 6; p++) {
+        const int pa = p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0);
+        const int pb = p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0);
 #pragma unroll
         for (int kc = 0; kc < 2; kc++) {
-          const uint64_t ad = sdesc(smem_addr(sA + pa[p] * TC_A_BYTES + kc * 256));
-          const uint64_t bd = sdesc(smem_addr(sB + pb[p] * TC_B_BYTES + kc * 256));
-          tc_mma(tmem, ad, bd, acc);
-          acc = 1;
+          const uint64_t ad = sdesc(smem_addr(sA + pa * TC_A_BYTES + kc * 256));
+          const uint64_t bd = sdesc(smem_addr(sB + pb * TC_B_BYTES + kc * 256));
+          tc_mma(tmem, ad, bd, (p | kc) != 0);
         }
+      }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
           smem_addr(&mbar_mma)));
+      // the raw tile is converted: stream in this CTA's next tile
+      const int64_t next = tile + gridDim.x;
+      if (next < ntiles) tile_load(smem_addr(sF), &fmap, (int32_t)(next * TC_ROWS), smem_addr(&mbar_ld));
     }
     if (!cta_wait(smem_addr(&mbar_mma), ph_mma)) { aborted = true; break; }
     ph_mma ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    // epilogue: this thread's row and half of the models
-    const int half = warp >> 2;
-    float acc[32];
-    tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + half * 32, acc);
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
-    // per-warp 32 x 32 float block in the raw buffer of this tile (consumed), columns
-    // XOR-swizzled by the row: row-wise writes and column-wise reads are conflict-free
-    float *blk = (float *)(sF + buf * TC_F_BYTES) + warp * 1024;
-#pragma unroll
-    for (int c = 0; c < 32; c++) blk[lane * 32 + (c ^ lane)] = acc[c];
-    __syncwarp();
-    const int64_t wrow = r0 + (warp & 3) * 32;   // first row of this warp's block
     if (MODE == 0) {
-      // coalesced T rows: half-warps write one 256-byte half row each
-      if (M == TC_N) {
-        const int cp = (lane & 15) * 2;
-#pragma unroll 4
-        for (int it = 0; it < 16; it++) {
-          const int j = 2 * it + (lane >> 4);
-          const float x = blk[j * 32 + (cp ^ j)], y = blk[j * 32 + ((cp + 1) ^ j)];
-          if (wrow + j < R) *(double2 *)(T + (wrow + j) * TC_N + half * 32 + cp) = make_double2(f32_to_f64(x), f32_to_f64(y));
+      // thread t: rows 16 s + t/4 and 16 s + t/4 + 8 of the warp's 32, column pairs
+      // 8 j + 2 (t%4) of the warp's 32 columns; each warp store writes 8 rows x 64 bytes
+      const int rq = lane >> 2, cq = 2 * (lane & 3);
+#pragma unroll
+      for (int s = 0; s < 2; s++) {
+        float v[16];
+        tmem_ld16x256(tmem + ((uint32_t)(quarter * 32 + 16 * s) << 16) + half * 32, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+          const int64_t row = r0 + quarter * 32 + 16 * s + rq + 8 * h;
+          if (row < R) {
+            if (M == TC_N) {
+              double *out = T + row * TC_N + half * 32 + cq;
+#pragma unroll
+              for (int j = 0; j < 4; j++)
+                *(double2 *)(out + 8 * j) = make_double2(f32_to_f64(v[4 * j + 2 * h]), f32_to_f64(v[4 * j + 2 * h + 1]));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; j++) {
+                const int col = half * 32 + 8 * j + cq;
+                if (col < M) T[row * M + col] = f32_to_f64(v[4 * j + 2 * h]);
+                if (col + 1 < M) T[row * M + col + 1] = f32_to_f64(v[4 * j + 2 * h + 1]);
+              }
+            }
+          }
         }
-      } else {
-        const int col = half * 32 + lane;
-#pragma unroll 4
-        for (int j = 0; j < 32; j++)
-          if (wrow + j < R && col < M) T[(wrow + j) * M + col] = f32_to_f64(blk[j * 32 + (lane ^ j)]);
+      }
+    } else {
+      // thread = row 32 quarter + lane; per column (model) the minimum over the warp's
+      // rows by a butterfly that halves the columns each lane keeps: lane l ends with
+      // column l.  Rows past R hold zero-filled counts and are masked to +inf.
+      float acc[32];
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + half * 32, acc);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+      const bool live = r0 + quarter * 32 + lane < R;
+      if (!live) {
+#pragma unroll
+        for (int c = 0; c < 32; c++) acc[c] = __int_as_float(0x7f800000);
+      }
+      float v[32];
+#pragma unroll
+      for (int c = 0; c < 32; c++) v[c] = acc[c];
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;   // keeps the upper half of its columns
+#pragma unroll
+        for (int c = 0; c < o; c++) {
+          const float send = up ? v[c] : v[c + o];
+          const float keep = up ? v[c + o] : v[c];
+          v[c] = fminf(keep, __shfl_xor_sync(0xffffffffu, send, o));
+        }
+      }
+      const float tmin = v[0];   // minimum of column `lane` over the warp's rows
+      // rows of later tiles are larger: only a strictly smaller value improves
+      const unsigned better = __ballot_sync(0xffffffffu, tmin < best_t);
+      if (better) {
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+          if (better & (1u << c)) {
+            const float m = __shfl_sync(0xffffffffu, tmin, c);
+            const unsigned hit = __ballot_sync(0xffffffffu, acc[c] == m);
+            if (lane == c) { best_t = m; best_r = r0 + quarter * 32 + (__ffs(hit) - 1); }
+          }
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
-    __syncthreads();   // TMEM read; blocks complete
-    if (MODE == 1) {
-      // model m = tid % 64 scans rows 32 q .. 32 q + 31 (the block of warp (q, m / 32))
-      const int m = tid % TC_N, q = tid / TC_N;
-      const float *col = (const float *)(sF + buf * TC_F_BYTES) + ((m >> 5) * 4 + q) * 1024;
-      const int mc = m & 31, rb = q * 32;
-      float bt = __int_as_float(0x7f800000);
-      int bi = 0;
-      if (rb + 32 <= nrows) {
-#pragma unroll
-        for (int j = 0; j < 32; j++) {   // rows in increasing order: the first minimum wins
-          const float x = col[j * 32 + (mc ^ j)];
-          const bool p = x < bt;
-          bt = p ? x : bt;
-          bi = p ? j : bi;
-        }
-      } else {
-        for (int j = 0; j < nrows - rb; j++) {
-          const float x = col[j * 32 + (mc ^ j)];
-          if (x < bt) { bt = x; bi = j; }
-        }
-      }
-      if (bt < best_t) { best_t = bt; best_r = r0 + rb + bi; }
-    }
-    // the raw buffer is refilled by the bulk-copy engine next iteration
-    asm volatile("fence.proxy.async.shared::cta;\n" ::);
-    __syncthreads();
+    __syncthreads();   // TMEM read before the next tile's MMAs overwrite it
   }
   if (aborted) {
     if (tid == 0) atomicOr(status, ST_TIMEOUT);
-    // let any bulk copy still in flight land before the CTA exits (bounded)
-    for (int b = 0; b < 2; b++) cta_wait(smem_addr(&mbar_ld[b]), ph_ld[b]);
+    // let a tile load still in flight land before the CTA exits (bounded)
+    cta_wait(smem_addr(&mbar_ld), ph_ld);
   }
   if (MODE == 1 && !aborted) {
-    // combine the four row ranges of each model, then publish this CTA's partial result
-    fin_t[tid] = best_t;
-    fin_r[tid] = best_r;
+    // combine the four row quarters of each model, then publish this CTA's partial result
+    const int model = half * 32 + lane;
+    fin_t[quarter * TC_N + model] = best_t;
+    fin_r[quarter * TC_N + model] = best_r;
     __syncthreads();
     if (tid < TC_N && tid < M) {
-      for (int q = 1; q < TC_THREADS / TC_N; q++) {
+      float bt = fin_t[tid];
+      int64_t br = fin_r[tid];
+      for (int q = 1; q < 4; q++) {
         const float ot = fin_t[q * TC_N + tid];
         const int64_t orr = fin_r[q * TC_N + tid];
-        if (ot < best_t || (ot == best_t && orr < best_r)) { best_t = ot; best_r = orr; }
+        if (ot < bt || (ot == bt && orr < br)) { bt = ot; br = orr; }
       }
-      part_t[(int64_t)blockIdx.x * M + tid] = (double)best_t;
-      part_r[(int64_t)blockIdx.x * M + tid] = best_r;
+      part_t[(int64_t)blockIdx.x * M + tid] = (double)bt;
+      part_r[(int64_t)blockIdx.x * M + tid] = br;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -383,33 +433,58 @@ __global__ void k_argmin_tc_reduce(const double *__restrict__ pt, const int64_t 
   mn[m] = bt;
 }
 
-static size_t tc_smem(int) { return 2 * TC_F_BYTES + 3 * TC_A_BYTES + 3 * TC_B_BYTES + 1024; }
+// raw tile + operand splits + 1 KB alignment slack: 69 KB, three CTAs per SM
+static size_t tc_smem() { return TC_F_BYTES + 3 * TC_A_BYTES + 3 * TC_B_BYTES + 1024; }
+constexpr int TC_CTAS_PER_SM = 3;
 
-// two resident CTAs per SM (101 KB of shared memory each)
-int tc_parts(int sms) { return sms * 2; }
-static int tc_grid(int, int sms) { return sms * 2; }
+int tc_parts(int sms) { return sms * TC_CTAS_PER_SM; }
 size_t tc_argmin_scratch_bytes(int M, int sms) { return (size_t)tc_parts(sms) * M * 16; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
 
 cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *W, int M, double *T, int64_t *arg,
                               double *mn, void *scratch, int sms, int *status, cudaStream_t st) {
-  if (k != TC_K || M > TC_N || M <= 0) return cudaErrorInvalidValue;
-  if (((uintptr_t)F & 15) != 0) return cudaErrorMisalignedAddress;   // bulk copies need 16-byte alignment
+  if (k != TC_K || M > TC_N || M <= 0 || R > INT32_MAX - TC_ROWS) return cudaErrorInvalidValue;
+  if (((uintptr_t)F & 15) != 0) return cudaErrorMisalignedAddress;   // tensor copies need 16-byte alignment
   if (R == 0) {   // no rows: argmin is -1 with time +inf
     if (arg) k_argmin_tc_reduce<<<(M + 63) / 64, 64, 0, st>>>(nullptr, nullptr, 0, M, arg, mn);
     return cudaGetLastError();
   }
+  PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const cuuint64_t dims[3] = {16, 2, (cuuint64_t)R};
+  const cuuint64_t strides[2] = {128, 256};   // bytes: half row, row
+  const cuuint32_t box[3] = {16, 2, TC_ROWS};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, (void *)F, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const int64_t ntiles = (R + TC_ROWS - 1) / TC_ROWS;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)tc_grid(arg ? 1 : 0, sms)));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)tc_parts(sms)));
+  const size_t sm = tc_smem();
   if (!arg) {
-    const size_t sm = tc_smem(0);
     cudaFuncSetAttribute(k_predict_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_predict_tc<0><<<grid, TC_THREADS, sm, st>>>(F, R, W, M, T, nullptr, nullptr, status);
+    k_predict_tc<0><<<grid, TC_THREADS, sm, st>>>(map, R, W, M, T, nullptr, nullptr, status);
   } else {
-    const size_t sm = tc_smem(1);
     double *pt = (double *)scratch;
     int64_t *pr = (int64_t *)((char *)scratch + (size_t)tc_parts(sms) * M * 8);
     cudaFuncSetAttribute(k_predict_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_predict_tc<1><<<grid, TC_THREADS, sm, st>>>(F, R, W, M, nullptr, pt, pr, status);
+    k_predict_tc<1><<<grid, TC_THREADS, sm, st>>>(map, R, W, M, nullptr, pt, pr, status);
     k_argmin_tc_reduce<<<(M + 63) / 64, 64, 0, st>>>(pt, pr, grid, M, arg, mn);
   }
   return cudaGetLastError();
