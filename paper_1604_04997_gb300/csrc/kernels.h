@@ -41,6 +41,10 @@ int k2_table_words();
 int k2_points_per_cta(int nw);
 
 // predict.cu
+struct ArgPart { double t; int64_t r; };   // a partial per-model minimum: time and row
+// per-model minimum over n_part partials part[p][M] (smaller time, then smaller row);
+// n_part == 0 gives -1 and +inf
+cudaError_t launch_argmin_reduce(const ArgPart *part, int n_part, int M, int64_t *arg, double *mn, cudaStream_t st);
 cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, int M, int precision, double *T,
                            cudaStream_t st);
 // argmin: per-model partial results go to scratch (n_part [M] (double, int64) pairs), then reduced.

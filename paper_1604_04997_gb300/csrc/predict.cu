@@ -144,8 +144,6 @@ cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, 
 
 // ---------------------------------------------------------------- argmin over rows per model
 
-struct ArgPart { double t; int64_t r; };
-
 __device__ __forceinline__ bool arg_less(double a, int64_t ra, double b, int64_t rb) {
   return a < b || (a == b && ra < rb);
 }
@@ -191,16 +189,37 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_argmin_part(const int
   }
 }
 
-__global__ void k_argmin_reduce(const ArgPart *__restrict__ part, int n_part, int M, int64_t *arg, double *mn) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
-  ArgPart b = part[m];
-  for (int p = 1; p < n_part; p++) {
-    ArgPart x = part[(int64_t)p * M + m];
-    if (arg_less(x.t, x.r, b.t, b.r)) b = x;
+// One CTA per model: strided scan of the partials, then a warp and a CTA reduction.
+__global__ void __launch_bounds__(128) k_argmin_reduce(const ArgPart *__restrict__ part, int n_part, int M,
+                                                       int64_t *arg, double *mn) {
+  __shared__ double s_t[4];
+  __shared__ int64_t s_r[4];
+  const int m = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double bt = __longlong_as_double(0x7ff0000000000000ll);
+  int64_t br = INT64_MAX;
+  for (int p = threadIdx.x; p < n_part; p += blockDim.x) {
+    const ArgPart x = part[(int64_t)p * M + m];
+    if (arg_less(x.t, x.r, bt, br)) { bt = x.t; br = x.r; }
   }
-  arg[m] = b.r == INT64_MAX ? -1 : b.r;
-  mn[m] = b.t;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double ot = __shfl_xor_sync(0xffffffffu, bt, o);
+    const int64_t orr = __shfl_xor_sync(0xffffffffu, br, o);
+    if (arg_less(ot, orr, bt, br)) { bt = ot; br = orr; }
+  }
+  if (lane == 0) { s_t[warp] = bt; s_r[warp] = br; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < 4; w++)
+      if (arg_less(s_t[w], s_r[w], bt, br)) { bt = s_t[w]; br = s_r[w]; }
+    arg[m] = br == INT64_MAX ? -1 : br;
+    mn[m] = bt;
+  }
+}
+
+cudaError_t launch_argmin_reduce(const ArgPart *part, int n_part, int M, int64_t *arg, double *mn, cudaStream_t st) {
+  k_argmin_reduce<<<M, 128, 0, st>>>(part, n_part, M, arg, mn);
+  return cudaGetLastError();
 }
 
 int argmin_parts() { return num_sms() * 4; }
@@ -211,8 +230,7 @@ static cudaError_t launch_argmin_parts(const int64_t *F, int64_t R, int k, const
   size_t sm = sizeof(PredictSmem);
   cudaFuncSetAttribute(k_predict_argmin_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_predict_argmin_part<<<np, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, (ArgPart *)scratch);
-  k_argmin_reduce<<<(M + 63) / 64, 64, 0, st>>>((const ArgPart *)scratch, np, M, arg, mn);
-  return cudaGetLastError();
+  return launch_argmin_reduce((const ArgPart *)scratch, np, M, arg, mn, st);
 }
 
 cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,

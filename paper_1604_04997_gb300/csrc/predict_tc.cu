@@ -222,8 +222,8 @@ __device__ __forceinline__ bool vr_less(float a, int ra, float b, int rb) { retu
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant__ CUtensorMap fmap, int64_t R,
                                                             const double *__restrict__ W, int M,
-                                                            double *__restrict__ T, double *__restrict__ part_t,
-                                                            int64_t *__restrict__ part_r, int *status) {
+                                                            double *__restrict__ T, ArgPart *__restrict__ part,
+                                                            int *status) {
   extern __shared__ uint8_t smem_raw[];
   // the swizzled tile needs a 1024-byte aligned destination
   uint8_t *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
@@ -280,10 +280,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant
     if (!cta_wait(smem_addr(&mbar_ld), ph_ld)) { aborted = true; break; }
     ph_ld ^= 1;
     // operands: counts -> float -> three exact bf16 splits, 16-byte K-major core-matrix rows
+    // warp w converts row groups w and w + 8 (8 rows x 4 k-groups each); lane i + 8 s takes
+    // row i of the group and k-group (2 (i / 4) + s) mod 4, which keeps both the swizzled
+    // reads and the operand stores of every quarter warp on distinct banks
 #pragma unroll
     for (int j = 0; j < TC_ROWS * 4 / TC_THREADS; j++) {
-      const int item = tid + j * TC_THREADS;
-      const int row = item >> 2, kg = item & 3;   // 8 counts: chunks 4 kg .. 4 kg + 3 of the row
+      const int i = lane & 7, sq = lane >> 3;
+      const int row = (warp + 8 * j) * 8 + i, kg = (2 * (i >> 2) + sq) & 3;   // 8 counts: chunks 4 kg .. 4 kg + 3
       uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
       for (int q = 0; q < 4; q++)
@@ -323,11 +326,13 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant
       // thread t: rows 16 s + t/4 and 16 s + t/4 + 8 of the warp's 32, column pairs
       // 8 j + 2 (t%4) of the warp's 32 columns; each warp store writes 8 rows x 64 bytes
       const int rq = lane >> 2, cq = 2 * (lane & 3);
+      float vv[2][16];
+      tmem_ld16x256(tmem + ((uint32_t)(quarter * 32) << 16) + half * 32, vv[0]);
+      tmem_ld16x256(tmem + ((uint32_t)(quarter * 32 + 16) << 16) + half * 32, vv[1]);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
 #pragma unroll
       for (int s = 0; s < 2; s++) {
-        float v[16];
-        tmem_ld16x256(tmem + ((uint32_t)(quarter * 32 + 16 * s) << 16) + half * 32, v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+        const float *v = vv[s];
 #pragma unroll
         for (int h = 0; h < 2; h++) {
           const int64_t row = r0 + quarter * 32 + 16 * s + rq + 8 * h;
@@ -409,28 +414,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant
         const int64_t orr = fin_r[q * TC_N + tid];
         if (ot < bt || (ot == bt && orr < br)) { bt = ot; br = orr; }
       }
-      part_t[(int64_t)blockIdx.x * M + tid] = (double)bt;
-      part_r[(int64_t)blockIdx.x * M + tid] = br;
+      part[(int64_t)blockIdx.x * M + tid] = ArgPart{(double)bt, br};
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_N));
-}
-
-__global__ void k_argmin_tc_reduce(const double *__restrict__ pt, const int64_t *__restrict__ pr, int n_part, int M,
-                                   int64_t *arg, double *mn) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
-  double bt = __longlong_as_double(0x7ff0000000000000ll);
-  int64_t br = INT64_MAX;
-  for (int p = 0; p < n_part; p++) {
-    const double t = pt[(int64_t)p * M + m];
-    const int64_t r = pr[(int64_t)p * M + m];
-    if (t < bt || (t == bt && r < br)) { bt = t; br = r; }
-  }
-  arg[m] = br == INT64_MAX ? -1 : br;
-  mn[m] = bt;
 }
 
 // raw tile + operand splits + 1 KB alignment slack: 69 KB, three CTAs per SM
@@ -460,8 +449,7 @@ cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *
   if (k != TC_K || M > TC_N || M <= 0 || R > INT32_MAX - TC_ROWS) return cudaErrorInvalidValue;
   if (((uintptr_t)F & 15) != 0) return cudaErrorMisalignedAddress;   // tensor copies need 16-byte alignment
   if (R == 0) {   // no rows: argmin is -1 with time +inf
-    if (arg) k_argmin_tc_reduce<<<(M + 63) / 64, 64, 0, st>>>(nullptr, nullptr, 0, M, arg, mn);
-    return cudaGetLastError();
+    return arg ? launch_argmin_reduce(nullptr, 0, M, arg, mn, st) : cudaSuccess;
   }
   PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return cudaErrorNotSupported;
@@ -479,13 +467,12 @@ cudaError_t launch_predict_tc(const int64_t *F, int64_t R, int k, const double *
   const size_t sm = tc_smem();
   if (!arg) {
     cudaFuncSetAttribute(k_predict_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_predict_tc<0><<<grid, TC_THREADS, sm, st>>>(map, R, W, M, T, nullptr, nullptr, status);
+    k_predict_tc<0><<<grid, TC_THREADS, sm, st>>>(map, R, W, M, T, nullptr, status);
   } else {
-    double *pt = (double *)scratch;
-    int64_t *pr = (int64_t *)((char *)scratch + (size_t)tc_parts(sms) * M * 8);
+    ArgPart *part = (ArgPart *)scratch;
     cudaFuncSetAttribute(k_predict_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_predict_tc<1><<<grid, TC_THREADS, sm, st>>>(map, R, W, M, nullptr, pt, pr, status);
-    k_argmin_tc_reduce<<<(M + 63) / 64, 64, 0, st>>>(pt, pr, grid, M, arg, mn);
+    k_predict_tc<1><<<grid, TC_THREADS, sm, st>>>(map, R, W, M, nullptr, part, status);
+    return launch_argmin_reduce(part, grid, M, arg, mn, st);
   }
   return cudaGetLastError();
 }
