@@ -205,7 +205,7 @@ pm_status pm_fit_weights(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t k, 
 /* ------------------------------------------------------------------ serving */
 
 typedef struct {
-  int32_t batch_interval_us;   /* how often the batcher packs waiting queries (e.g. 200) */
+  int32_t batch_interval_us;   /* longest a query waits for batch mates while the GPU is busy (e.g. 200) */
   int32_t n_streams;           /* compute streams that overlap batches (>= 1) */
   int32_t max_batch_queries;   /* queries per batch (<= 1024) */
   int32_t reserved;
@@ -241,9 +241,11 @@ typedef struct {
 pm_status pm_serve_set_weights(pm_ctx *ctx, const double *h_W, int32_t n_models);
 /* Start the serve loop (a batching thread and a completion thread).  It holds
  * min(mem_budget, 1 GiB) of device memory and as much pinned host memory for the
- * queries in flight.  A batch is launched when its oldest query has waited
- * batch_interval_us or max_batch_queries are queued; queries are admitted in arrival
- * order while they fit the free memory, so a small budget queues them. */
+ * queries in flight.  Queries are batched while the GPU is busy: a batch is launched
+ * at once when no batch is in flight, otherwise when its oldest query has waited
+ * batch_interval_us, max_batch_queries are queued or the batches in flight finish.
+ * Queries are admitted in arrival order while they fit the free memory, so a small
+ * budget queues them. */
 pm_status pm_serve_start(pm_ctx *ctx, const pm_serve_config *cfg);
 /* Queue a query (thread-safe).  Its tables must be PM_LAYOUT_32 tables of this
  * context; h_tables and h_points are read when its batch is formed, so they too stay

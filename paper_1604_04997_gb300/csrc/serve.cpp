@@ -3,8 +3,9 @@
 // questions, so they are batched).
 //
 //   submit   validates a query on the host and queues it (FIFO), returning a ticket.
-//   worker   forms a batch: it waits until the oldest queued query is batch_interval_us
-//            old or max_batch_queries are queued, then admits queries in FIFO order
+//   worker   forms a batch: at once if no batch is in flight, otherwise once the oldest
+//            queued query is batch_interval_us old, max_batch_queries are queued or the
+//            batches in flight have finished; it admits queries in FIFO order
 //            while their bytes fit the free part of the memory region; packs them into
 //            pinned staging memory and launches copy-in, the two kernels and copy-out on
 //            the next of n_streams streams.
@@ -204,9 +205,11 @@ static void worker_loop(ServeState *S) {
   while (true) {
     S->cv_work.wait(lk, [&] { return S->stopping || !S->queue.empty(); });
     if (S->queue.empty()) break;   // stopping and drained
-    // batching window
+    // batching window: an idle GPU takes the queue at once; a busy one lets queries
+    // gather until the oldest has waited batch_interval_us or the GPU drains
     const auto deadline = S->queue.front().t_submit + interval;
-    while (!S->stopping && (int)S->queue.size() < S->cfg.max_batch_queries && Clock::now() < deadline)
+    while (!S->stopping && !S->flight.empty() && (int)S->queue.size() < S->cfg.max_batch_queries &&
+           Clock::now() < deadline)
       S->cv_work.wait_until(lk, deadline);
     // admission: FIFO while the batch fits the largest free block; needs a free event
     if (S->free_events.empty()) {
