@@ -433,7 +433,9 @@ def run_other(args):
                             "argmin_only_ms": ms_arg, "argmin_only_gbs": nb_arg / (ms_arg / 1e3) / 1e9,
                             "fp64_accurate_ms": times["fp64_T"][0]},
                     roofline={"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                              "frac": nbytes / (ms / 1e3) / 1e9 / hbm, "traffic": None, "kernel": "k_predict_tc",
+                              "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
+                              "traffic": _profile_traffic("predict_tc_1e6x32x64.md", ("predict_tc.cu",)),
+                              "kernel": "k_predict_tc",
                               "algorithmic_bytes": "256 B read + 8 B written per (row, model)"},
                     clocks=ck, gpu_launches=args.steps)
     elif args.workload == "fit":
