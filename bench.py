@@ -5,8 +5,10 @@ template, every (variant, point) pair evaluated (exact int64 counts), predicted
 
 One step = one pass of that whole path over the batch.  Prints one JSON line.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Multi-GPU (torchrun): every rank runs the same per-GPU batch (weak scaling); no
-data-path collective, the process group only brackets the timing.
+Multi-GPU (torchrun): every rank ranks its own point batch of the same size (weak
+scaling; rank r draws its points with seed 3 + 7919 r); no data-path collective, the
+process group only brackets the timing (barrier, max over ranks).
+Other workloads: --workload eval | predict | fit | serve.
 """
 from __future__ import annotations
 
@@ -179,6 +181,7 @@ def run_ours(args):
 
     import __graft_entry__
     from paper_1604_04997_gb300 import binding as B
+    from paper_1604_04997_gb300 import sharding
     from paper_1604_04997_gb300 import tuning
     from paper_1604_04997_gb300 import workloads as W
 
@@ -193,7 +196,8 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     ctx = B.Context(local)
     ctx.tune(not args.no_tune, None)
-    bp = tuning.build(ctx, args.variants, args.points)
+    # weak scaling: every rank ranks its own point batch (independent units, no exchange)
+    bp = tuning.build(ctx, args.variants, args.points, point_seed=sharding.rank_point_seed(3, rank))
     w = W.draw_weights(32, 1, 4)[0]
     n = bp.points.shape[0]
     stream = torch.cuda.Stream(dev)
@@ -233,10 +237,8 @@ def run_ours(args):
     ctx.sync_status(stream)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
     ms = sum(step_ms) / len(step_ms)
+    ms = sharding.max_over_ranks(ms, dev)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
 
     # end to end through the C ABI with host buffers: points H2D, ranking D2H, every step
@@ -259,10 +261,7 @@ def run_ours(args):
         e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = sharding.max_over_ranks(e2e_ms, dev)
 
     evals = bp.total_evals
     value = evals * ws / (ms / 1e3)
