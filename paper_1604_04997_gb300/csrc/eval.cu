@@ -99,56 +99,51 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_all;\n" ::); }
 
-__device__ __forceinline__ bool kid_less(int64_t ak, int ai, int64_t bk, int bi) {
-  return ak < bk || (ak == bk && ai < bi);
+// A ranking entry packs the top 48 bits of the monotone key (sign, exponent and 40
+// mantissa bits: 2^-40 relative resolution) above a 16-bit variant index, so one
+// signed 64-bit comparison orders by (key, variant) and exact ties (duplicate
+// variants) fall to the smaller index.  INT64_MAX marks an empty slot.
+constexpr int64_t K2_EMPTY = INT64_MAX;
+__device__ __forceinline__ int64_t pack_entry(int64_t key, int vid) {
+  return (int64_t)(((uint64_t)(key >> 16) << 16) | (uint32_t)vid);
 }
+__device__ __forceinline__ int entry_vid(int64_t e) { return (int)(e & 0xFFFF); }
+__device__ __forceinline__ int64_t entry_key(int64_t e) { return (int64_t)((uint64_t)e & ~0xFFFFull); }
 
-// The 16 best (key, variant) pairs of one point, sorted.  Within one warp variants
-// arrive in increasing index order, so a strict key comparison keeps ties in index order.
+// The 16 best entries of one point, sorted ascending.
 struct TopK {
   int64_t k[K2_TOPK];
-  int id[K2_TOPK];
   __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int q = 0; q < K2_TOPK; q++) { k[q] = INT64_MAX; id[q] = 0x7fffffff; }
+    for (int q = 0; q < K2_TOPK; q++) k[q] = K2_EMPTY;
   }
-  __device__ __forceinline__ void insert(int64_t key, int vid) {
+  __device__ __forceinline__ void insert(int64_t e) {
 #pragma unroll
-    for (int q = K2_TOPK - 1; q > 0; q--) {
-      const bool shift = key < k[q - 1];
-      const bool here = !shift && key < k[q];
-      k[q] = shift ? k[q - 1] : (here ? key : k[q]);
-      id[q] = shift ? id[q - 1] : (here ? vid : id[q]);
-    }
-    if (key < k[0]) { k[0] = key; id[0] = vid; }
+    for (int q = K2_TOPK - 1; q > 0; q--) k[q] = e < k[q - 1] ? k[q - 1] : (e < k[q] ? e : k[q]);
+    if (e < k[0]) k[0] = e;
   }
 };
 
 // Merge n sorted lists of 16 (element (list, q) at list*stride_list + q*stride_q) for this lane.
-template <int MAXN, bool CG>
-__device__ __forceinline__ void merge_lists(const int64_t *ks, const int *is, int n, int stride_list, int stride_q,
-                                            TopK &out) {
+template <int MAXN>
+__device__ __forceinline__ void merge_lists(const int64_t *ks, int n, int stride_list, int stride_q, TopK &out) {
   int head[MAXN];
 #pragma unroll
   for (int w = 0; w < MAXN; w++) head[w] = 0;
 #pragma unroll
   for (int q = 0; q < K2_TOPK; q++) {
     int best = -1;
-    int64_t bk = INT64_MAX;
-    int bi = 0x7fffffff;
+    int64_t bk = K2_EMPTY;
 #pragma unroll
     for (int w = 0; w < MAXN; w++) {
       if (w < n && head[w] < K2_TOPK) {
-        const int o = w * stride_list + head[w] * stride_q;
-        const int64_t xk = CG ? __ldcg(ks + o) : ks[o];
-        const int xi = CG ? __ldcg(is + o) : is[o];
-        if (best < 0 || kid_less(xk, xi, bk, bi)) { best = w; bk = xk; bi = xi; }
+        const int64_t xk = __ldcg(ks + w * stride_list + head[w] * stride_q);
+        if (best < 0 || xk < bk) { best = w; bk = xk; }
       }
     }
 #pragma unroll
     for (int w = 0; w < MAXN; w++) if (w == best) head[w]++;
     out.k[q] = bk;
-    out.id[q] = bi;
   }
 }
 
@@ -170,8 +165,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *tbuf = (uint32_t *)smem;                                  // [2][TB_WORDS]
   int64_t *slots = (int64_t *)(tbuf + 2 * TB_WORDS);                  // [NW][24 slots][32 lanes]
-  int64_t *bk = slots + NW * pmt::MAX_SLOTS * 32;                     // [NW][K2_BUF][32] candidate keys
-  int *bi = (int *)(bk + NW * K2_BUF * 32);                           // [NW][K2_BUF][32] candidate variants
+  int64_t *bk = slots + NW * pmt::MAX_SLOTS * 32;                     // [NW][K2_BUF][32] candidate entries
   __shared__ uint32_t s_w0[pmt::MAX_COLS];
   __shared__ int32_t s_w1[pmt::MAX_COLS];
   __shared__ int s_E, s_unit;
@@ -179,7 +173,6 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t *myslots = slots + warp * pmt::MAX_SLOTS * 32 + lane;
   int64_t *mybk = bk + warp * K2_BUF * 32 + lane;
-  int *mybi = bi + warp * K2_BUF * 32 + lane;
 
   if (threadIdx.x == 0) {
     const int E = weight_exponent(a.w, 32);
@@ -225,14 +218,17 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     }
     TopK tk;
     tk.init();
-    int64_t thr = INT64_MAX;                     // the list's 16th key
-    Acc128 thr_s = {~0ull, (uint64_t)INT64_MAX};  // S < thr_s  <=>  key(S) < thr (thr > 0)
+    // Candidates of this unit arrive in increasing variant order, so one passes iff
+    // its 48-bit key is below the 16th entry's: thr is that key (low 16 bits clear),
+    // and for thr > 0 the exact test is S < key_floor(thr).
+    int64_t thr = entry_key(K2_EMPTY);
+    Acc128 thr_s = {~0ull, (uint64_t)INT64_MAX};
     int nbuf = 0;
     auto flush = [&]() {
-      for (int b = 0; b < nbuf; b++) tk.insert(mybk[b * 32], mybi[b * 32]);
+      for (int b = 0; b < nbuf; b++) tk.insert(mybk[b * 32]);
       nbuf = 0;
-      thr = tk.k[K2_TOPK - 1];
-      if (thr == INT64_MAX) { thr_s.lo = ~0ull; thr_s.hi = (uint64_t)INT64_MAX; }
+      thr = entry_key(tk.k[K2_TOPK - 1]);
+      if (tk.k[K2_TOPK - 1] == K2_EMPTY) { thr_s.lo = ~0ull; thr_s.hi = (uint64_t)INT64_MAX; }
       else if (thr > 0) thr_s = key_floor(thr);
     };
     const int v0 = a.var_off[t];
@@ -262,10 +258,9 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
         if (!ok) atomicOr(a.status, ST_BAD_TABLE);
         const Acc128 S = la.sum();
         // strict: an equal key of a later variant ranks after the earlier one
-        const bool pass = thr > 0 ? acc_less(S, thr_s) : acc_key(S) < thr;
+        const bool pass = thr > 0 ? acc_less(S, thr_s) : entry_key(pack_entry(acc_key(S), 0)) < thr;
         if (pass) {
-          mybk[nbuf * 32] = acc_key(S);
-          mybi[nbuf * 32] = v - v0;
+          mybk[nbuf * 32] = pack_entry(acc_key(S), v - v0);
           nbuf++;
         }
       }
@@ -278,10 +273,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       // publish this slice's lists, then the last slice of the chunk merges all of them
       const int64_t slot0 = (int64_t)(C.w + U.y) * K2_TOPK * (NW * 32) + pl;
 #pragma unroll
-      for (int q = 0; q < K2_TOPK; q++) {
-        a.part_k[slot0 + q * (NW * 32)] = tk.k[q];
-        a.part_i[slot0 + q * (NW * 32)] = tk.id[q];
-      }
+      for (int q = 0; q < K2_TOPK; q++) a.part_k[slot0 + q * (NW * 32)] = tk.k[q];
       __threadfence();
       __syncthreads();
       if (threadIdx.x == 0) s_unit = atomicAdd(a.chunk_count + U.x, 1) == S - 1;
@@ -289,7 +281,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       if (s_unit) {
         __threadfence();
         const int64_t b = (int64_t)C.w * K2_TOPK * (NW * 32) + pl;
-        merge_lists<K2_MAX_SLICES, true>(a.part_k + b, a.part_i + b, S, K2_TOPK * (NW * 32), NW * 32, tk);
+        merge_lists<K2_MAX_SLICES>(a.part_k + b, S, K2_TOPK * (NW * 32), NW * 32, tk);
         write_out = true;
       }
     }
@@ -300,9 +292,9 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 #pragma unroll
       for (int q = 0; q < K2_TOPK; q++) {
         if (q < a.topk) {
-          const bool real = tk.id[q] != 0x7fffffff;
-          oi[q] = real ? tk.id[q] : -1;
-          ot[q] = real ? key_value(tk.k[q], E) : __longlong_as_double(0x7ff0000000000000ll);
+          const bool real = tk.k[q] != K2_EMPTY;
+          oi[q] = real ? entry_vid(tk.k[q]) : -1;
+          ot[q] = real ? key_value(entry_key(tk.k[q]), E) : __longlong_as_double(0x7ff0000000000000ll);
         }
       }
     }
@@ -313,7 +305,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
 int k2_table_words() { return TB_WORDS; }
 
 size_t k2_smem_bytes(int nw) {
-  return (size_t)2 * TB_WORDS * 4 + (size_t)nw * pmt::MAX_SLOTS * 32 * 8 + (size_t)nw * K2_BUF * 32 * 12;
+  return (size_t)2 * TB_WORDS * 4 + (size_t)nw * pmt::MAX_SLOTS * 32 * 8 + (size_t)nw * K2_BUF * 32 * 8;
 }
 
 int k2_points_per_cta(int nw) { return nw * 32; }

@@ -26,8 +26,7 @@ struct K2Args {
   int n_units;
   int *unit_counter;           // reset to 0 before each launch
   int *chunk_count;            // [n_chunks] slices finished, reset to 0 before each launch
-  int64_t *part_k;             // [slots][16][256] partial lists (ranking keys) of chunks with S > 1
-  int *part_i;                 // [slots][16][256] their variant indices
+  int64_t *part_k;             // [slots][16][points per chunk] partial lists (packed entries) of chunks with S > 1
   const int64_t *points;       // [total][4]
   const double *w;             // [32]
   int topk;

@@ -60,9 +60,12 @@ static double table_work(const std::vector<uint32_t> &w) {
 pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, int T, const int64_t *pt_off,
                       Plan **out) {
   if (var_off[0] != 0 || pt_off[0] != 0) return pm_set_error(PM_ERR_INVALID_ARG, "offsets must start at 0");
-  for (int t = 0; t < T; t++)
+  for (int t = 0; t < T; t++) {
     if (var_off[t + 1] < var_off[t] || pt_off[t + 1] < pt_off[t])
       return pm_set_error(PM_ERR_INVALID_ARG, "offsets must be non-decreasing");
+    if (var_off[t + 1] - var_off[t] > 65536)
+      return pm_set_error(PM_ERR_INVALID_ARG, "at most 65,536 variants per template");
+  }
   const int nv = var_off[T];
   const int64_t np = pt_off[T];
   if (np > (int64_t(1) << 31) - 64) return pm_set_error(PM_ERR_INVALID_ARG, "too many points");
@@ -165,8 +168,6 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   const size_t part = (size_t)slots * 16 * UNIT_POINTS;
   if ((s = alloc(nullptr, part * 8, &d))) return s;
   p->d_part_k = (int64_t *)d;
-  if ((s = alloc(nullptr, part * 4, &d))) return s;
-  p->d_part_i = (int *)d;
   p->n_chunks = (int)chunks.size();
   p->n_units = (int)hu.size();
   p->n_templates = T;
@@ -197,7 +198,6 @@ static pm_status launch_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double 
   a.unit_counter = p->d_counter;
   a.chunk_count = p->d_counter + 1;
   a.part_k = p->d_part_k;
-  a.part_i = p->d_part_i;
   a.points = pts;
   a.w = w;
   a.topk = topk;

@@ -23,7 +23,6 @@ struct Plan {
   const int4 *d_units = nullptr;
   int *d_counter = nullptr;
   int64_t *d_part_k = nullptr;
-  int *d_part_i = nullptr;
   int n_units = 0, n_templates = 0, n_chunks = 0;
   int64_t total_points = 0, total_evals = 0;
   double work_per_eval = 0;         // average (atoms + conditions + monomials) per evaluation
