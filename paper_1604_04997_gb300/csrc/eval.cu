@@ -166,8 +166,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   uint32_t *tbuf = (uint32_t *)smem;                                  // [2][TB_WORDS]
   int64_t *slots = (int64_t *)(tbuf + 2 * TB_WORDS);                  // [NW][24 slots][32 lanes]
   int64_t *bk = slots + NW * pmt::MAX_SLOTS * 32;                     // [NW][K2_BUF][32] candidate entries
-  __shared__ uint32_t s_w0[pmt::MAX_COLS];
-  __shared__ int32_t s_w1[pmt::MAX_COLS];
+  __shared__ uint2 s_w[pmt::MAX_COLS];   // fixed-point weight limbs (low 28 bits, signed high part)
   __shared__ int s_E, s_unit;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -178,8 +177,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
     const int E = weight_exponent(a.w, 32);
     for (int c = 0; c < pmt::MAX_COLS; c++) {
       const int64_t W = c < 32 ? llrint(ldexp(a.w[c], E)) : 0;   // |W| < 2^56
-      s_w0[c] = (uint32_t)(W & 0x0FFFFFFF);
-      s_w1[c] = (int32_t)(W >> 28);
+      s_w[c] = make_uint2((uint32_t)(W & 0x0FFFFFFF), (uint32_t)(int32_t)(W >> 28));
     }
     s_E = E;
   }
@@ -253,8 +251,8 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
         la.zero();
         const bool ok = eval_table(
             tbuf + buf * TB_WORDS, n, myslots, 32,
-            [&](int col, int64_t val) { if (col < 32) la.add((uint64_t)val, s_w0[col], s_w1[col]); },
-            [&](int col, int64_t val) { la.add((uint64_t)val, s_w0[col], s_w1[col]); });
+            [&](int col, int64_t val) { if (col < 32) la.add((uint64_t)val, s_w[col]); },
+            [&](int col, int64_t val) { la.add((uint64_t)val, s_w[col]); });
         if (!ok) atomicOr(a.status, ST_BAD_TABLE);
         const Acc128 S = la.sum();
         // strict: an equal key of a later variant ranks after the earlier one

@@ -140,19 +140,25 @@ struct Acc128 {
   __device__ __forceinline__ void zero() { lo = hi = 0; }
 };
 
+// Exact sum of count x weight products in four 64-bit limb accumulators.  A count
+// v (0 <= v < 2^62) is split into 28-bit limbs v0, v1 and the top bits v2; a weight
+// W = w.y 2^28 + w.x (w.x in [0, 2^28), |w.y| < 2^28).  Each partial product is one
+// 32x32 -> 64-bit multiply-add; with at most 34 terms no accumulator overflows.
 struct LimbAcc {
   uint64_t l0;
   int64_t l1, l2, l3;
   __device__ __forceinline__ void zero() { l0 = 0; l1 = l2 = l3 = 0; }
-  __device__ __forceinline__ void add(uint64_t v, uint32_t w0, int32_t w1) {
+  __device__ __forceinline__ void add(uint64_t v, uint2 w) {
     const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
     const uint32_t v0 = lo & 0x0FFFFFFFu;
     const uint32_t v1 = __funnelshift_r(lo, hi, 28) & 0x0FFFFFFFu;
-    const int32_t v2 = (int32_t)(hi >> 24);
-    l0 += (uint64_t)v0 * w0;
-    l1 += (int64_t)(int32_t)v0 * w1 + (int64_t)(int32_t)v1 * (int32_t)w0;
-    l2 += (int64_t)(int32_t)v1 * w1 + (int64_t)v2 * (int32_t)w0;
-    l3 += (int64_t)v2 * w1;
+    const uint32_t v2 = hi >> 24;
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l0) : "r"(v0), "r"(w.x));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l1) : "r"(v0), "r"(w.y));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l1) : "r"(v1), "r"(w.x));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v1), "r"(w.y));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v2), "r"(w.x));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l3) : "r"(v2), "r"(w.y));
   }
   __device__ __forceinline__ Acc128 sum() const {
     // S = l0 + l1 2^28 + l2 2^56 + l3 2^84, in 128-bit two's complement

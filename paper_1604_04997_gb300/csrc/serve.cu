@@ -17,7 +17,7 @@ constexpr int SV_TOPK_THREADS = 256;
 
 // Per-model fixed-point weights W_i = round(w_i 2^E) as 28-bit limb pairs, computed by
 // warp 0 (lane i holds weight i); every CTA of a batch derives the same values.
-__device__ __forceinline__ void load_model_limbs(const double *w, uint32_t *s_w0, int32_t *s_w1, int *s_E) {
+__device__ __forceinline__ void load_model_limbs(const double *w, uint2 *s_w, int *s_E) {
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
     const double x = w[lane];
@@ -28,20 +28,18 @@ __device__ __forceinline__ void load_model_limbs(const double *w, uint32_t *s_w0
     if (mx > 0) frexp(mx, &e);
     const int E = 56 - e;
     const int64_t W = llrint(ldexp(x, E));   // |W| < 2^56
-    s_w0[lane] = (uint32_t)(W & 0x0FFFFFFF);
-    s_w1[lane] = (int32_t)(W >> 28);
+    s_w[lane] = make_uint2((uint32_t)(W & 0x0FFFFFFF), (uint32_t)(int32_t)(W >> 28));
     if (lane == 0) *s_E = E;
   }
 }
 
 __global__ void __launch_bounds__(SV_THREADS) k_serve_eval(ServeArgs a) {
   __shared__ int64_t slots[pmt::MAX_SLOTS * SV_THREADS];
-  __shared__ uint32_t s_w0[32];
-  __shared__ int32_t s_w1[32];
+  __shared__ uint2 s_w[32];
   __shared__ int s_E;
   const int2 b = a.blocks[blockIdx.x];
   const SQuery q = a.queries[b.x];
-  load_model_limbs(a.models + (int64_t)q.model * 32, s_w0, s_w1, &s_E);
+  load_model_limbs(a.models + (int64_t)q.model * 32, s_w, &s_E);
   __syncthreads();
   const int i = b.y * SV_THREADS + threadIdx.x;
   if (i >= q.n) return;
@@ -56,8 +54,8 @@ __global__ void __launch_bounds__(SV_THREADS) k_serve_eval(ServeArgs a) {
     la.zero();
     const bool ok = eval_table(
         T, n, slots + threadIdx.x, SV_THREADS,
-        [&](int col, int64_t val) { if (col < 32) la.add((uint64_t)val, s_w0[col], s_w1[col]); },
-        [&](int col, int64_t val) { la.add((uint64_t)val, s_w0[col], s_w1[col]); });
+        [&](int col, int64_t val) { if (col < 32) la.add((uint64_t)val, s_w[col]); },
+        [&](int col, int64_t val) { la.add((uint64_t)val, s_w[col]); });
     if (!ok) atomicOr(a.q_status + b.x, ST_BAD_TABLE);
     else key = acc_key(la.sum());
   }
@@ -97,13 +95,12 @@ __device__ __forceinline__ bool pair_less(int64_t ka, int32_t ia, int64_t kb, in
 }
 
 __global__ void __launch_bounds__(SV_TOPK_THREADS) k_serve_topk(ServeArgs a) {
-  __shared__ uint32_t s_w0[32];
-  __shared__ int32_t s_w1[32];
+  __shared__ uint2 s_w[32];
   __shared__ int s_E;
   __shared__ int64_t r_k[SV_TOPK_THREADS / 32];
   __shared__ int32_t r_i[SV_TOPK_THREADS / 32];
   const SQuery q = a.queries[blockIdx.x];
-  load_model_limbs(a.models + (int64_t)q.model * 32, s_w0, s_w1, &s_E);
+  load_model_limbs(a.models + (int64_t)q.model * 32, s_w, &s_E);
   SvList L;
   L.init();
   for (int i = threadIdx.x; i < q.n; i += SV_TOPK_THREADS) L.insert(a.keys[q.begin + i], i);
