@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "eval_common.cuh"
 #include "kernels.h"
 
@@ -99,6 +101,144 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_all;\n" ::); }
 
+// A += W * v (mod 2^128): W a 128-bit two's-complement weight (four 32-bit limbs),
+// v a signed 64-bit slot value.  Twelve 32-bit multiply-adds in carry chains, then
+// the sign correction of v (v = v_unsigned - 2^64 when negative).  Since the exact
+// sum of all terms lies within +-2^124, the modular sum is that sum.
+__device__ __forceinline__ void mac128(uint32_t (&A)[4], const uint4 &W, int64_t v) {
+  const uint32_t s0 = (uint32_t)v, s1 = (uint32_t)((uint64_t)v >> 32);
+  asm("mad.lo.cc.u32  %0, %4, %8, %0;\n\t"
+      "madc.lo.cc.u32 %1, %5, %8, %1;\n\t"
+      "madc.lo.cc.u32 %2, %6, %8, %2;\n\t"
+      "madc.lo.u32    %3, %7, %8, %3;\n\t"
+      "mad.hi.cc.u32  %1, %4, %8, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %8, %2;\n\t"
+      "madc.hi.u32    %3, %6, %8, %3;\n\t"
+      "mad.lo.cc.u32  %1, %4, %9, %1;\n\t"
+      "madc.lo.cc.u32 %2, %5, %9, %2;\n\t"
+      "madc.lo.u32    %3, %6, %9, %3;\n\t"
+      "mad.hi.cc.u32  %2, %4, %9, %2;\n\t"
+      "madc.hi.u32    %3, %5, %9, %3;\n\t"
+      : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3])
+      : "r"(W.x), "r"(W.y), "r"(W.z), "r"(W.w), "r"(s0), "r"(s1));
+  if (v < 0) {
+    asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %3;\n\t" : "+r"(A[2]), "+r"(A[3]) : "r"(W.x), "r"(W.y));
+  }
+}
+
+// Fill the 128-bit slot weights of the K2 programs: Weff = sum over contributions of
+// W_col * coef, with W_col = round(w_col 2^E) the fixed-point weights (|W| < 2^56).
+__global__ void __launch_bounds__(128) k_k2_weights(uint32_t *__restrict__ prog, const uint4 *__restrict__ targets,
+                                                    const uint4 *__restrict__ contrib, int n_targets,
+                                                    const double *__restrict__ w) {
+  __shared__ uint4 sW[32];   // each weight sign-extended to 128 bits
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double x = w[lane];
+    double mx = fabs(x);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    int e = 0;
+    if (mx > 0) frexp(mx, &e);
+    const int64_t W = llrint(ldexp(x, 56 - e));
+    const uint32_t sx = W < 0 ? 0xFFFFFFFFu : 0u;
+    sW[lane] = make_uint4((uint32_t)W, (uint32_t)((uint64_t)W >> 32), sx, sx);
+  }
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_targets; i += gridDim.x * blockDim.x) {
+    const uint4 tg = targets[i];
+    uint32_t A[4] = {0, 0, 0, 0};
+    for (uint32_t c = 0; c < tg.z; c++) {
+      const uint4 cb = contrib[tg.y + c];
+      mac128(A, sW[cb.x & 31], (int64_t)((uint64_t)cb.z | ((uint64_t)cb.w << 32)));
+    }
+    *(uint4 *)(prog + tg.x) = make_uint4(A[0], A[1], A[2], A[3]);
+  }
+}
+
+cudaError_t launch_k2_weights(uint32_t *prog, const uint4 *targets, const uint4 *contrib, int n_targets,
+                              const double *w, cudaStream_t st) {
+  const int grid = std::max(1, std::min(1024, (n_targets + 127) / 128));
+  k_k2_weights<<<grid, 128, 0, st>>>(prog, targets, contrib, n_targets, w);
+  return cudaGetLastError();
+}
+
+// Evaluate a K2 program (table + weight image) at n and return the exact fixed-point
+// prediction S = sum_col W_col p_col(n) (128 bits).  Same values, pieces and products
+// as eval_table; the column sums and the dot product are one pass over the piece's
+// weighted slots, plus the held columns and post-ops.  Returns false on a malformed
+// program.
+__device__ __forceinline__ bool eval_dot(const uint32_t *__restrict__ T, const int32_t *n, int64_t *slots, int ss,
+                                         Acc128 &S) {
+  const int P = (int)T[pmt::H_NPARAMS];
+  const int A = (int)T[pmt::H_NATOMS];
+  const int NC = (int)T[pmt::H_NCONDS];
+  if (P > 4 || P + A > pmt::MAX_VALUES || NC > pmt::MAX_CONDS) return false;
+#pragma unroll
+  for (int p = 0; p < 4; p++) {
+    if (p < P) slots[p * ss] = n[p];
+    slots[(pmt::HOLD_SLOT + p) * ss] = 0;
+  }
+  slots[pmt::CONST_SLOT * ss] = 1;
+  const uint32_t *at = T + T[pmt::H_OFF_ATOMS];
+  for (int a = 0; a < A; a++, at += pmt::ATOM_WORDS) {
+    const uint4 q0 = *(const uint4 *)at, q1 = *(const uint4 *)(at + 4);
+    int32_t num = (int32_t)q1.x;
+    num += (int32_t)q0.x * n[0];
+    if (P > 1) num += (int32_t)q0.y * n[1];
+    if (P > 2) num += (int32_t)q0.z * n[2];
+    if (P > 3) num += (int32_t)q0.w * n[3];
+    slots[(P + a) * ss] = floor_div(num, q1.y, q1.z, (q1.w >> 8) & 0xFF, (q1.w >> 16) & 1);
+  }
+  uint32_t bits = 0;
+  const uint32_t *cd = T + T[pmt::H_OFF_CONDS];
+  for (int c = 0; c < NC; c++) {
+    const int nt = (int)cd[0];
+    int64_t s = ld64(cd + 1);
+    for (int t = 0; t < nt; t++)
+      s += (int64_t)(int32_t)cd[4 + 2 * t] * slots[min(cd[3 + 2 * t], (uint32_t)pmt::MAX_SLOTS - 1) * ss];
+    bits |= (uint32_t)(s >= 0) << c;
+    cd += 3 + 2 * nt;
+  }
+  const uint32_t *lut = T + T[pmt::H_OFF_LUT];
+  const uint32_t piece = (lut[bits >> 2] >> (8 * (bits & 3))) & 0xFF;
+  if (piece >= T[pmt::H_NPIECES]) return false;
+  const uint4 pc = *(const uint4 *)(T + T[pmt::H_OFF_PIECES] + 4 * piece);
+  if (P + A + pc.y > (uint32_t)pmt::MAX_PRODS) return false;
+  const uint32_t *pr = T + T[pmt::H_OFF_PRODS] + pc.x;
+  int64_t *dst = slots + (P + A) * ss;
+  for (uint32_t j = 0; j < pc.y; j++, dst += ss) {
+    const uint32_t w = pr[j];
+    *dst = (int64_t)((uint64_t)slots[min(w & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss] *
+                     (uint64_t)slots[min((w >> 8) & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
+  }
+  const uint32_t I = (T[pmt::H_OFF_ENTRIES] + 3) & ~3u;
+  const uint4 ip = *(const uint4 *)(T + I + 4 + 4 * piece);
+  uint32_t acc[4] = {0, 0, 0, 0};
+  const uint4 *dw = (const uint4 *)(T + ip.x);
+  const uint32_t *ds = T + ip.z;
+  for (uint32_t d = 0; d < ip.y; d++) mac128(acc, dw[d], slots[min(ds[d], (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
+  const uint4 *hl = (const uint4 *)(T + (ip.w & 0xFFFF));
+  for (uint32_t h = 0; h < (ip.w >> 16); h++) {
+    const uint4 E = hl[h];
+    const uint64_t coef = (uint64_t)E.z | ((uint64_t)E.w << 32);
+    int64_t *hs = slots + (pmt::HOLD_SLOT + ((E.x >> 8) & 3)) * ss;
+    *hs += (int64_t)(coef * (uint64_t)slots[min(E.x & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
+  }
+  const uint32_t npost = T[I];
+  const uint4 *pw = (const uint4 *)(T + T[I + 1]);
+  const uint32_t *ph = T + T[I + 2];
+  for (uint32_t q = 0; q < npost; q++) {
+    const uint32_t hw = ph[q];
+    const int64_t va = slots[(pmt::HOLD_SLOT + (hw & 3)) * ss];
+    const int64_t vb = slots[(pmt::HOLD_SLOT + ((hw >> 8) & 3)) * ss];
+    mac128(acc, pw[q], va < vb ? va : vb);
+  }
+  S.lo = (uint64_t)acc[0] | ((uint64_t)acc[1] << 32);
+  S.hi = (uint64_t)acc[2] | ((uint64_t)acc[3] << 32);
+  return true;
+}
+
 // A ranking entry packs the top 48 bits of the monotone key (sign, exponent and 40
 // mantissa bits: 2^-40 relative resolution) above a 16-bit variant index, so one
 // signed 64-bit comparison orders by (key, variant) and exact ties (duplicate
@@ -166,21 +306,13 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
   uint32_t *tbuf = (uint32_t *)smem;                                  // [2][TB_WORDS]
   int64_t *slots = (int64_t *)(tbuf + 2 * TB_WORDS);                  // [NW][24 slots][32 lanes]
   int64_t *bk = slots + NW * pmt::MAX_SLOTS * 32;                     // [NW][K2_BUF][32] candidate entries
-  __shared__ uint2 s_w[pmt::MAX_COLS];   // fixed-point weight limbs (low 28 bits, signed high part)
   __shared__ int s_E, s_unit;
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t *myslots = slots + warp * pmt::MAX_SLOTS * 32 + lane;
   int64_t *mybk = bk + warp * K2_BUF * 32 + lane;
 
-  if (threadIdx.x == 0) {
-    const int E = weight_exponent(a.w, 32);
-    for (int c = 0; c < pmt::MAX_COLS; c++) {
-      const int64_t W = c < 32 ? llrint(ldexp(a.w[c], E)) : 0;   // |W| < 2^56
-      s_w[c] = make_uint2((uint32_t)(W & 0x0FFFFFFF), (uint32_t)(int32_t)(W >> 28));
-    }
-    s_E = E;
-  }
+  if (threadIdx.x == 0) s_E = weight_exponent(a.w, 32);   // the programs' weights are round(w 2^E)
   __syncthreads();
 
   while (true) {
@@ -235,7 +367,7 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       if (vv < ve) {
         const uint64_t po = a.tab_off[vv];
         const int words = min((int)(po >> 40), TB_WORDS);
-        const uint32_t *g = a.arena + (po & OFF_MASK);
+        const uint32_t *g = a.prog + (po & OFF_MASK);
         for (int i = threadIdx.x; i < words / 4; i += NW * 32) cp_async16(tbuf + buf * TB_WORDS + 4 * i, g + 4 * i);
       }
       cp_async_commit();
@@ -247,14 +379,12 @@ __global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
       __syncthreads();                  // table v visible; table v-1 no longer read by any warp
       stage(v + 1, buf ^ 1);            // overlaps with the evaluation of table v
       if (valid) {
-        LimbAcc la;
-        la.zero();
-        const bool ok = eval_table(
-            tbuf + buf * TB_WORDS, n, myslots, 32,
-            [&](int col, int64_t val) { if (col < 32) la.add((uint64_t)val, s_w[col]); },
-            [&](int col, int64_t val) { la.add((uint64_t)val, s_w[col]); });
-        if (!ok) atomicOr(a.status, ST_BAD_TABLE);
-        const Acc128 S = la.sum();
+        Acc128 S;
+        if (!eval_dot(tbuf + buf * TB_WORDS, n, myslots, 32, S)) {
+          atomicOr(a.status, ST_BAD_TABLE);
+          S.lo = ~0ull;
+          S.hi = (uint64_t)INT64_MAX;
+        }
         // strict: an equal key of a later variant ranks after the earlier one
         const bool pass = thr > 0 ? acc_less(S, thr_s) : entry_key(pack_entry(acc_key(S), 0)) < thr;
         if (pass) {

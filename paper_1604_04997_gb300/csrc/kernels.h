@@ -15,8 +15,8 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
 // K2 (eval.cu)
 constexpr int K2_MAX_SLICES = 16;
 struct K2Args {
-  const uint32_t *arena;
-  const uint64_t *tab_off;     // [n_variants] word offset into arena | table words << 40
+  const uint32_t *prog;        // K2 programs: table words followed by the weight image
+  const uint64_t *tab_off;     // [n_variants] word offset into prog | program words << 40
   const int32_t *var_off;      // [n_templates+1] CSR into tab_off
   const int32_t *tmpl_nparams; // [n_templates]
   const int32_t *tmpl_slices;  // [n_templates] variant slices S per point chunk (<= K2_MAX_SLICES)
@@ -35,6 +35,9 @@ struct K2Args {
   int *status;
 };
 cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st);
+// fill the 128-bit weights of the K2 programs from w (fp64 [32])
+cudaError_t launch_k2_weights(uint32_t *prog, const uint4 *targets, const uint4 *contrib, int n_targets,
+                              const double *w, cudaStream_t st);
 int k2_max_blocks_per_sm(int nw);
 int k2_table_words();
 int k2_points_per_cta(int nw);

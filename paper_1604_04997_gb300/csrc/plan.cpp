@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <fstream>
+#include <map>
 #include <numeric>
 #include <sstream>
 #include <string>
@@ -57,6 +58,91 @@ static double table_work(const std::vector<uint32_t> &w) {
   return ops + per / np;
 }
 
+// K2 program of one table: the table's words up to its entries, then a weight image that turns the
+// per-column sums and the weight dot product into one dot product over the piece's
+// evaluation slots (sum_col W_col sum_e coef_e slot_e = sum_slot Weff_slot slot).
+// The image holds, per piece, the slots with their 128-bit weights Weff (filled on
+// the device from the call's weights: `targets` name each weight's position and its
+// (column, coefficient) contributions), the entries of the columns that feed post-ops
+// (their sums are needed for min()), and per post-op its weight and hold pair.
+//   image (word I = the table's entry offset rounded up to 4): [n_post, post_w, post_h, 0]
+//   then per piece [dot_w, n_dot, dot_s, hold_off | n_hold << 16]
+//   dot_w: n_dot uint4 weights; dot_s: n_dot slot words; hold_off: n_hold uint4
+//   {slot | hold << 8, 0, coef_lo, coef_hi}; post_w: n_post uint4 weights; post_h:
+//   n_post words {hold A | hold B << 8}.  Offsets are words from the program start.
+static bool build_k2_program(const std::vector<uint32_t> &T, uint32_t base, std::vector<uint32_t> &out,
+                             std::vector<uint4> &targets, std::vector<uint4> &contrib) {
+  auto pad4 = [&]() { while (out.size() % 4) out.push_back(0); };
+  out.assign(T.begin(), T.begin() + T[pmt::H_OFF_ENTRIES]);   // entries and post-ops are replaced by the image
+  pad4();
+  const uint32_t I = (uint32_t)out.size();
+  const uint32_t npieces = T[pmt::H_NPIECES], npost = T[pmt::H_NPOST];
+  out.resize(I + 4 + 4 * npieces, 0);
+  auto add_target = [&](uint32_t word, const std::vector<std::pair<uint32_t, uint64_t>> &cs) {
+    targets.push_back(make_uint4(base + word, (uint32_t)contrib.size(), (uint32_t)cs.size(), 0));
+    for (auto &cc : cs) contrib.push_back(make_uint4(cc.first, 0, (uint32_t)cc.second, (uint32_t)(cc.second >> 32)));
+  };
+  for (uint32_t p = 0; p < npieces; p++) {
+    const uint32_t *pc = T.data() + T[pmt::H_OFF_PIECES] + 4 * p;
+    const uint32_t *en = T.data() + T[pmt::H_OFF_ENTRIES] + pmt::ENTRY_WORDS * pc[2];
+    std::map<uint32_t, std::vector<std::pair<uint32_t, uint64_t>>> by_slot;
+    std::vector<uint4> holds;
+    size_t col_begin = 0;
+    std::vector<uint4> col_entries;
+    for (uint32_t e = 0; e < pc[3]; e++, en += pmt::ENTRY_WORDS) {
+      const uint32_t col = en[2] & 0xFF, slot = (en[2] >> 8) & 0xFF;
+      if (slot >= (uint32_t)pmt::MAX_SLOTS) return false;
+      const uint64_t coef = (uint64_t)en[0] | ((uint64_t)en[1] << 32);
+      if (col < 32) by_slot[slot].push_back({col, coef});
+      col_entries.push_back(make_uint4(slot, 0, en[0], en[1]));
+      if (en[2] & pmt::ENTRY_LAST) {
+        const uint32_t hold = (en[2] >> 16) & 0xF;
+        if (hold) {
+          if (hold > (uint32_t)pmt::MAX_HOLD) return false;
+          for (size_t i = col_begin; i < col_entries.size(); i++) {
+            uint4 h = col_entries[i];
+            h.x |= (hold - 1) << 8;
+            holds.push_back(h);
+          }
+        }
+        col_begin = col_entries.size();
+      }
+    }
+    const uint32_t dot_w = (uint32_t)out.size();
+    for (auto &kv : by_slot) {
+      add_target((uint32_t)out.size(), kv.second);
+      out.resize(out.size() + 4, 0);
+    }
+    const uint32_t dot_s = (uint32_t)out.size();
+    for (auto &kv : by_slot) out.push_back(kv.first);
+    pad4();
+    const uint32_t hold_off = (uint32_t)out.size();
+    for (const uint4 &h : holds) { out.push_back(h.x); out.push_back(h.y); out.push_back(h.z); out.push_back(h.w); }
+    if (hold_off >= 65536 || holds.size() >= 65536) return false;
+    uint32_t *ip = out.data() + I + 4 + 4 * p;
+    ip[0] = dot_w;
+    ip[1] = (uint32_t)by_slot.size();
+    ip[2] = dot_s;
+    ip[3] = hold_off | ((uint32_t)holds.size() << 16);
+  }
+  const uint32_t post_w = (uint32_t)out.size();
+  for (uint32_t q = 0; q < npost; q++) {
+    const uint32_t w = T[T[pmt::H_OFF_POST] + q];
+    add_target((uint32_t)out.size(), {{w & 0xFF, 1ull}});
+    out.resize(out.size() + 4, 0);
+  }
+  const uint32_t post_h = (uint32_t)out.size();
+  for (uint32_t q = 0; q < npost; q++) {
+    const uint32_t w = T[T[pmt::H_OFF_POST] + q];
+    out.push_back(((w >> 8) & 3) | (((w >> 16) & 3) << 8));
+  }
+  pad4();
+  out[I] = npost;
+  out[I + 1] = post_w;
+  out[I + 2] = post_h;
+  return true;
+}
+
 pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, int T, const int64_t *pt_off,
                       Plan **out) {
   if (var_off[0] != 0 || pt_off[0] != 0) return pm_set_error(PM_ERR_INVALID_ARG, "offsets must start at 0");
@@ -78,6 +164,9 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   if (it != c->plans.end()) { *out = it->second; return PM_OK; }
 
   std::vector<int64_t> off(nv);
+  std::vector<uint32_t> prog;                                   // K2 programs of the distinct tables
+  std::vector<uint4> targets, contrib;                          // their weight-fill recipes
+  std::map<int, std::pair<uint32_t, uint32_t>> prog_of;         // table id -> (word offset, words)
   std::vector<int32_t> nparams(T, 0);
   std::vector<double> tw(T, 0);
   std::vector<int4> box(2 * T, make_int4(0, 0, 0, 0));
@@ -100,7 +189,19 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
       if (v == var_off[t]) { box[2 * t] = lo; box[2 * t + 1] = hi; }
       else if (std::memcmp(&box[2 * t], &lo, sizeof lo) || std::memcmp(&box[2 * t + 1], &hi, sizeof hi))
         return pm_set_error(PM_ERR_UNSUPPORTED, "variants of one template must share one parameter box");
-      off[v] = (int64_t)((uint64_t)c->dev_off[id] | ((uint64_t)w[pmt::H_WORDS] << 40));
+      auto pit = prog_of.find(id);
+      if (pit == prog_of.end()) {
+        std::vector<uint32_t> pw;
+        const uint32_t base = (uint32_t)prog.size();
+        if (!build_k2_program(w, base, pw, targets, contrib))
+          return pm_set_error(PM_ERR_INVALID_ARG, "malformed table");
+        if ((int)pw.size() > pmd::k2_table_words())
+          return pm_set_error(PM_ERR_UNSUPPORTED, "fused ranking needs tables whose program fits " +
+                                                      std::to_string(pmd::k2_table_words() * 4) + " bytes");
+        prog.insert(prog.end(), pw.begin(), pw.end());
+        pit = prog_of.emplace(id, std::make_pair(base, (uint32_t)pw.size())).first;
+      }
+      off[v] = (int64_t)((uint64_t)pit->second.first | ((uint64_t)pit->second.second << 40));
       tw[t] += table_work(w);
     }
   }
@@ -151,6 +252,13 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
   pm_status s;
   if ((s = alloc(off.data(), off.size() * 8, &d))) return s;
   p->d_tab_off = (const uint64_t *)d;
+  if ((s = alloc(prog.data(), prog.size() * 4, &d))) return s;
+  p->d_prog = (uint32_t *)d;
+  if ((s = alloc(targets.data(), targets.size() * sizeof(uint4), &d))) return s;
+  p->d_targets = (const uint4 *)d;
+  if ((s = alloc(contrib.data(), contrib.size() * sizeof(uint4), &d))) return s;
+  p->d_contrib = (const uint4 *)d;
+  p->n_targets = (int)targets.size();
   if ((s = alloc(var_off, sizeof(int32_t) * (T + 1), &d))) return s;
   p->d_var_off = (const int32_t *)d;
   if ((s = alloc(nparams.data(), sizeof(int32_t) * T, &d))) return s;
@@ -185,8 +293,9 @@ pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, 
 static pm_status launch_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w, int topk, int32_t *idx,
                            double *t, cudaStream_t st, int nw, int grid) {
   CU(cudaMemsetAsync(p->d_counter, 0, sizeof(int) * (p->n_chunks + 1), st));
+  CU(pmd::launch_k2_weights(p->d_prog, p->d_targets, p->d_contrib, p->n_targets, w, st));
   pmd::K2Args a;
-  a.arena = c->arena;
+  a.prog = p->d_prog;
   a.tab_off = p->d_tab_off;
   a.var_off = p->d_var_off;
   a.tmpl_nparams = p->d_nparams;
@@ -306,7 +415,7 @@ pm_status ctx_run_k2(pm_ctx *c, Plan *p, const int64_t *pts, const double *w, in
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (st) CU(cudaStreamIsCapturing(st, &cs));
   if (!st || cs != cudaStreamCaptureStatusNone) return launch_k2(c, p, pts, w, topk, idx, t, st, p->nw, p->grid);
-  const void *key[6] = {pts, w, idx, t, c->arena, st};
+  const void *key[6] = {pts, w, idx, t, p->d_prog, st};
   bool same = p->graph_exec && p->g_topk == topk && p->g_nw == p->nw && p->g_grid == p->grid &&
               std::memcmp(key, p->g_key, sizeof key) == 0;
   if (!same) {

@@ -14,7 +14,11 @@ struct ServeState;
 // Cached schedule of one pm_eval_predict_topk argument set.
 struct Plan {
   std::vector<void *> dev;          // device allocations owned by the plan
-  const uint64_t *d_tab_off = nullptr;    // word offset | table words << 40
+  const uint64_t *d_tab_off = nullptr;    // per variant: program word offset | program words << 40
+  uint32_t *d_prog = nullptr;             // K2 programs (tables + weight images) of the distinct tables
+  const uint4 *d_targets = nullptr;       // weight-fill recipe: (word, first contribution, count)
+  const uint4 *d_contrib = nullptr;       // contributions (column, -, coef lo, coef hi)
+  int n_targets = 0;
   const int32_t *d_var_off = nullptr;
   const int32_t *d_nparams = nullptr;
   const int32_t *d_slices = nullptr;
