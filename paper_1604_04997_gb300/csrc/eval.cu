@@ -214,12 +214,17 @@ __device__ __forceinline__ bool eval_dot(const uint32_t *__restrict__ T, const i
   }
   const uint32_t I = (T[pmt::H_OFF_ENTRIES] + 3) & ~3u;
   const uint4 ip = *(const uint4 *)(T + I + 4 + 4 * piece);
-  uint32_t acc[4] = {0, 0, 0, 0};
   const uint4 *dw = (const uint4 *)(T + ip.x);
   const uint32_t *ds = T + ip.z;
-  for (uint32_t d = 0; d < ip.y; d++) mac128(acc, dw[d], slots[min(ds[d], (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
+  const uint32_t d0 = ip.w >> 31;   // the first weight belongs to the constant slot (value 1)
+  uint32_t acc[4] = {0, 0, 0, 0};
+  if (d0) {
+    const uint4 c = dw[0];
+    acc[0] = c.x; acc[1] = c.y; acc[2] = c.z; acc[3] = c.w;
+  }
+  for (uint32_t d = d0; d < ip.y; d++) mac128(acc, dw[d], slots[min(ds[d], (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
   const uint4 *hl = (const uint4 *)(T + (ip.w & 0xFFFF));
-  for (uint32_t h = 0; h < (ip.w >> 16); h++) {
+  for (uint32_t h = 0; h < ((ip.w >> 16) & 0x7FFF); h++) {
     const uint4 E = hl[h];
     const uint64_t coef = (uint64_t)E.z | ((uint64_t)E.w << 32);
     int64_t *hs = slots + (pmt::HOLD_SLOT + ((E.x >> 8) & 3)) * ss;

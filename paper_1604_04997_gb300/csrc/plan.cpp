@@ -66,7 +66,7 @@ static double table_work(const std::vector<uint32_t> &w) {
 // (column, coefficient) contributions), the entries of the columns that feed post-ops
 // (their sums are needed for min()), and per post-op its weight and hold pair.
 //   image (word I = the table's entry offset rounded up to 4): [n_post, post_w, post_h, 0]
-//   then per piece [dot_w, n_dot, dot_s, hold_off | n_hold << 16]
+//   then per piece [dot_w, n_dot, dot_s, hold_off | n_hold << 16 | const-first << 31]
 //   dot_w: n_dot uint4 weights; dot_s: n_dot slot words; hold_off: n_hold uint4
 //   {slot | hold << 8, 0, coef_lo, coef_hi}; post_w: n_post uint4 weights; post_h:
 //   n_post words {hold A | hold B << 8}.  Offsets are words from the program start.
@@ -108,22 +108,26 @@ static bool build_k2_program(const std::vector<uint32_t> &T, uint32_t base, std:
         col_begin = col_entries.size();
       }
     }
+    // the constant slot, when present, goes first: its product is the weight itself
+    std::vector<std::pair<uint32_t, std::vector<std::pair<uint32_t, uint64_t>>>> dots(by_slot.begin(), by_slot.end());
+    const bool has_const = !dots.empty() && dots.back().first == pmt::CONST_SLOT;
+    if (has_const) std::rotate(dots.begin(), dots.end() - 1, dots.end());
     const uint32_t dot_w = (uint32_t)out.size();
-    for (auto &kv : by_slot) {
+    for (auto &kv : dots) {
       add_target((uint32_t)out.size(), kv.second);
       out.resize(out.size() + 4, 0);
     }
     const uint32_t dot_s = (uint32_t)out.size();
-    for (auto &kv : by_slot) out.push_back(kv.first);
+    for (auto &kv : dots) out.push_back(kv.first);
     pad4();
     const uint32_t hold_off = (uint32_t)out.size();
     for (const uint4 &h : holds) { out.push_back(h.x); out.push_back(h.y); out.push_back(h.z); out.push_back(h.w); }
-    if (hold_off >= 65536 || holds.size() >= 65536) return false;
+    if (hold_off >= 65536 || holds.size() >= 32768) return false;
     uint32_t *ip = out.data() + I + 4 + 4 * p;
     ip[0] = dot_w;
     ip[1] = (uint32_t)by_slot.size();
     ip[2] = dot_s;
-    ip[3] = hold_off | ((uint32_t)holds.size() << 16);
+    ip[3] = hold_off | ((uint32_t)holds.size() << 16) | (has_const ? 1u << 31 : 0u);
   }
   const uint32_t post_w = (uint32_t)out.size();
   for (uint32_t q = 0; q < npost; q++) {
