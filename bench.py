@@ -275,7 +275,7 @@ def run_ours(args):
     peak_ops = sms * 128 * max_mhz * 1e6           # lane-instruction issue rate at the maximum clock
     achieved = evals * info["work_per_eval"] / (ms / 1e3)
     traffic = _profile_traffic("eval_predict_topk_batched_10000x4096.md",
-                               ("eval.cu", "eval_common.cuh", "pm_table.h"))
+                               ("eval.cu", "eval_common.cuh", "pm_table.h", "plan.cpp"))
 
     if rank == 0:
         line = {
