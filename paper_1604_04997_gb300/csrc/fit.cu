@@ -66,14 +66,16 @@ __global__ void k_scale(const int64_t *__restrict__ F, int64_t R, int k, const u
 
 // ---- row factors as float-float: 1/t (relative) or 1 (absolute); beta = 1 or t
 __global__ void k_rowfac(const double *__restrict__ T, int64_t n, int objective, float2 *__restrict__ rf,
-                         float2 *__restrict__ beta) {
+                         float2 *__restrict__ beta, double *__restrict__ inv, int *status) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double t = T[i];
+    if (!(t > 0.0) || t > 1e300) atomicOr(status, ST_BAD_INPUT);
     const double r = objective == PM_FIT_RELATIVE ? 1.0 / t : 1.0;
     const double b = objective == PM_FIT_RELATIVE ? 1.0 : t;
     const float rh = __double2float_rn(r), bh = __double2float_rn(b);
     rf[i] = make_float2(rh, __double2float_rn(r - (double)rh));
     beta[i] = make_float2(bh, __double2float_rn(b - (double)bh));
+    inv[i] = r;   // 1/t once, reused by every residual
   }
 }
 
@@ -126,73 +128,80 @@ __device__ __forceinline__ int acol_exp(unsigned bits) {
 // Grid (row chunks, models).  Each CTA accumulates, for its model, the upper triangle
 // of sum_r v_r v_r^T and sum_r v_r * beta_r over its rows, where
 // relative: v = u / t, beta = 1;   absolute: v = u, beta = t.
-// Each thread owns up to 3 of the (k(k+1)/2 + k) sums, accumulated with TwoSum
-// compensation; the chunk result is added to the FP64 totals with atomics.
+// The row [v | beta] (k + 1 <= 33 values, padded to 36) is staged in shared memory as
+// float-float pairs; the 36 x 36 upper triangle is cut into the 45 4x4 blocks (bi <=
+// bj) of a 9 x 9 block grid, and each of 5 row groups of 45 threads takes every
+// block once: a thread reads two 4-column slices per row and forms 16 error-free
+// products, accumulated with TwoSum compensation.  Chunk results are added to the
+// FP64 totals with atomics.
+constexpr int GB_COLS = 36, GB_BLOCKS = 9, GB_TASKS = 45, GB_GROUPS = 5;
 __global__ void __launch_bounds__(FIT_THREADS) k_gram(const float *__restrict__ Uh, const float *__restrict__ Ul,
                                                       const float2 *__restrict__ rf, const float2 *__restrict__ bt,
                                                       int64_t R, int k, int M, int64_t rows_per_chunk,
                                                       const unsigned *__restrict__ amax, double *__restrict__ G,
                                                       double *__restrict__ rhs) {
-  __shared__ float vh[FIT_ROWS][FIT_MAXK + 1], vl[FIT_ROWS][FIT_MAXK + 1];
-  __shared__ float2 beta[FIT_ROWS];
+  __shared__ __align__(16) float vh[FIT_ROWS][GB_COLS], vl[FIT_ROWS][GB_COLS];
   __shared__ int f[FIT_MAXK];
   const int m = blockIdx.y;
   if (threadIdx.x < FIT_MAXK) f[threadIdx.x] = threadIdx.x < k ? acol_exp(amax[m * FIT_MAXK + threadIdx.x]) : 0;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r1 = min(R, r0 + rows_per_chunk);
-  const int npairs = k * (k + 1) / 2, nsums = npairs + k;
-  int pa[3], pb[3];
-  float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+  // this thread's block (bi, bj) and row group
+  const int task = threadIdx.x % GB_TASKS, grp = threadIdx.x / GB_TASKS;
+  int bi = 0, rest = task;
+  while (rest >= GB_BLOCKS - bi) { rest -= GB_BLOCKS - bi; bi++; }
+  const int bj = bi + rest;
+  const bool active = grp < GB_GROUPS && 4 * bi <= k && 4 * bj <= k;   // column k is beta
+  constexpr int RPG = (FIT_ROWS + GB_GROUPS - 1) / GB_GROUPS;
+  float s[16], c[16];
 #pragma unroll
-  for (int q = 0; q < 3; q++) {
-    int id = threadIdx.x + q * FIT_THREADS;
-    pa[q] = pb[q] = -1;
-    if (id < npairs) {
-      int a = 0;
-      while (id >= k - a) { id -= k - a; a++; }
-      pa[q] = a;
-      pb[q] = a + id;
-    } else if (id < nsums) {
-      pa[q] = id - npairs;
-      pb[q] = -2;  // right-hand side
-    }
-  }
+  for (int q = 0; q < 16; q++) s[q] = c[q] = 0.f;
   for (int64_t rb = r0; rb < r1; rb += FIT_ROWS) {
     __syncthreads();
     const int nr = (int)min((int64_t)FIT_ROWS, r1 - rb);
-    for (int i = threadIdx.x; i < FIT_ROWS * k; i += FIT_THREADS) {
-      const int rr = i / k, cc = i - rr * k;
+    for (int i = threadIdx.x; i < FIT_ROWS * GB_COLS; i += FIT_THREADS) {
+      const int rr = i / GB_COLS, cc = i - rr * GB_COLS;
       float2 v = make_float2(0.f, 0.f);
       if (rr < nr) {
-        const int64_t o = (rb + rr) * k + cc;
-        const float2 r = rf[(rb + rr) * M + m];
-        v = ff_mul(Uh[o], Ul[o], r.x, r.y);
-        v.x = ldexpf(v.x, -f[cc]);
-        v.y = ldexpf(v.y, -f[cc]);
+        if (cc < k) {
+          const int64_t o = (rb + rr) * k + cc;
+          const float2 r = rf[(rb + rr) * M + m];
+          v = ff_mul(Uh[o], Ul[o], r.x, r.y);
+          v.x = ldexpf(v.x, -f[cc]);
+          v.y = ldexpf(v.y, -f[cc]);
+        } else if (cc == k) {
+          v = bt[(rb + rr) * M + m];
+        }
       }
       vh[rr][cc] = v.x;
       vl[rr][cc] = v.y;
     }
-    for (int rr = threadIdx.x; rr < FIT_ROWS; rr += FIT_THREADS)
-      beta[rr] = rr < nr ? bt[(rb + rr) * M + m] : make_float2(0.f, 0.f);
     __syncthreads();
+    if (active) {
+      const int rend = min(nr, (grp + 1) * RPG);
+      for (int rr = grp * RPG; rr < rend; rr++) {
+        const float4 ah = *(const float4 *)&vh[rr][4 * bi], al = *(const float4 *)&vl[rr][4 * bi];
+        const float4 bh = *(const float4 *)&vh[rr][4 * bj], bl = *(const float4 *)&vl[rr][4 * bj];
+        const float xa[4] = {ah.x, ah.y, ah.z, ah.w}, ya[4] = {al.x, al.y, al.z, al.w};
+        const float xb[4] = {bh.x, bh.y, bh.z, bh.w}, yb[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
-    for (int q = 0; q < 3; q++) {
-      if (pa[q] < 0) continue;
-      const int a = pa[q], b = pb[q];
-      for (int rr = 0; rr < nr; rr++) {
-        const float2 p = b >= 0 ? ff_mul(vh[rr][a], vl[rr][a], vh[rr][b], vl[rr][b])
-                                : ff_mul(vh[rr][a], vl[rr][a], beta[rr].x, beta[rr].y);
-        ff_acc(s[q], c[q], p);
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+          for (int j = 0; j < 4; j++) ff_acc(s[4 * i + j], c[4 * i + j], ff_mul(xa[i], ya[i], xb[j], yb[j]));
       }
     }
   }
+  if (!active) return;
 #pragma unroll
-  for (int q = 0; q < 3; q++) {
-    if (pa[q] < 0) continue;
-    const double val = (double)s[q] + (double)c[q];
-    if (pb[q] >= 0) atomicAdd(&G[((int64_t)m * FIT_MAXK + pa[q]) * FIT_MAXK + pb[q]], val);
-    else atomicAdd(&rhs[(int64_t)m * FIT_MAXK + pa[q]], val);
+  for (int i = 0; i < 4; i++) {
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int a = 4 * bi + i, b = 4 * bj + j;
+      if (a > b || a >= k || b > k) continue;
+      const double val = (double)s[4 * i + j] + (double)c[4 * i + j];
+      if (b < k) atomicAdd(&G[((int64_t)m * FIT_MAXK + a) * FIT_MAXK + b], val);
+      else atomicAdd(&rhs[(int64_t)m * FIT_MAXK + a], val);
+    }
   }
 }
 
@@ -288,25 +297,29 @@ __global__ void k_unscale(const double *__restrict__ x, int k, int M, const unsi
 
 // ---- residual q = (b - A x) scaled for A^T q, from the exact product p = F w:
 // relative: r = 1 - p / t, q = r / t;   absolute: r = t - p, q = r.  Also sums r^2 and b^2.
-__global__ void k_residual(const double *__restrict__ P, const double *__restrict__ T, int64_t R, int M,
-                           int objective, float2 *__restrict__ Q, double *__restrict__ rr, double *__restrict__ bb,
-                           int *status) {
+__global__ void k_residual(const double *__restrict__ P, const double *__restrict__ T, const double *__restrict__ inv,
+                           int64_t R, int M, int objective, float2 *__restrict__ Q, double *__restrict__ rr,
+                           double *__restrict__ bb) {
   __shared__ double s_r[64], s_b[64];
   if (threadIdx.x < 64) { s_r[threadIdx.x] = 0; s_b[threadIdx.x] = 0; }
   __syncthreads();
-  const int64_t n = R * M;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t n = R * M, stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool fixed_m = stride % M == 0;   // then every element of this thread has model i0 % M
+  double ar = 0, ab = 0;
+  for (int64_t i = i0; i < n; i += stride) {
     const int m = (int)(i % M);
     const double t = T[i], p = P[i];
-    if (!(t > 0.0) || t > 1e300) atomicOr(status, ST_BAD_INPUT);
     double r, q, b;
-    if (objective == PM_FIT_RELATIVE) { r = 1.0 - p / t; q = r / t; b = 1.0; }
+    // relative: r = 1 - p/t = (t - p) (1/t); q = r / t
+    if (objective == PM_FIT_RELATIVE) { const double it = inv[i]; r = (t - p) * it; q = r * it; b = 1.0; }
     else { r = t - p; q = r; b = t; }
     const float qh = __double2float_rn(q);
     Q[i] = make_float2(qh, __double2float_rn(q - (double)qh));
-    atomicAdd(&s_r[m], r * r);
-    atomicAdd(&s_b[m], b * b);
+    if (fixed_m) { ar += r * r; ab += b * b; }
+    else { atomicAdd(&s_r[m], r * r); atomicAdd(&s_b[m], b * b); }
   }
+  if (fixed_m && i0 < n) { atomicAdd(&s_r[i0 % M], ar); atomicAdd(&s_b[i0 % M], ab); }
   __syncthreads();
   if (threadIdx.x < M && threadIdx.x < 64) {
     atomicAdd(&rr[threadIdx.x], s_r[threadIdx.x]);
@@ -314,29 +327,46 @@ __global__ void k_residual(const double *__restrict__ P, const double *__restric
   }
 }
 
-// ---- g_m = U^T q_m  (float-float products and sums per chunk, FP64 totals); grid (row chunks, models)
+// ---- g_m = U^T q_m  (float-float products and sums per chunk, FP64 totals).
+// Grid (row chunks, groups of 8 models): each feature value is read once for the 8
+// models of its CTA; thread (column c, row lane) keeps 8 compensated sums.
+constexpr int ATQ_MODELS = 8;
 __global__ void __launch_bounds__(FIT_THREADS) k_atq(const float *__restrict__ Uh, const float *__restrict__ Ul,
                                                      const float2 *__restrict__ Q, int64_t R, int k, int M,
                                                      int64_t rows_per_chunk, const unsigned *__restrict__ amax,
                                                      double *__restrict__ g) {
-  const int m = blockIdx.y;
+  const int m0 = blockIdx.y * ATQ_MODELS;
   const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk;
   const int64_t r1 = min(R, r0 + rows_per_chunk);
   const int c = threadIdx.x % 32, lane_r = threadIdx.x / 32;   // 8 row lanes x 32 columns
-  float s = 0.f, cc = 0.f;
+  const int nm = min(ATQ_MODELS, M - m0);
+  float s[ATQ_MODELS], cc[ATQ_MODELS];
+#pragma unroll
+  for (int j = 0; j < ATQ_MODELS; j++) s[j] = cc[j] = 0.f;
   if (c < k) {
     for (int64_t r = r0 + lane_r; r < r1; r += FIT_THREADS / 32) {
-      const float2 q = Q[r * M + m];
-      ff_acc(s, cc, ff_mul(Uh[r * k + c], Ul[r * k + c], q.x, q.y));
+      const float uh = Uh[r * k + c], ul = Ul[r * k + c];
+      const float2 *q = Q + r * M + m0;
+#pragma unroll
+      for (int j = 0; j < ATQ_MODELS; j++) {
+        if (j < nm) {
+          const float2 qj = q[j];
+          ff_acc(s[j], cc[j], ff_mul(uh, ul, qj.x, qj.y));
+        }
+      }
     }
   }
-  __shared__ double red[FIT_THREADS];
-  red[threadIdx.x] = (double)s + (double)cc;
+  __shared__ double red[FIT_THREADS / 32][ATQ_MODELS][32];
+#pragma unroll
+  for (int j = 0; j < ATQ_MODELS; j++) red[lane_r][j][c] = (double)s[j] + (double)cc[j];
   __syncthreads();
-  if (threadIdx.x < 32 && c < k) {
-    double tot = 0;
-    for (int q = 0; q < FIT_THREADS / 32; q++) tot += red[q * 32 + threadIdx.x];
-    atomicAdd(&g[(int64_t)m * FIT_MAXK + c], ldexp(tot, -acol_exp(amax[m * FIT_MAXK + c])));
+  for (int o = threadIdx.x; o < ATQ_MODELS * 32; o += FIT_THREADS) {
+    const int j = o / 32, col = o % 32;
+    if (j < nm && col < k) {
+      double tot = 0;
+      for (int q = 0; q < FIT_THREADS / 32; q++) tot += red[q][j][col];
+      atomicAdd(&g[(int64_t)(m0 + j) * FIT_MAXK + col], ldexp(tot, -acol_exp(amax[(m0 + j) * FIT_MAXK + col])));
+    }
   }
 }
 
@@ -378,6 +408,7 @@ size_t fit_scratch_bytes(int64_t R, int k, int M) {
   b += (size_t)R * M * 16;                         // row factors, beta
   b += (size_t)R * M * 8;                          // Q
   b += (size_t)R * M * 8;                          // P
+  b += (size_t)R * M * 8;                          // 1 / t
   b += (size_t)M * FIT_MAXK * FIT_MAXK * 8;        // G / L
   b += (size_t)M * FIT_MAXK * 8 * 3;               // rhs, x, g
   b += (size_t)M * (4 * 4 + 8 * 4);                // info, ratio, upd, rr, bb
@@ -401,6 +432,7 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   float2 *bt = (float2 *)carve(p, (size_t)R * M * 8);
   float2 *Q = (float2 *)carve(p, (size_t)R * M * 8);
   double *P = (double *)carve(p, (size_t)R * M * 8);
+  double *inv = (double *)carve(p, (size_t)R * M * 8);
   double *G = (double *)carve(p, (size_t)M * FIT_MAXK * FIT_MAXK * 8);
   double *rhs = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
   double *x = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
@@ -421,20 +453,23 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   k_colmax<<<sms * 2, 256, 0, st>>>(F, R, k, cmax);
   k_scale<<<sms * 8, 256, 0, st>>>(F, R, k, cmax, U, Ul);
-  k_rowfac<<<sms * 8, 256, 0, st>>>(T, R * M, objective, rf, bt);
+  k_rowfac<<<sms * 8, 256, 0, st>>>(T, R * M, objective, rf, bt, inv, status);
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / std::max(1, M) + 1, (R + 255) / 256));
   const int64_t rpc = (R + chunks - 1) / chunks;
   k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, rf, R, k, M, rpc, amax);
   k_gram<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Ul, rf, bt, R, k, M, rpc, amax, G, rhs);
   k_chol_solve<<<M, 32, 0, st>>>(G, rhs, k, M, cmax, x, info, ratio);
+  const int groups = (M + ATQ_MODELS - 1) / ATQ_MODELS;
+  const int achunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / groups + 1, (R + 255) / 256));
+  const int64_t arpc = (R + achunks - 1) / achunks;
   for (int it = 0; it < steps; it++) {
     k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
     if ((e = launch_predict(F, R, k, W_out, M, PM_PREC_FP64, P, st)) != cudaSuccess) return e;
     cudaMemsetAsync(rr, 0, (size_t)M * 8, st);
     cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
     cudaMemsetAsync(g, 0, (size_t)M * FIT_MAXK * 8, st);
-    k_residual<<<sms * 4, 256, 0, st>>>(P, T, R, M, objective, Q, rr, bb, status);
-    k_atq<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Ul, Q, R, k, M, rpc, amax, g);
+    k_residual<<<sms * 4, 256, 0, st>>>(P, T, inv, R, M, objective, Q, rr, bb);
+    k_atq<<<dim3(achunks, groups), FIT_THREADS, 0, st>>>(U, Ul, Q, R, k, M, arpc, amax, g);
     k_refine_update<<<(M + 31) / 32, 32, 0, st>>>(G, g, k, M, info, x, upd);
   }
   k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
@@ -442,7 +477,7 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   if ((e = launch_predict(F, R, k, W_out, M, PM_PREC_FP64, P, st)) != cudaSuccess) return e;
   cudaMemsetAsync(rr, 0, (size_t)M * 8, st);
   cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
-  k_residual<<<sms * 4, 256, 0, st>>>(P, T, R, M, objective, Q, rr, bb, status);
+  k_residual<<<sms * 4, 256, 0, st>>>(P, T, inv, R, M, objective, Q, rr, bb);
   cudaMemcpyAsync(host->info, info, (size_t)M * 16, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(host->ratio, ratio, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(host->upd, upd, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
