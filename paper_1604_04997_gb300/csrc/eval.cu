@@ -213,31 +213,32 @@ __device__ __forceinline__ bool eval_dot(const uint32_t *__restrict__ T, const i
                      (uint64_t)slots[min((w >> 8) & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
   }
   const uint32_t I = (T[pmt::H_OFF_ENTRIES] + 3) & ~3u;
-  const uint4 ip = *(const uint4 *)(T + I + 4 + 4 * piece);
+  const uint4 ip = *(const uint4 *)(T + I + 8 * piece), iq = *(const uint4 *)(T + I + 8 * piece + 4);
   const uint4 *dw = (const uint4 *)(T + ip.x);
   const uint32_t *ds = T + ip.z;
-  const uint32_t d0 = ip.w >> 31;   // the first weight belongs to the constant slot (value 1)
+  const uint32_t d0 = ip.w;   // 1: the first weight belongs to the constant slot (value 1)
   uint32_t acc[4] = {0, 0, 0, 0};
   if (d0) {
     const uint4 c = dw[0];
     acc[0] = c.x; acc[1] = c.y; acc[2] = c.z; acc[3] = c.w;
   }
   for (uint32_t d = d0; d < ip.y; d++) mac128(acc, dw[d], slots[min(ds[d], (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
-  const uint4 *hl = (const uint4 *)(T + (ip.w & 0xFFFF));
-  for (uint32_t h = 0; h < ((ip.w >> 16) & 0x7FFF); h++) {
-    const uint4 E = hl[h];
-    const uint64_t coef = (uint64_t)E.z | ((uint64_t)E.w << 32);
-    int64_t *hs = slots + (pmt::HOLD_SLOT + ((E.x >> 8) & 3)) * ss;
-    *hs += (int64_t)(coef * (uint64_t)slots[min(E.x & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
-  }
-  const uint32_t npost = T[I];
-  const uint4 *pw = (const uint4 *)(T + T[I + 1]);
-  const uint32_t *ph = T + T[I + 2];
-  for (uint32_t q = 0; q < npost; q++) {
-    const uint32_t hw = ph[q];
-    const int64_t va = slots[(pmt::HOLD_SLOT + (hw & 3)) * ss];
-    const int64_t vb = slots[(pmt::HOLD_SLOT + ((hw >> 8) & 3)) * ss];
-    mac128(acc, pw[q], va < vb ? va : vb);
+  if (iq.w) {   // post-ops whose smaller operand depends on n
+    const uint4 *hl = (const uint4 *)(T + iq.x);
+    for (uint32_t h = 0; h < iq.y; h++) {
+      const uint4 E = hl[h];
+      const uint64_t coef = (uint64_t)E.z | ((uint64_t)E.w << 32);
+      int64_t *hs = slots + (pmt::HOLD_SLOT + ((E.x >> 8) & 3)) * ss;
+      *hs += (int64_t)(coef * (uint64_t)slots[min(E.x & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
+    }
+    const uint4 *pw = (const uint4 *)(T + iq.z);
+    for (uint32_t q = 0; q < iq.w; q++) {
+      const uint4 w = pw[2 * q];
+      const uint32_t hw = pw[2 * q + 1].x;
+      const int64_t va = slots[(pmt::HOLD_SLOT + (hw & 3)) * ss];
+      const int64_t vb = slots[(pmt::HOLD_SLOT + ((hw >> 8) & 3)) * ss];
+      mac128(acc, w, va < vb ? va : vb);
+    }
   }
   S.lo = (uint64_t)acc[0] | ((uint64_t)acc[1] << 32);
   S.hi = (uint64_t)acc[2] | ((uint64_t)acc[3] << 32);

@@ -58,18 +58,62 @@ static double table_work(const std::vector<uint32_t> &w) {
   return ops + per / np;
 }
 
-// K2 program of one table: the table's words up to its entries, then a weight image that turns the
-// per-column sums and the weight dot product into one dot product over the piece's
-// evaluation slots (sum_col W_col sum_e coef_e slot_e = sum_slot Weff_slot slot).
-// The image holds, per piece, the slots with their 128-bit weights Weff (filled on
-// the device from the call's weights: `targets` name each weight's position and its
-// (column, coefficient) contributions), the entries of the columns that feed post-ops
-// (their sums are needed for min()), and per post-op its weight and hold pair.
-//   image (word I = the table's entry offset rounded up to 4): [n_post, post_w, post_h, 0]
-//   then per piece [dot_w, n_dot, dot_s, hold_off | n_hold << 16 | const-first << 31]
-//   dot_w: n_dot uint4 weights; dot_s: n_dot slot words; hold_off: n_hold uint4
-//   {slot | hold << 8, 0, coef_lo, coef_hi}; post_w: n_post uint4 weights; post_h:
-//   n_post words {hold A | hold B << 8}.  Offsets are words from the program start.
+// Value ranges of a piece's evaluation slots over the table's parameter box (interval
+// arithmetic, wide integers): parameters, atoms floor((a.n + b)/c), the constant 1 and
+// the piece's products.
+using i128 = __int128;
+struct Range { i128 lo, hi; };
+// Slot values and coefficients of a valid table stay below 2^63, so products stay
+// below 2^126; anything wider is clamped to +-2^120 and never used in a proof.
+static constexpr i128 WIDE_LIM = (i128)1 << 120;
+static i128 clamp_wide(i128 v) { return v > WIDE_LIM ? WIDE_LIM : (v < -WIDE_LIM ? -WIDE_LIM : v); }
+static i128 floor_div_wide(i128 a, i128 c) { return a >= 0 ? a / c : -((-a + c - 1) / c); }
+static std::vector<Range> slot_ranges(const std::vector<uint32_t> &T, const uint32_t *pc) {
+  std::vector<Range> r(pmt::MAX_SLOTS, Range{0, 0});
+  const int P = (int)T[pmt::H_NPARAMS], A = (int)T[pmt::H_NATOMS];
+  i128 lo[4], hi[4];
+  for (int p = 0; p < 4; p++) {
+    lo[p] = (int32_t)T[pmt::H_BOX_LO + p];
+    hi[p] = (int32_t)T[pmt::H_BOX_HI + p];
+    if (p < P) r[p] = Range{lo[p], hi[p]};
+  }
+  const uint32_t *at = T.data() + T[pmt::H_OFF_ATOMS];
+  for (int a = 0; a < A && P + a < pmt::MAX_SLOTS; a++, at += pmt::ATOM_WORDS) {
+    i128 mn = (int32_t)at[4], mx = (int32_t)at[4];
+    for (int p = 0; p < P; p++) {
+      const i128 k = (int32_t)at[p];
+      mn += k >= 0 ? k * lo[p] : k * hi[p];
+      mx += k >= 0 ? k * hi[p] : k * lo[p];
+    }
+    const i128 c = at[5] ? (i128)at[5] : 1;
+    r[P + a] = Range{floor_div_wide(mn, c), floor_div_wide(mx, c)};
+  }
+  r[pmt::CONST_SLOT] = Range{1, 1};
+  const uint32_t *pr = T.data() + T[pmt::H_OFF_PRODS] + pc[0];
+  for (uint32_t j = 0; j < pc[1] && P + A + (int)j < pmt::MAX_SLOTS; j++) {
+    const Range x = r[std::min<uint32_t>(pr[j] & 0xFF, pmt::MAX_SLOTS - 1)];
+    const Range y = r[std::min<uint32_t>((pr[j] >> 8) & 0xFF, pmt::MAX_SLOTS - 1)];
+    const i128 q[4] = {clamp_wide(x.lo * y.lo), clamp_wide(x.lo * y.hi), clamp_wide(x.hi * y.lo),
+                       clamp_wide(x.hi * y.hi)};
+    r[P + A + j] = Range{*std::min_element(q, q + 4), *std::max_element(q, q + 4)};
+  }
+  return r;
+}
+
+// K2 program of one table: the table's words up to its entries, then a weight image
+// that turns the per-column sums and the weight dot product into one dot product over
+// the piece's evaluation slots (sum_col W_col sum_e coef_e slot_e = sum_slot Weff_slot
+// slot).  Per piece the image holds the slots with their 128-bit weights Weff (filled
+// on the device from the call's weights: `targets` name each weight's position and its
+// (column, coefficient) contributions).  A post-op min(hold A, hold B) whose sign of
+// A - B is fixed over the box (interval arithmetic on the piece's slots) is folded
+// into the dot as the smaller column; the others stay as runtime post-ops with the
+// entries of their held columns.
+//   piece header p (8 words at I + 8 p, I = the table's entry offset rounded up to 4):
+//     [dot_w, n_dot, dot_s, const-first, hold_off, n_hold, post_off, n_post]
+//   dot_w: n_dot uint4 weights; dot_s: n_dot slot words; hold entries (4 words):
+//   {slot | hold << 8, 0, coef_lo, coef_hi}; post entries (8 words): weight (4 words),
+//   hold A | hold B << 8, 0, 0, 0.  Offsets are words from the program start.
 static bool build_k2_program(const std::vector<uint32_t> &T, uint32_t base, std::vector<uint32_t> &out,
                              std::vector<uint4> &targets, std::vector<uint4> &contrib) {
   auto pad4 = [&]() { while (out.size() % 4) out.push_back(0); };
@@ -77,39 +121,65 @@ static bool build_k2_program(const std::vector<uint32_t> &T, uint32_t base, std:
   pad4();
   const uint32_t I = (uint32_t)out.size();
   const uint32_t npieces = T[pmt::H_NPIECES], npost = T[pmt::H_NPOST];
-  out.resize(I + 4 + 4 * npieces, 0);
-  auto add_target = [&](uint32_t word, const std::vector<std::pair<uint32_t, uint64_t>> &cs) {
+  out.resize(I + 8 * npieces, 0);
+  using Contribs = std::vector<std::pair<uint32_t, uint64_t>>;
+  auto add_target = [&](uint32_t word, const Contribs &cs) {
     targets.push_back(make_uint4(base + word, (uint32_t)contrib.size(), (uint32_t)cs.size(), 0));
     for (auto &cc : cs) contrib.push_back(make_uint4(cc.first, 0, (uint32_t)cc.second, (uint32_t)(cc.second >> 32)));
   };
   for (uint32_t p = 0; p < npieces; p++) {
     const uint32_t *pc = T.data() + T[pmt::H_OFF_PIECES] + 4 * p;
     const uint32_t *en = T.data() + T[pmt::H_OFF_ENTRIES] + pmt::ENTRY_WORDS * pc[2];
-    std::map<uint32_t, std::vector<std::pair<uint32_t, uint64_t>>> by_slot;
-    std::vector<uint4> holds;
-    size_t col_begin = 0;
-    std::vector<uint4> col_entries;
+    std::map<uint32_t, Contribs> by_slot;
+    std::vector<std::vector<std::pair<uint32_t, int64_t>>> held(pmt::MAX_HOLD);   // hold -> (slot, coef)
+    std::vector<std::pair<uint32_t, int64_t>> col_entries;
     for (uint32_t e = 0; e < pc[3]; e++, en += pmt::ENTRY_WORDS) {
       const uint32_t col = en[2] & 0xFF, slot = (en[2] >> 8) & 0xFF;
       if (slot >= (uint32_t)pmt::MAX_SLOTS) return false;
       const uint64_t coef = (uint64_t)en[0] | ((uint64_t)en[1] << 32);
       if (col < 32) by_slot[slot].push_back({col, coef});
-      col_entries.push_back(make_uint4(slot, 0, en[0], en[1]));
+      col_entries.push_back({slot, (int64_t)coef});
       if (en[2] & pmt::ENTRY_LAST) {
         const uint32_t hold = (en[2] >> 16) & 0xF;
         if (hold) {
           if (hold > (uint32_t)pmt::MAX_HOLD) return false;
-          for (size_t i = col_begin; i < col_entries.size(); i++) {
-            uint4 h = col_entries[i];
-            h.x |= (hold - 1) << 8;
-            holds.push_back(h);
-          }
+          held[hold - 1] = col_entries;
         }
-        col_begin = col_entries.size();
+        col_entries.clear();
+      }
+    }
+    // post-ops: fold those whose smaller operand is fixed over the box
+    const std::vector<Range> rg = slot_ranges(T, pc);
+    std::vector<uint32_t> runtime_posts;
+    bool hold_used[pmt::MAX_HOLD] = {false, false, false, false};
+    for (uint32_t q = 0; q < npost; q++) {
+      const uint32_t w = T[T[pmt::H_OFF_POST] + q];
+      const uint32_t out_col = w & 0xFF, ha = (w >> 8) & 3, hb = (w >> 16) & 3;
+      std::map<uint32_t, i128> d;   // A - B per slot
+      for (auto &x : held[ha]) d[x.first] += (i128)x.second;
+      for (auto &x : held[hb]) d[x.first] -= (i128)x.second;
+      i128 mn = 0, mx = 0;
+      bool sound = true;
+      for (auto &kv : d) {
+        const Range r = rg[kv.first];
+        const i128 lim = (i128)1 << 63;
+        if (kv.second >= lim || kv.second <= -lim || r.lo <= -lim || r.hi >= lim) { sound = false; break; }
+        const i128 a = kv.second * r.lo, b = kv.second * r.hi;
+        mn += std::min(a, b);
+        mx += std::max(a, b);
+      }
+      int pick = -1;
+      if (sound && mn >= 0) pick = (int)hb;        // A >= B everywhere: min = B
+      else if (sound && mx <= 0) pick = (int)ha;   // A <= B everywhere: min = A
+      if (pick >= 0 && out_col < 32) {
+        for (auto &x : held[pick]) by_slot[x.first].push_back({out_col, (uint64_t)x.second});
+      } else {
+        runtime_posts.push_back(w);
+        hold_used[ha] = hold_used[hb] = true;
       }
     }
     // the constant slot, when present, goes first: its product is the weight itself
-    std::vector<std::pair<uint32_t, std::vector<std::pair<uint32_t, uint64_t>>>> dots(by_slot.begin(), by_slot.end());
+    std::vector<std::pair<uint32_t, Contribs>> dots(by_slot.begin(), by_slot.end());
     const bool has_const = !dots.empty() && dots.back().first == pmt::CONST_SLOT;
     if (has_const) std::rotate(dots.begin(), dots.end() - 1, dots.end());
     const uint32_t dot_w = (uint32_t)out.size();
@@ -121,29 +191,32 @@ static bool build_k2_program(const std::vector<uint32_t> &T, uint32_t base, std:
     for (auto &kv : dots) out.push_back(kv.first);
     pad4();
     const uint32_t hold_off = (uint32_t)out.size();
-    for (const uint4 &h : holds) { out.push_back(h.x); out.push_back(h.y); out.push_back(h.z); out.push_back(h.w); }
-    if (hold_off >= 65536 || holds.size() >= 32768) return false;
-    uint32_t *ip = out.data() + I + 4 + 4 * p;
+    uint32_t n_hold = 0;
+    for (int h = 0; h < pmt::MAX_HOLD; h++) {
+      if (!hold_used[h]) continue;
+      for (auto &x : held[h]) {
+        const uint64_t cf = (uint64_t)x.second;
+        const uint32_t e[4] = {x.first | ((uint32_t)h << 8), 0, (uint32_t)cf, (uint32_t)(cf >> 32)};
+        out.insert(out.end(), e, e + 4);
+        n_hold++;
+      }
+    }
+    const uint32_t post_off = (uint32_t)out.size();
+    for (uint32_t w : runtime_posts) {
+      add_target((uint32_t)out.size(), {{w & 0xFF, 1ull}});
+      const uint32_t e[8] = {0, 0, 0, 0, ((w >> 8) & 3) | (((w >> 16) & 3) << 8), 0, 0, 0};
+      out.insert(out.end(), e, e + 8);
+    }
+    uint32_t *ip = out.data() + I + 8 * p;
     ip[0] = dot_w;
-    ip[1] = (uint32_t)by_slot.size();
+    ip[1] = (uint32_t)dots.size();
     ip[2] = dot_s;
-    ip[3] = hold_off | ((uint32_t)holds.size() << 16) | (has_const ? 1u << 31 : 0u);
+    ip[3] = has_const ? 1u : 0u;
+    ip[4] = hold_off;
+    ip[5] = n_hold;
+    ip[6] = post_off;
+    ip[7] = (uint32_t)runtime_posts.size();
   }
-  const uint32_t post_w = (uint32_t)out.size();
-  for (uint32_t q = 0; q < npost; q++) {
-    const uint32_t w = T[T[pmt::H_OFF_POST] + q];
-    add_target((uint32_t)out.size(), {{w & 0xFF, 1ull}});
-    out.resize(out.size() + 4, 0);
-  }
-  const uint32_t post_h = (uint32_t)out.size();
-  for (uint32_t q = 0; q < npost; q++) {
-    const uint32_t w = T[T[pmt::H_OFF_POST] + q];
-    out.push_back(((w >> 8) & 3) | (((w >> 16) & 3) << 8));
-  }
-  pad4();
-  out[I] = npost;
-  out[I + 1] = post_w;
-  out[I + 2] = post_h;
   return true;
 }
 
