@@ -220,6 +220,29 @@ static bool build_k2_program(const std::vector<uint32_t> &T, uint32_t base, std:
   return true;
 }
 
+// Test hook, not part of the C ABI in pm.h: the K2 program of one compiled table (at
+// word offset 0) and its weight-fill recipe, for host-side checks of the program
+// builder.  targets: 4 words each (program word, first contribution, count, 0);
+// contrib: 4 words each (column, 0, coef_lo, coef_hi).  Returns 0, 1 if a buffer is
+// too small (sizes are still reported), -1 for a malformed table.
+extern "C" int pmx_k2_program(const uint32_t *table, size_t words, uint32_t *prog, size_t prog_cap,
+                              size_t *prog_words, uint32_t *tgt, size_t tgt_cap, size_t *n_tgt, uint32_t *con,
+                              size_t con_cap, size_t *n_con) {
+  if (!table || words < (size_t)pmt::HEADER_WORDS || table[pmt::H_MAGIC] != pmt::MAGIC || table[pmt::H_WORDS] != words)
+    return -1;
+  std::vector<uint32_t> T(table, table + words), out;
+  std::vector<uint4> targets, contrib;
+  if (!build_k2_program(T, 0, out, targets, contrib)) return -1;
+  *prog_words = out.size();
+  *n_tgt = targets.size();
+  *n_con = contrib.size();
+  if (out.size() > prog_cap || targets.size() > tgt_cap || contrib.size() > con_cap) return 1;
+  std::memcpy(prog, out.data(), out.size() * 4);
+  std::memcpy(tgt, targets.data(), targets.size() * 16);
+  std::memcpy(con, contrib.data(), contrib.size() * 16);
+  return 0;
+}
+
 pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, int T, const int64_t *pt_off,
                       Plan **out) {
   if (var_off[0] != 0 || pt_off[0] != 0) return pm_set_error(PM_ERR_INVALID_ARG, "offsets must start at 0");

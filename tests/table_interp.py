@@ -45,6 +45,30 @@ class Table:
                             sh2=(q[7] >> 8) & 0xFF, neg=(q[7] >> 16) & 1))
         return out
 
+    def slots_and_piece(self, n):
+        """Evaluation slots (parameters, atoms, products, constant) and the piece at n."""
+        w = self.w
+        vals = list(n[:self.P])
+        for at in self.atoms():
+            vals.append((at["b"] + sum(at["a"][i] * n[i] for i in range(self.P))) // at["c"])
+        bits, o = 0, w[H_OFF_CONDS]
+        for c in range(self.C):
+            nt = w[o]
+            s = _s64(w[o + 1], w[o + 2])
+            for t in range(nt):
+                s += _s32(w[o + 4 + 2 * t]) * vals[w[o + 3 + 2 * t]]
+            bits |= int(s >= 0) << c
+            o += 3 + 2 * nt
+        piece = (w[w[H_OFF_LUT] + (bits >> 2)] >> (8 * (bits & 3))) & 0xFF
+        p0, n_prod = w[w[H_OFF_PIECES] + 4 * piece], w[w[H_OFF_PIECES] + 4 * piece + 1]
+        slots = list(vals) + [0] * (24 - len(vals))
+        slots[23] = 1
+        V = len(vals)
+        for j in range(n_prod):
+            x = w[w[H_OFF_PRODS] + p0 + j]
+            slots[V + j] = slots[x & 0xFF] * slots[(x >> 8) & 0xFF]
+        return slots, piece
+
     def evaluate(self, n, check_magic=True):
         """Exact feature columns at point n (Python integers)."""
         w = self.w
@@ -106,3 +130,29 @@ class Table:
             x = w[po + q]
             cols[x & 0xFF] = min(hold[(x >> 8) & 0xFF], hold[(x >> 16) & 0xFF])
         return cols[:self.k]
+
+
+def _wide(words):
+    """Four 32-bit words -> signed 128-bit integer."""
+    x = sum((int(words[i]) & 0xFFFFFFFF) << (32 * i) for i in range(4))
+    return x - (1 << 128) if x >= (1 << 127) else x
+
+
+def program_dot(prog, table, n):
+    """The fused ranking kernel's value of a K2 program at n: sum over the piece's
+    weighted slots, then the runtime post-ops (signed 128-bit result)."""
+    slots, piece = table.slots_and_piece(n)
+    I = (table.w[H_OFF_ENTRIES] + 3) & ~3
+    dot_w, n_dot, dot_s, flags, hold_off, n_hold, post_off, n_post = prog[I + 8 * piece: I + 8 * piece + 8]
+    S = 0
+    for d in range(n_dot):
+        S += _wide(prog[dot_w + 4 * d: dot_w + 4 * d + 4]) * slots[prog[dot_s + d]]
+    if n_post:
+        hold = [0, 0, 0, 0]
+        for h in range(n_hold):
+            e = prog[hold_off + 4 * h: hold_off + 4 * h + 4]
+            hold[(e[0] >> 8) & 3] += _s64(e[2], e[3]) * slots[e[0] & 0xFF]
+        for q in range(n_post):
+            e = prog[post_off + 8 * q: post_off + 8 * q + 8]
+            S += _wide(e[:4]) * min(hold[e[4] & 3], hold[(e[4] >> 8) & 3])
+    return S
