@@ -412,7 +412,7 @@ size_t fit_scratch_bytes(int64_t R, int k, int M) {
   b += (size_t)M * FIT_MAXK * FIT_MAXK * 8;        // G / L
   b += (size_t)M * FIT_MAXK * 8 * 3;               // rhs, x, g
   b += (size_t)M * (4 * 4 + 8 * 4);                // info, ratio, upd, rr, bb
-  return b + 16 * 64;
+  return b + 32 * 256;                             // every carve rounds up to 256 bytes
 }
 
 static char *carve(char *&p, size_t bytes) {
