@@ -8,7 +8,7 @@ One step = one pass of that whole path over the batch.  Prints one JSON line.
 Multi-GPU (torchrun): every rank ranks its own point batch of the same size (weak
 scaling; rank r draws its points with seed 3 + 7919 r); no data-path collective, the
 process group only brackets the timing (barrier, max over ranks).
-Other workloads: --workload eval | predict | fit | serve.
+Other workloads: --workload eval | predict | fit | serve | calibrate.
 """
 from __future__ import annotations
 
@@ -554,6 +554,36 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def run_calibrate(args):
+    """Fit the model to this GPU from timed measurement kernels and predict held-out
+    test kernels (Sec. 4-5): the model's own accuracy on GB300."""
+    import __graft_entry__
+    from paper_1604_04997_gb300 import binding as B
+    from paper_1604_04997_gb300 import calibrate as C
+    __graft_entry__.build()
+    ctx = B.Context(0)
+    t0 = time.perf_counter()
+    r = C.calibrate(ctx, quick=args.steps < 5)
+    wall = time.perf_counter() - t0
+    ctx.close()
+    groups = {k: round(v["geomean_rel_err"], 4) for k, v in r["test"]["groups"].items()}
+    mgroups = {k: round(v["geomean_rel_err"], 4) for k, v in r["measurement"]["groups"].items()}
+    line = {"metric": "geomean relative prediction error on held-out test kernels (weights fitted on this GPU)",
+            "value": r["test"]["geomean_rel_err"], "unit": "fraction", "n_gpus": 1, "steps": 1, "warmup": 4,
+            "ms_per_step": wall * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "fp32/fp64 kernels; exact counts; FP64 fit", "data": "synthetic",
+            "config": {"workload": f"{r['measurement']['n']} measurement + {r['test']['n']} test kernel runs, "
+                                   "30 timed runs each, first 4 dropped, minimum kept",
+                       "measurement_geomean_rel_err": r["measurement"]["geomean_rel_err"],
+                       "test_groups": groups, "measurement_groups": mgroups,
+                       "fit": {k: r["fit_report"][k] for k in ("rank", "cond_est", "rel_resid", "status")},
+                       "weights": r["weights"]},
+            "roofline": None, "gpu_launches": None}
+    print(json.dumps(line))
+    if args.calib_out:
+        json.dump(r, open(args.calib_out, "w"), indent=1)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -566,13 +596,17 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape")
-    ap.add_argument("--workload", default="batched", choices=["batched", "eval", "predict", "fit", "serve"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "eval", "predict", "fit", "serve", "calibrate"])
+    ap.add_argument("--calib-out", default=None, help="write the full calibration result (JSON) here")
     ap.add_argument("--serve-queries", type=int, default=1000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "calibrate":
+        run_calibrate(args)
     elif args.workload != "batched":
         run_other(args)
     else:

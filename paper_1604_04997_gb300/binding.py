@@ -56,6 +56,16 @@ class Query(ctypes.Structure):
                 ("h_top_idx", ctypes.c_void_p), ("h_top_t", ctypes.c_void_p)]
 
 
+class PmmConfig(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("variant", ctypes.c_int32), ("k", ctypes.c_int32), ("gx", ctypes.c_int32),
+                ("gy", ctypes.c_int32), ("f64", ctypes.c_int32), ("n", ctypes.c_int64), ("m", ctypes.c_int64),
+                ("l", ctypes.c_int64)]
+
+
+PMM_KINDS = ("empty", "copy", "sum4", "index", "vsa", "filled", "arith", "transpose_p", "transpose_r", "transpose_w",
+             "matmul", "matmul_naive", "stencil", "matvec", "reduction", "axpy", "vecadd")
+
+
 class ServeStats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
@@ -91,6 +101,8 @@ def lib():
             "pm_serve_poll": ([vp, ctypes.c_uint64, i32], i32),
             "pm_serve_stats": ([vp, i32, ctypes.POINTER(ServeStats)], i32),
             "pm_serve_stop": ([vp], i32),
+            "pmm_time": ([ctypes.POINTER(PmmConfig), i32, i32, ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double), vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -105,7 +117,7 @@ def exported_symbols() -> Sequence[str]:
             "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
             "pm_eval_predict_topk", "pm_tune",
             "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
-            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop")
+            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time")
 
 
 def _check(rc: int, ok=(PM_OK,)) -> int:
@@ -243,6 +255,16 @@ class Context:
 
     def serve_stop(self):
         _check(lib().pm_serve_stop(self.h))
+
+
+def pmm_time(kind: str, variant: int = 0, k: int = 0, gx: int = 256, gy: int = 1, n: int = 1, m: int = 0,
+             l: int = 0, runs: int = 30, skip: int = 4, stream=None, f64: bool = False) -> Tuple[float, float]:
+    """Time one measurement-kernel configuration (include/pm_measure.h): (min, mean) ms
+    over runs - skip timed runs."""
+    cfg = PmmConfig(PMM_KINDS.index(kind), variant, k, gx, gy, int(f64), n, m, l)
+    mn, me = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pmm_time(ctypes.byref(cfg), runs, skip, ctypes.byref(mn), ctypes.byref(me), _stream(stream)))
+    return mn.value, me.value
 
 
 def make_query(model: int, topk: int, tables: np.ndarray, points: np.ndarray, top_idx: np.ndarray,

@@ -415,6 +415,110 @@ def draw_queries(n_queries: int, rate_per_s: float, n_variants: Sequence[int], n
     return out
 
 
+# --------------------------------------------------------------------------- measurement kernels
+
+PROBE_KINDS = ("empty", "copy", "sum4", "index", "vsa", "filled", "arith", "transpose_p", "transpose_r",
+               "transpose_w", "matmul", "matmul_naive", "stencil", "matvec", "reduction", "axpy", "vecadd")
+ARITH_TYPES = ("add", "mul", "div", "pow", "spec")
+
+
+@dataclasses.dataclass(frozen=True)
+class Probe:
+    """One measurement or test kernel configuration (Sec. 4.1, Sec. 5): its kind, a
+    kind-specific variant (stride for vsa/filled, index into ARITH_TYPES for arith,
+    tile for the 2-D tiled kinds), an inner trip count k (arith, filled) and the
+    work-group size gx (x gy)."""
+    kind: str
+    variant: int = 0
+    k: int = 0
+    gx: int = 256
+    gy: int = 1
+    f64: bool = False   # fp64 data and arithmetic (copy, vsa, arith add/mul/div)
+
+    @property
+    def n_params(self) -> int:
+        return 3 if self.kind in ("matmul", "matmul_naive") else 1
+
+    @property
+    def name(self) -> str:
+        return f"{self.kind}{'64' if self.f64 else ''}_v{self.variant}_k{self.k}_g{self.gx}x{self.gy}"
+
+
+def _probe_1d(p: Probe, head: List[str], body: List[str]) -> str:
+    W = p.gx
+    X = f"{W}*g+l"
+    L = [f"kernel {p.name}", "param n"] + head + [f"dim g g0 0 ceil(n/{W})", f"dim l l0 0 {W}",
+                                                  "stmt s g,l", f"guard {X} < n"]
+    return "\n".join(L + [b.replace("X", X) for b in body] + ["end"]) + "\n"
+
+
+def probe_ir(p: Probe) -> str:
+    """The IR of a measurement/test kernel; the CUDA kernel of the same Probe performs
+    exactly these loads, stores, flops and barriers per work-item."""
+    k, s, W = p.kind, p.variant, p.gx
+    dt = "f64" if p.f64 else "f32"
+    if k == "copy":
+        return _probe_1d(p, [f"array a global {dt} n", f"array b global {dt} n"], ["load a[X]", "store b[X]"])
+    if k == "sum4":
+        return _probe_1d(p, [f"array a{i} global {dt} n" for i in range(4)] + [f"array c global {dt} n"],
+                         [f"load a{i}[X]" for i in range(4)] + [f"flop {dt} add 3", "store c[X]"])
+    if k == "index":
+        return _probe_1d(p, [f"array a global {dt} n"], ["store a[X]"])
+    if k == "vsa":
+        ext = f"{s}*n" if s > 1 else "n"
+        idx = f"{s}*(X)" if s > 1 else "X"
+        return _probe_1d(p, [f"array a global {dt} {ext}", f"array b global {dt} {ext}", f"array c global {dt} {ext}"],
+                         [f"load a[{idx}]", f"load b[{idx}]", f"flop {dt} mul 2", f"flop {dt} add 1", f"store c[{idx}]"])
+    if k == "filled":
+        X = f"{W}*g+l"
+        return "\n".join([f"kernel {p.name}", "param n", f"array a global f32 {p.k},{s}*n", "array o global f32 n",
+                          f"dim g g0 0 ceil(n/{W})", f"dim l l0 0 {W}", f"dim k seq 0 {p.k}", f"dim j seq 0 {s}",
+                          "stmt acc g,k,j,l", f"guard {X} < n", f"load a[k,{s}*({X})+j]", "flop f32 add 1", "end",
+                          "stmt st g,l", f"guard {X} < n", f"store o[{X}]", "end"]) + "\n"
+    if k in ("arith", "empty"):
+        X, Y = f"{p.gx}*gx+lx", f"{p.gy}*gy+ly"
+        L = [f"kernel {p.name}", "param n"] + ([f"array o global {dt} n,n"] if k == "arith" else []) + [
+            f"dim gx g0 0 ceil(n/{p.gx})", f"dim gy g1 0 ceil(n/{p.gy})", f"dim lx l0 0 {p.gx}",
+            f"dim ly l1 0 {p.gy}"]
+        if k == "empty":
+            return "\n".join(L + ["stmt s gx,gy,lx,ly", "end"]) + "\n"
+        t = ARITH_TYPES[s]
+        ops = {"add": [f"flop {dt} add 8"], "mul": [f"flop {dt} mul 8"], "div": [f"flop {dt} div 8"],
+               "pow": ["flop f32 pow 8", "flop f32 add 8"], "spec": ["flop f32 spec 8", "flop f32 add 8"]}[t]
+        return "\n".join(L + [f"dim k seq 0 {p.k}", "stmt a gx,gy,ly,lx,k", f"guard {Y} < n", f"guard {X} < n"]
+                         + ops + ["end", "stmt st gx,gy,ly,lx", f"guard {Y} < n", f"guard {X} < n",
+                                  f"store o[{Y},{X}]", "end"]) + "\n"
+    if k == "transpose_w":
+        T = p.gx
+        X, Y = f"{T}*gx+lx", f"{T}*gy+ly"
+        return "\n".join([f"kernel {p.name}", "param n", "array in global f32 n,n", "array out global f32 n,n",
+                          f"dim gx g0 0 ceil(n/{T})", f"dim gy g1 0 ceil(n/{T})", f"dim ly l1 0 {T}",
+                          f"dim lx l0 0 {T}", "stmt cp gx,gy,ly,lx", f"guard {Y} < n", f"guard {X} < n",
+                          f"load in[{X},{Y}]", f"store out[{Y},{X}]", "end"]) + "\n"
+    return variant_ir(probe_variant(p))
+
+
+def probe_variant(p: Probe) -> Variant:
+    """The template variant behind a template-shaped probe (tile p.gx, one item per
+    element for the 2-D kinds)."""
+    T = p.gx
+    if p.kind == "transpose_p":
+        return Variant("transpose", T, T, 1, True, T * T)
+    if p.kind == "transpose_r":
+        return Variant("transpose", T, T, 1, False, T * T)
+    if p.kind == "matmul":
+        return Variant("matmul", T, T, 1, True, T * T)
+    if p.kind == "matmul_naive":
+        return Variant("matmul", T, T, 1, False, T * T)
+    if p.kind == "stencil":
+        return Variant("stencil", T, T, 1, False, T * T)
+    if p.kind == "matvec":
+        return Variant("matvec", 8, 8, 1, False, 256)
+    if p.kind in ("reduction", "axpy", "vecadd"):
+        return Variant(p.kind, p.variant, p.variant, 1, False, p.gx)   # tile variant x variant elements per group
+    raise ValueError(p.kind)
+
+
 # --------------------------------------------------------------------------- small workload
 
 POW2_SMALL = (64, 128, 256)

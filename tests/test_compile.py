@@ -27,8 +27,10 @@ def ctx():
 
 
 def test_library_exports_every_declared_symbol(ctx):
-    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "pm.h")).read(), flags=re.S)
-    decl = set(re.findall(r"\b(pm_[a-z_0-9]+)\s*\(", text))
+    decl = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", h)).read(), flags=re.S)
+        decl |= set(re.findall(r"\b(pmm?_[a-z_0-9]+)\s*\(", text))
     L = B.lib()
     missing = [s for s in decl if not hasattr(L, s)]
     assert not missing and set(B.exported_symbols()) <= decl
@@ -122,3 +124,37 @@ def test_loopy_example_table(ctx):
     for n in (1, 7, 64, 65, 1000, 1 << 20):
         F = T.evaluate([n])
         assert (F[4], F[17], F[24], F[1]) == (n, n, n, -(-n // 64))
+
+
+def test_measurement_config_checks_need_no_gpu(ctx):
+    """pmm_time rejects bad configurations before touching the device."""
+    for kw in (dict(kind="copy", n=0), dict(kind="vsa", variant=0, n=1024), dict(kind="arith", variant=7, k=8, n=64),
+               dict(kind="matmul", gx=8, gy=8, n=64, m=64, l=64), dict(kind="reduction", variant=8, gx=256, n=4096),
+               dict(kind="copy", n=1024, gx=2048)):
+        with pytest.raises(B.PMError) as e:
+            B.pmm_time(**kw, runs=5, skip=1)
+        assert e.value.code == -1
+    with pytest.raises(B.PMError):
+        B.pmm_time("copy", n=1024, runs=4, skip=4)
+
+
+def test_probe_tables_match_oracle(ctx):
+    """The measurement and test kernels' IR (the CUDA kernels' operation counts),
+    compiled, against the oracle's brute-force counting at small sizes."""
+    from paper_1604_04997_gb300 import calibrate as C
+    seen = set()
+    for case in C.measurement_set(quick=True) + C.test_set(quick=True):
+        p = case.probe
+        if p in seen:
+            continue
+        seen.add(p)
+        small = W.Probe(p.kind, p.variant, min(p.k, 4), min(p.gx, 16), min(p.gy, 16), p.f64) \
+            if p.kind in ("arith", "filled", "empty") else p
+        ir = W.probe_ir(small)
+        P = small.n_params
+        tid, _ = ctx.compile_counts(ir, 32, [1] * P, [4096] * P)
+        T = Table(ctx.table_image(tid))
+        sizes = [(40,), (64,), (70,)] if P == 1 else [(40, 24, 36), (64, 32, 64), (33, 17, 48)]
+        for n in sizes:
+            ref = oracle.Kernel(ir).features(np.array([n]), 32, "brute")[0]
+            assert T.evaluate(list(n)) == list(ref), (small.name, n)
