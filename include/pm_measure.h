@@ -28,6 +28,8 @@
  *   PMM_REDUCTION    one sum per group of variant^2 elements           group gx
  *   PMM_AXPY         y = alpha x + y (fp64), variant^2 elements/group  group gx
  *   PMM_VECADD       c = a + b, variant^2 elements per group           group gx
+ *   PMM_NBODY        all-pairs gravitation on n bodies (f32)           group gx
+ *   PMM_CONV5        5 x 5 convolution, valid region of n x n (f32)    group gx x gy
  * Sizes: n (and m, l for the matmuls) as in the IR's parameters.
  *
  * pmm_time runs the configuration `runs` times on `stream` (each run timed by
@@ -50,7 +52,7 @@ extern "C" {
 enum {
   PMM_EMPTY = 0, PMM_COPY, PMM_SUM4, PMM_INDEX, PMM_VSA, PMM_FILLED, PMM_ARITH, PMM_TRANSPOSE_P,
   PMM_TRANSPOSE_R, PMM_TRANSPOSE_W, PMM_MATMUL, PMM_MATMUL_NAIVE, PMM_STENCIL, PMM_MATVEC,
-  PMM_REDUCTION, PMM_AXPY, PMM_VECADD, PMM_NKINDS
+  PMM_REDUCTION, PMM_AXPY, PMM_VECADD, PMM_NBODY, PMM_CONV5, PMM_NKINDS
 };
 
 typedef struct {

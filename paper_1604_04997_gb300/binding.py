@@ -63,7 +63,7 @@ class PmmConfig(ctypes.Structure):
 
 
 PMM_KINDS = ("empty", "copy", "sum4", "index", "vsa", "filled", "arith", "transpose_p", "transpose_r", "transpose_w",
-             "matmul", "matmul_naive", "stencil", "matvec", "reduction", "axpy", "vecadd")
+             "matmul", "matmul_naive", "stencil", "matvec", "reduction", "axpy", "vecadd", "nbody", "conv5")
 
 
 class ServeStats(ctypes.Structure):

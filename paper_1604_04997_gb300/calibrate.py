@@ -7,8 +7,9 @@ Each is timed with the protocol of Sec. 4.2 (30 runs, the first 4 dropped, the
 minimum kept); its properties come from its IR through pm_compile_counts and
 pm_eval_counts; the weights are the relative-error least-squares fit of Sec. 4.3
 (pm_fit_weights).  Test kernels (a 5-point stencil, a skinny matrix product, batched
-matrix-vector products, a reduction, axpy, vector add) are timed the same way and
-predicted with the fitted weights (pm_predict).  Everything that computes runs in
+matrix-vector products, a reduction, axpy, vector add, all-pairs n-body, a 5 x 5
+convolution) are timed the same way and predicted with the fitted weights
+(pm_predict).  Everything that computes runs in
 the library's CUDA kernels; this module only lists configurations and marshals
 arrays.
 """
@@ -109,9 +110,8 @@ def test_set(quick: bool = False) -> List[Case]:
     out: List[Case] = []
     for n in pw(10, 14):
         out.append(Case(P("stencil", gx=16, gy=16), (n,), "5-point stencil"))
-    for n in pw(10, 12):
-        for m in (32, 128):
-            out.append(Case(P("matmul", gx=16, gy=16), (n, m, n), "skinny matmul"))
+    for n in pw(7, 10):   # skinny: n = l, m = 8 n
+        out.append(Case(P("matmul", gx=16, gy=16), (n, 8 * n, n), "skinny matmul"))
     for b in pw(12, 18):
         out.append(Case(P("matvec"), (b,), "batched matvec f64"))
     for n in pw(22, 28):
@@ -120,6 +120,10 @@ def test_set(quick: bool = False) -> List[Case]:
         out.append(Case(P("axpy", 32, gx=256), (n,), "axpy f64"))
     for n in pw(22, 28):
         out.append(Case(P("vecadd", 16, gx=256), (n,), "vector add"))
+    for n in pw(12, 16):
+        out.append(Case(P("nbody", gx=256), (n,), "n-body"))
+    for n in pw(10, 14):
+        out.append(Case(P("conv5", gx=32, gy=8), (n,), "5x5 convolution"))
     return out
 
 

@@ -207,6 +207,43 @@ __global__ void k_vecadd(const float *__restrict__ a, const float *__restrict__ 
   }
 }
 
+// All-pairs gravitation: work-item i sums the pull of every body j on body i.  Per
+// pair: 3 subtractions, the squared distance (3 mul, 3 add with the softening), one
+// rsqrt, inv^3 (2 mul), the mass factor (1 mul) and 3 accumulations (3 mul, 3 add).
+__global__ void k_nbody(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
+                        const float *__restrict__ m, float *__restrict__ ax, float *__restrict__ ay,
+                        float *__restrict__ az, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float xi = x[i], yi = y[i], zi = z[i];
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int64_t j = 0; j < n; j++) {
+    const float dx = x[j] - xi, dy = y[j] - yi, dz = z[j] - zi;
+    const float r2 = dx * dx + dy * dy + dz * dz + 1e-3f;
+    const float inv = rsqrtf(r2);
+    const float s = m[j] * (inv * inv * inv);
+    sx = sx + dx * s;
+    sy = sy + dy * s;
+    sz = sz + dz * s;
+  }
+  ax[i] = sx;
+  ay[i] = sy;
+  az[i] = sz;
+}
+
+// 5 x 5 convolution over the valid region of an n x n image
+__global__ void k_conv5(const float *__restrict__ in, const float *__restrict__ w, float *__restrict__ out,
+                        int64_t n) {
+  const int64_t Y = (int64_t)blockDim.y * blockIdx.y + threadIdx.y, X = (int64_t)blockDim.x * blockIdx.x + threadIdx.x;
+  if (Y >= n - 4 || X >= n - 4) return;
+  float acc = 0.f;
+#pragma unroll
+  for (int fy = 0; fy < 5; fy++)
+#pragma unroll
+    for (int fx = 0; fx < 5; fx++) acc = acc + w[fy * 5 + fx] * in[(Y + fy) * n + X + fx];
+  out[Y * n + X] = acc;
+}
+
 unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 }  // namespace
@@ -222,7 +259,10 @@ extern "C" pm_status pmm_time(const pmm_config *cfg, int32_t runs, int32_t skip,
   if (n < 1 || n > (int64_t(1) << 30) || (mm && (m < 1 || l < 1 || m > 65536 || l > 65536 || n > 65536)))
     return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: bad sizes");
   const bool two_d = c.kind == PMM_EMPTY || c.kind == PMM_ARITH || c.kind == PMM_TRANSPOSE_P ||
-                     c.kind == PMM_TRANSPOSE_R || c.kind == PMM_TRANSPOSE_W || mm || c.kind == PMM_STENCIL;
+                     c.kind == PMM_TRANSPOSE_R || c.kind == PMM_TRANSPOSE_W || mm || c.kind == PMM_STENCIL ||
+                     c.kind == PMM_CONV5;
+  if (c.kind == PMM_NBODY && n > (int64_t(1) << 20)) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: n-body n <= 2^20");
+  if (c.kind == PMM_CONV5 && n < 5) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: convolution needs n >= 5");
   if (two_d && n > 65536) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: 2-D n must be <= 65536");
   const int gx = c.gx, gy = c.gy;
   if (gx < 1 || gy < 1 || gx * gy > 1024) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: bad group size");
@@ -264,6 +304,8 @@ extern "C" pm_status pmm_time(const pmm_config *cfg, int32_t runs, int32_t skip,
     case PMM_REDUCTION: bytes = {(size_t)n * 4, (size_t)ceil_div(n, E) * 4}; break;
     case PMM_AXPY: bytes = {(size_t)n * 8, (size_t)n * 8}; break;
     case PMM_VECADD: bytes = std::vector<size_t>(3, (size_t)n * 4); break;
+    case PMM_NBODY: bytes = std::vector<size_t>(7, (size_t)n * 4); break;
+    case PMM_CONV5: bytes = {(size_t)n * n * 4, 25 * 4, (size_t)n * n * 4}; break;
     default: break;
   }
   size_t total = 0;
@@ -340,6 +382,11 @@ extern "C" pm_status pmm_time(const pmm_config *cfg, int32_t runs, int32_t skip,
       case PMM_REDUCTION: k_reduction<<<ceil_div(n, E), b1, gx * 4, st>>>(F(0), F(1), n, E); break;
       case PMM_AXPY: k_axpy<<<ceil_div(n, E), b1, 0, st>>>(D(0), D(1), n, E, 1.5); break;
       case PMM_VECADD: k_vecadd<<<ceil_div(n, E), b1, 0, st>>>(F(0), F(1), F(2), n, E); break;
+      case PMM_NBODY: k_nbody<<<ceil_div(n, gx), b1, 0, st>>>(F(0), F(1), F(2), F(3), F(4), F(5), F(6), n); break;
+      case PMM_CONV5:
+        k_conv5<<<dim3(ceil_div(std::max<int64_t>(n - 4, 1), gx), ceil_div(std::max<int64_t>(n - 4, 1), gy)), b2, 0,
+                  st>>>(F(0), F(1), F(2), n);
+        break;
       default: break;
     }
   };

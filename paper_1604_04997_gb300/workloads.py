@@ -418,7 +418,8 @@ def draw_queries(n_queries: int, rate_per_s: float, n_variants: Sequence[int], n
 # --------------------------------------------------------------------------- measurement kernels
 
 PROBE_KINDS = ("empty", "copy", "sum4", "index", "vsa", "filled", "arith", "transpose_p", "transpose_r",
-               "transpose_w", "matmul", "matmul_naive", "stencil", "matvec", "reduction", "axpy", "vecadd")
+               "transpose_w", "matmul", "matmul_naive", "stencil", "matvec", "reduction", "axpy", "vecadd",
+               "nbody", "conv5")
 ARITH_TYPES = ("add", "mul", "div", "pow", "spec")
 
 
@@ -488,6 +489,25 @@ def probe_ir(p: Probe) -> str:
         return "\n".join(L + [f"dim k seq 0 {p.k}", "stmt a gx,gy,ly,lx,k", f"guard {Y} < n", f"guard {X} < n"]
                          + ops + ["end", "stmt st gx,gy,ly,lx", f"guard {Y} < n", f"guard {X} < n",
                                   f"store o[{Y},{X}]", "end"]) + "\n"
+    if k == "nbody":
+        X = f"{W}*g+l"
+        return "\n".join([f"kernel {p.name}", "param n"] + [f"array {a} global f32 n" for a in
+                                                             ("x", "y", "z", "m", "ax", "ay", "az")] + [
+            f"dim g g0 0 ceil(n/{W})", f"dim l l0 0 {W}", "dim j seq 0 n",
+            "stmt own g,l", f"guard {X} < n", f"load x[{X}]", f"load y[{X}]", f"load z[{X}]", "end",
+            "stmt pair g,l,j", f"guard {X} < n", "load x[j]", "load y[j]", "load z[j]", "load m[j]",
+            "flop f32 add 9", "flop f32 mul 9", "flop f32 spec 1", "end",
+            "stmt st g,l", f"guard {X} < n", f"store ax[{X}]", f"store ay[{X}]", f"store az[{X}]", "end"]) + "\n"
+    if k == "conv5":
+        X, Y = f"{p.gx}*gx+lx", f"{p.gy}*gy+ly"
+        return "\n".join([f"kernel {p.name}", "param n", "array in global f32 n,n", "array w global f32 5,5",
+                          "array out global f32 n,n", f"dim gx g0 0 ceil((n-4)/{p.gx})",
+                          f"dim gy g1 0 ceil((n-4)/{p.gy})", f"dim lx l0 0 {p.gx}", f"dim ly l1 0 {p.gy}",
+                          "dim fy seq 0 5", "dim fx seq 0 5",
+                          "stmt mac gx,gy,ly,lx,fy,fx", f"guard {Y} < n-4", f"guard {X} < n-4",
+                          f"load in[{Y}+fy,{X}+fx]", "load w[fy,fx]", "flop f32 mul 1", "flop f32 add 1", "end",
+                          "stmt st gx,gy,ly,lx", f"guard {Y} < n-4", f"guard {X} < n-4", f"store out[{Y},{X}]",
+                          "end"]) + "\n"
     if k == "transpose_w":
         T = p.gx
         X, Y = f"{T}*gx+lx", f"{T}*gy+ly"
