@@ -577,6 +577,8 @@ def run_calibrate(args):
                        "measurement_geomean_rel_err": r["measurement"]["geomean_rel_err"],
                        "test_groups": groups, "measurement_groups": mgroups,
                        "fit": {k: r["fit_report"][k] for k in ("rank", "cond_est", "rel_resid", "status")},
+                       "selection": {k: r["selection"][k] for k in ("top1_hit_rate", "mean_top1_slowdown",
+                                                                     "mean_top2_slowdown")},
                        "weights": r["weights"]},
             "roofline": None, "gpu_launches": None}
     print(json.dumps(line))

@@ -163,6 +163,68 @@ def _geomean(x) -> float:
     return float(np.exp(np.mean(np.log(np.maximum(x, 1e-12))))) if len(x) else float("nan")
 
 
+def selection_families(quick: bool = False) -> Dict[str, Tuple[List[W.Probe], List[Tuple[int, ...]]]]:
+    """Configuration choices for one computation each (tile, group size, local
+    prefetch or not) and the problem sizes to choose them for."""
+    P = W.Probe
+    two = lambda a, b: [a, b]
+    fams = {
+        "transpose": ([P(k, gx=T, gy=T) for k in ("transpose_p", "transpose_r", "transpose_w") for T in (16, 32)],
+                      [(1 << 11,), (1 << 13,)] if not quick else [(1 << 11,)]),
+        "matmul": ([P(k, gx=T, gy=T) for k in ("matmul", "matmul_naive") for T in (16, 32)],
+                   [(512, 512, 512), (2048, 2048, 2048)] if not quick else [(512, 512, 512)]),
+        "reduction": ([P("reduction", E, gx=Wg) for E, Wg in ((16, 128), (16, 256), (32, 256), (32, 512), (64, 256),
+                                                              (64, 512))],
+                      [(1 << 22,), (1 << 26,)] if not quick else [(1 << 22,)]),
+        "vector add": ([P("vecadd", E, gx=Wg) for E, Wg in ((16, 256), (32, 256), (32, 512), (64, 512))],
+                       [(1 << 22,), (1 << 26,)] if not quick else [(1 << 22,)]),
+    }
+    return fams
+
+
+def select(ctx: B.Context, weights: np.ndarray, quick: bool = False, runs: int = 30, skip: int = 4) -> dict:
+    """Model-guided configuration selection (the extension the paper proposes in
+    Sec. 6.2): rank every candidate configuration of a computation with the fitted
+    model through the serve API, then time all of them.  Reports whether the
+    predicted best is the measured best, and the slowdown of the predicted best and
+    of the best of the predicted top two (an autotuner that times only two) against
+    the measured best."""
+    fams = selection_families(quick)
+    ctx.serve_set_weights(np.ascontiguousarray(weights, dtype=np.float64).reshape(1, 32))
+    ctx.serve_start(batch_interval_us=0, n_streams=1, max_batch_queries=16)
+    out = {}
+    try:
+        for fam, (probes, sizes) in fams.items():
+            P = probes[0].n_params
+            hi = [max(sz[j] for sz in sizes) for j in range(P)]
+            tids = [ctx.compile_counts(W.probe_ir(p), 32, [1] * P, hi)[0] for p in probes]
+            rows = []
+            for sz in sizes:
+                tables = np.array(tids, dtype=np.int32)
+                pts = np.zeros((len(probes), 4), dtype=np.int64)
+                pts[:, :P] = sz
+                idx, tt = np.zeros(16, dtype=np.int32), np.zeros(16)
+                tk = ctx.serve_submit(B.make_query(0, len(probes), tables, pts, idx, tt))
+                while ctx.serve_poll(tk, 100000) == B.PM_PENDING:
+                    pass
+                order = [int(i) for i in idx[:len(probes)]]
+                meas = time_cases([Case(p, sz, fam) for p in probes], runs, skip)
+                best = float(meas.min())
+                rows.append({"size": list(sz), "candidates": [p.name for p in probes],
+                             "predicted_order": order, "predicted_s": [float(x) for x in tt[:len(probes)]],
+                             "measured_s": [float(x) for x in meas],
+                             "top1_hit": bool(meas[order[0]] == best),
+                             "top1_slowdown": float(meas[order[0]] / best - 1.0),
+                             "top2_slowdown": float(min(meas[order[0]], meas[order[1]]) / best - 1.0)})
+            out[fam] = rows
+    finally:
+        ctx.serve_stop()
+    flat = [r for rows in out.values() for r in rows]
+    return {"families": out, "top1_hit_rate": float(np.mean([r["top1_hit"] for r in flat])),
+            "mean_top1_slowdown": float(np.mean([r["top1_slowdown"] for r in flat])),
+            "mean_top2_slowdown": float(np.mean([r["top2_slowdown"] for r in flat]))}
+
+
 def calibrate(ctx: B.Context, quick: bool = False, runs: int = 30, skip: int = 4) -> dict:
     """Time the measurement set, fit the weights, predict the test set."""
     import torch
@@ -189,6 +251,7 @@ def calibrate(ctx: B.Context, quick: bool = False, runs: int = 30, skip: int = 4
                     "cases": [(cases[i].label, float(meas_t[i]), float(pred_t[i])) for i in v]} for k, v in g.items()}
 
     return {
+        "selection": select(ctx, wv, quick, runs, skip),
         "fit_status": rc, "fit_report": rep[0],
         "weights": {COLUMN_NAMES[i]: float(wv[i]) for i in range(32) if wv[i] != 0.0},
         "measurement": {"n": len(meas), "geomean_rel_err": _geomean(em), "groups": per_group(meas, em, tm, pm)},

@@ -48,3 +48,9 @@ def test_quick_calibration(ctx):
     assert r["fit_status"] in (0, 1)
     assert r["measurement"]["geomean_rel_err"] < 0.5
     assert np.isfinite(r["test"]["geomean_rel_err"])
+    sel = r["selection"]
+    for rows in sel["families"].values():
+        for row in rows:
+            assert sorted(row["predicted_order"]) == list(range(len(row["candidates"])))
+            assert row["top1_slowdown"] >= 0 and row["top2_slowdown"] <= row["top1_slowdown"]
+            assert row["predicted_s"] == sorted(row["predicted_s"])
