@@ -8,8 +8,9 @@
  * |pi_i(D_i)| * n_ops,i, where |pi_i(D_i)| is the number of integer points of the
  * instruction's loop domain.  orc_count_brute obtains |pi_i(D_i)| by visiting every
  * point; orc_count_struct evaluates the same number per axis, numerically, at the
- * given parameter values (a box intersected with per-axis guards), and is pinned to
- * the brute force by the tests.
+ * given parameter values (a box intersected with per-axis guards; where guards couple
+ * indices, by visiting all indices but one and counting the last one's interval), and
+ * is pinned to the brute force by the tests.
  */
 #include "oracle.h"
 
@@ -620,6 +621,78 @@ static int struct_stmt(const orc_kernel *k, int s, const int64_t *par, i128 *out
   return 0;
 }
 
+/* Count of statement s at par when its guards couple indices (j < i, a band, a sequential
+   index bounded by a tiled one).  The indices fall into groups joined by shared guards;
+   the count is the product of the groups' counts.  In each group, visit every point of
+   all its indices but the one with the widest range, and take that index's interval
+   from the guards directly (each guard is affine: c x + e >= 0 with the others fixed).
+   Returns 0 and *out, or -3 if a group needs more than max_outer visits. */
+static int semi_stmt(const orc_kernel *k, int s, const int64_t *par, i128 max_outer, i128 *out) {
+  const stmt_t *st = &k->st[s];
+  int nd = st->n_dims;
+  i128 lo[MAXD], hi[MAXD];
+  int grp[MAXD];
+  for (int j = 0; j < nd; j++) {
+    dim_range(k, st->dims[j], par, &lo[j], &hi[j]);
+    if (hi[j] <= lo[j]) { *out = 0; return 0; }
+    grp[j] = j;
+  }
+  for (int g = 0; g < st->n_guards; g++) {          /* join the indices of each guard */
+    int first = -1;
+    for (int j = 0; j < nd; j++) {
+      if (!st->guards[g].coef[j]) continue;
+      if (first < 0) { first = j; continue; }
+      int a = grp[j], b = grp[first];
+      for (int q = 0; q < nd; q++) if (grp[q] == a) grp[q] = b;
+    }
+  }
+  i128 total = 1;
+  int64_t dimv[MAXD] = {0};
+  for (int g = 0; g < st->n_guards; g++) {          /* guards on the parameters alone */
+    int param_only = 1;
+    for (int j = 0; j < nd; j++) param_only &= !st->guards[g].coef[j];
+    if (param_only && ev(k, st->guards[g].e, par, dimv) < 0) { *out = 0; return 0; }
+  }
+  for (int r = 0; r < nd; r++) {
+    if (grp[r] != r) continue;                       /* r names its group */
+    int last = -1;
+    for (int j = 0; j < nd; j++)
+      if (grp[j] == r && (last < 0 || hi[j] - lo[j] >= hi[last] - lo[last])) last = j;
+    i128 outer = 1;
+    for (int j = 0; j < nd; j++) {
+      if (grp[j] != r || j == last) continue;
+      outer *= hi[j] - lo[j];
+      if (outer > max_outer) return -3;
+      dimv[st->dims[j]] = (int64_t)lo[j];
+    }
+    dimv[st->dims[last]] = 0;
+    i128 cnt = 0;
+    for (i128 it = 0; it < outer; it++) {
+      i128 a = lo[last], b = hi[last];
+      for (int g = 0; g < st->n_guards && a < b; g++) {
+        int mine = 0;
+        for (int j = 0; j < nd; j++) mine |= st->guards[g].coef[j] && grp[j] == r;
+        if (!mine) continue;
+        i128 e0 = ev(k, st->guards[g].e, par, dimv);   /* the guard at x_last = 0 */
+        i128 c = st->guards[g].coef[last];
+        if (c == 0) { if (e0 < 0) b = a; }
+        else if (c > 0) { i128 t = -floordiv(e0, c); if (t > a) a = t; }        /* x >= ceil(-e0/c) */
+        else { i128 t = floordiv(e0, -c) + 1; if (t < b) b = t; }               /* x <= floor(e0/|c|) */
+      }
+      if (b > a) cnt += b - a;
+      for (int j = nd - 1; j >= 0; j--) {                /* odometer over the group's other indices */
+        if (grp[j] != r || j == last) continue;
+        int d = st->dims[j];
+        if (++dimv[d] < hi[j]) break;
+        dimv[d] = (int64_t)lo[j];
+      }
+    }
+    total *= cnt;
+  }
+  *out = total;
+  return 0;
+}
+
 /* ------------------------------------------------------------------ classification (Sec. 2.1, Alg. 2) */
 
 static i128 lin_offset(const orc_kernel *k, const acc_t *a, const int64_t *par, const int64_t *dimv) {
@@ -797,6 +870,7 @@ int orc_count_struct(orc_kernel *k, const int64_t *par, int64_t *out) {
   for (int s = 0; s < k->n_st; s++) {
     i128 cnt;
     int r = struct_stmt(k, s, par, &cnt);
+    if (r == -3) r = semi_stmt(k, s, par, ((i128)1) << 30, &cnt);
     if (r) return r;
     add_stmt_keys(k, s, cnt, keys);
   }

@@ -40,9 +40,13 @@ from typing import Dict, List, Sequence, Tuple
 import numpy as np
 
 TEMPLATES = ("vecadd", "axpy", "copy", "transpose", "matmul", "stencil", "reduction", "matvec")
+# Kernels whose loop domains couple indices (triangles, bands): their counts are sums
+# of powers over piece chambers rather than products of per-axis intervals.
+COUPLED_TEMPLATES = ("trmv", "syrk", "band", "pairs")
 TEMPLATE_PARAMS = {
     "vecadd": ("n",), "axpy": ("n",), "copy": ("n",), "transpose": ("n",),
     "matmul": ("n", "m", "l"), "stencil": ("n",), "reduction": ("n",), "matvec": ("b",),
+    "trmv": ("n",), "syrk": ("n", "m"), "band": ("n", "w"), "pairs": ("n",),
 }
 TILES = (8, 16, 32, 64)
 UNROLLS = (1, 2, 4, 8)
@@ -280,8 +284,77 @@ def ir_matvec(v: Variant) -> str:
     return "\n".join(L) + "\n"
 
 
+# --------------------------------------------------------------------------- coupled domains
+
+def _rows(v: Variant) -> Tuple[List[str], str, str]:
+    """Row-per-work-item blocking of the 1-D coupled templates (wg rows per group) and
+    an unrolled inner index J = u*jo + ji over [0, ceil(extent/u)*u)."""
+    W, u = v.wg, v.unroll
+    return [f"dim g g0 0 ceil(n/{W})", f"dim l l0 0 {W}"], _lin([(W, "g"), (1, "l")]), \
+        _lin([(u, "jo"), (1, "ji")])
+
+
+def ir_trmv(v: Variant) -> str:
+    """y = L x with L lower triangular (diagonal included): row i sums over j <= i."""
+    dims, I, J = _rows(v)
+    u = v.unroll
+    L = [f"kernel {v.name}", "param n", "array a global f32 n,n", "array x global f32 n",
+         "array y global f32 n"] + dims + [
+        f"dim jo seq 0 ceil(n/{u})", f"dim ji seq 0 {u}",
+        "stmt mac g,l,jo,ji", f"guard {I} < n", f"guard {J} < n", f"guard {J} <= {I}",
+        f"load a[{I},{J}]", f"load x[{J}]", "flop f32 mul 1", "flop f32 add 1", "end",
+        "stmt st g,l", f"guard {I} < n", f"store y[{I}]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_pairs(v: Variant) -> str:
+    """Pairwise interactions over j < i (each pair once, as in a symmetric n-body step):
+    relative position, r^2 + eps, rsqrt, r^-3 m and the force accumulation."""
+    dims, I, J = _rows(v)
+    u = v.unroll
+    L = [f"kernel {v.name}", "param n", "array p global f32 n,4", "array f global f32 n,4"] + dims + [
+        f"dim jo seq 0 ceil(n/{u})", f"dim ji seq 0 {u}",
+        "stmt own g,l", f"guard {I} < n", f"load p[{I},0]", f"load p[{I},1]", f"load p[{I},2]", "end",
+        "stmt pair g,l,jo,ji", f"guard {I} < n", f"guard {J} < n", f"guard {J} < {I}",
+        f"load p[{J},0]", f"load p[{J},1]", f"load p[{J},2]", f"load p[{J},3]",
+        "flop f32 add 9", "flop f32 mul 9", "flop f32 spec 1", "end",
+        "stmt st g,l", f"guard {I} < n", f"store f[{I},0]", f"store f[{I},1]", f"store f[{I},2]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_band(v: Variant) -> str:
+    """y = A x for A banded with half-bandwidth w, stored as n x (2w+1): row i reads
+    x[i - w + t] for the t in [0, 2w] that land inside [0, n)."""
+    dims, I, T = _rows(v)
+    T = _lin([(v.unroll, "to"), (1, "ti")])
+    u = v.unroll
+    L = [f"kernel {v.name}", "param n w", "array a global f32 n,2*w+1", "array x global f32 n",
+         "array y global f32 n"] + dims + [
+        f"dim to seq 0 ceil((2*w+1)/{u})", f"dim ti seq 0 {u}",
+        "stmt mac g,l,to,ti", f"guard {I} < n", f"guard {T} < 2*w+1", f"guard {I}+{T} >= w",
+        f"guard {I}+{T} < n+w", f"load a[{I},{T}]", f"load x[{I}+{T}-w]", "flop f32 mul 1", "flop f32 add 1",
+        "end", "stmt st g,l", f"guard {I} < n", f"store y[{I}]", "end"]
+    return "\n".join(L) + "\n"
+
+
+def ir_syrk(v: Variant) -> str:
+    """Lower triangle of C = A A^T (A: n x m): tx x ty tiles of C per group, column
+    index on the lanes, the m-loop unrolled by u; only entries with j <= i."""
+    tx, ty, u = v.tx, v.ty, v.unroll
+    I, J, K = _lin([(ty, "gy"), (1, "ly")]), _lin([(tx, "gx"), (1, "lx")]), _lin([(u, "ko"), (1, "ki")])
+    tri = [f"guard {J} < n", f"guard {I} < n", f"guard {J} <= {I}"]
+    L = [f"kernel {v.name}", "param n m", "array A global f32 n,m", "array C global f32 n,n",
+         f"dim gx g0 0 ceil(n/{tx})", f"dim gy g1 0 ceil(n/{ty})", f"dim ly l1 0 {ty}", f"dim lx l0 0 {tx}",
+         f"dim ko seq 0 ceil(m/{u})", f"dim ki seq 0 {u}",
+         "stmt mac gx,gy,ly,lx,ko,ki"] + tri + [f"guard {K} < m", f"load A[{I},{K}]", f"load A[{J},{K}]",
+                                                "flop f32 mul 1", "flop f32 add 1", "end",
+                                                "stmt st gx,gy,ly,lx"] + tri + [f"store C[{I},{J}]", "end"]
+    return "\n".join(L) + "\n"
+
+
 _IR = {"vecadd": ir_vecadd, "axpy": ir_axpy, "copy": ir_copy, "transpose": ir_transpose,
-       "matmul": ir_matmul, "stencil": ir_stencil, "reduction": ir_reduction, "matvec": ir_matvec}
+       "matmul": ir_matmul, "stencil": ir_stencil, "reduction": ir_reduction, "matvec": ir_matvec,
+       "trmv": ir_trmv, "pairs": ir_pairs, "band": ir_band, "syrk": ir_syrk}
 
 
 def variant_ir(v: Variant) -> str:
@@ -317,6 +390,10 @@ def valid(v: Variant) -> bool:
         return WY <= ty and ty % WY == 0 and ((ty // WY) % u == 0)
     if t == "matvec":
         return (tx, ty) == (8, 8) and 32 % u == 0
+    if t in ("trmv", "pairs", "band"):
+        return (not p) and tx == W and ty == 1
+    if t == "syrk":
+        return (not p) and tx * ty == W
     return False
 
 
@@ -343,6 +420,27 @@ def all_variants() -> List[Variant]:
     return out
 
 
+def coupled_variants() -> List[Variant]:
+    """The tuning space of the coupled-domain templates: rows per group (trmv, pairs,
+    band) or the C tile (syrk) and the inner unroll."""
+    out = []
+    for t in COUPLED_TEMPLATES:
+        for W in WGS:
+            for u in UNROLLS:
+                if t == "syrk":
+                    out += [Variant(t, tx, W // tx, u, False, W) for tx in TILES if W // tx in TILES]
+                else:
+                    out.append(Variant(t, W, 1, u, False, W))
+    return out
+
+
+def draw_coupled_variants(n_variants: int, seed: int = 12) -> List[Variant]:
+    """Coupled-domain variants drawn uniformly with replacement (duplicates tie)."""
+    allv = coupled_variants()
+    rng = np.random.default_rng(seed)
+    return [allv[i] for i in rng.integers(len(allv), size=n_variants)]
+
+
 def draw_variants(n_variants: int, seed: int = 2) -> List[Variant]:
     """Draw variants with replacement from the tuning space: template, tile in
     {8..64}^2, unroll in {1,2,4,8}, prefetch on/off, work-group size in {64..512}.
@@ -359,8 +457,8 @@ def draw_variants(n_variants: int, seed: int = 2) -> List[Variant]:
     return out
 
 
-def group_by_template(variants: Sequence[Variant]) -> Dict[str, List[int]]:
-    g: Dict[str, List[int]] = {t: [] for t in TEMPLATES}
+def group_by_template(variants: Sequence[Variant], templates: Sequence[str] = TEMPLATES) -> Dict[str, List[int]]:
+    g: Dict[str, List[int]] = {t: [] for t in templates}
     for i, v in enumerate(variants):
         g[v.template].append(i)
     return g
@@ -373,10 +471,11 @@ def draw_points(n_params: int, n_points: int, seed: int, lo: int = BOX_LO, hi: i
     return np.clip(np.floor(x), lo, hi).astype(np.int64)
 
 
-def template_points(seed: int, n_points: int, lo: int = BOX_LO, hi: int = BOX_HI) -> Dict[str, np.ndarray]:
+def template_points(seed: int, n_points: int, lo: int = BOX_LO, hi: int = BOX_HI,
+                    templates: Sequence[str] = TEMPLATES) -> Dict[str, np.ndarray]:
     """One independent point set per template (seed offset by template index)."""
     return {t: draw_points(len(TEMPLATE_PARAMS[t]), n_points, seed * 1000 + i, lo, hi)
-            for i, t in enumerate(TEMPLATES)}
+            for i, t in enumerate(templates)}
 
 
 def draw_weights(k: int, n_models: int, seed: int, lo: float = 1e-12, hi: float = 1e-9) -> np.ndarray:

@@ -117,6 +117,59 @@ def test_planted_mistake_is_caught():
     assert bad.features([65], 32, "brute")[0][4] == 128 != 65
 
 
+# ----------------------------------------------------------------------------- coupled domains
+
+def _band_entries(n, w):
+    """Entries of an n x n band |i - j| <= w: the full-width band minus its two clipped
+    triangular corners of w(w+1)/2 entries each (w < n), or the whole matrix."""
+    return n * n if w >= n - 1 else n * (2 * w + 1) - w * (w + 1)
+
+
+_KERN = {}
+
+
+def ckern(v):
+    if v.key not in _KERN:
+        _KERN[v.key] = kern(v)
+    return _KERN[v.key]
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 64, 1000, 65536])
+def test_coupled_closed_forms(n):
+    """Domains whose bounds couple indices (Sec. 3.2 counts the integer points of any
+    affine domain): j <= i has n(n+1)/2 points, j < i has n(n-1)/2, syrk's m-loop
+    multiplies its triangle by m, and a band of half-width w has n(2w+1) - w(w+1)."""
+    cv = {t: [v for v in W.coupled_variants() if v.template == t] for t in W.COUPLED_TEMPLATES}
+    for v in cv["trmv"][::5]:
+        F = ckern(v).features([n])[0]
+        assert F[4] == F[3] == n * (n + 1) // 2 and F[24] == n, v.name      # mul, add, y stores
+    for v in cv["pairs"][::5]:
+        F = ckern(v).features([n])[0]
+        assert F[7] == n * (n - 1) // 2 and F[4] == F[3] == 9 * n * (n - 1) // 2, v.name
+    for m in (1, 3, 100):
+        for v in cv["syrk"][::7]:
+            F = ckern(v).features([n, m])[0]
+            assert F[4] == m * n * (n + 1) // 2 and F[24] == n * (n + 1) // 2, v.name
+    for w in sorted({0, 1, 5, max(n - 1, 0), n, 3 * n}):
+        for v in cv["band"][::5]:
+            F = ckern(v).features([n, w])[0]
+            assert F[4] == _band_entries(n, w) and F[24] == n, (v.name, w)
+
+
+@pytest.mark.parametrize("t", W.COUPLED_TEMPLATES)
+def test_brute_equals_struct_coupled(t):
+    """The per-axis evaluator's coupled path (all indices but one visited) against
+    visiting every point, on every n in [1, 40] (and w in a few widths)."""
+    vs = [v for v in W.coupled_variants() if v.template == t][::3]
+    if t in ("syrk", "band"):
+        pts = np.array([(a, b) for a in range(1, 41, 3) for b in (0, 1, 2, 7, 39, 80) if t == "band" or b > 0])
+    else:
+        pts = np.arange(1, 41, dtype=np.int64).reshape(-1, 1)
+    for v in vs:
+        k = ckern(v)
+        assert (k.features(pts, 32, "brute") == k.features(pts, 32, "struct")).all(), v.name
+
+
 # ----------------------------------------------------------------------------- classification
 
 def _acc_kernel(accesses, n_arr_ext="4*n"):
