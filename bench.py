@@ -8,7 +8,8 @@ One step = one pass of that whole path over the batch.  Prints one JSON line.
 Multi-GPU (torchrun): every rank ranks its own point batch of the same size (weak
 scaling; rank r draws its points with seed 3 + 7919 r); no data-path collective, the
 process group only brackets the timing (barrier, max over ranks).
-Other workloads: --workload eval | predict | fit | serve | calibrate.
+Other workloads: --workload eval | predict | fit | serve | calibrate | coupled
+(coupled: the same fused path over the coupled-domain templates, triangles and bands).
 """
 from __future__ import annotations
 
@@ -27,6 +28,8 @@ sys.path.insert(0, ROOT)
 METRIC = "model evals/s (variant x param points), fused evaluate+predict+top-16"
 UNIT = "evals/s"
 WORKLOAD = "batched tuning space: 10,000 variants x 4,096 points per template, 8 templates, top-16, FP64-accurate"
+WORKLOAD_COUPLED = ("coupled-domain tuning space (triangular matvec, syrk, band matvec, pair interactions): "
+                    "10,000 variants x 4,096 points per template, 4 templates, top-16, FP64-accurate")
 
 
 def _dist():
@@ -79,10 +82,12 @@ class Clocks:
                 "samples": len(self.rows), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(bp, w, target_s: float = 8.0):
-    """The oracle (structural counts + compensated dot + insertion top-16), as it
-    stands, on all host cores, on a bounded sample of the same workload: every
-    variant of every template, the first n points of each template."""
+def _oracle_sample(bp, w, target_s: float):
+    """Time the oracle (structural counts + compensated dot + insertion top-16), as it
+    stands, on all host cores, on a bounded sample of the workload: the first v
+    variants and the first n points of every template, grown from 8 variants x 2 points
+    per core (variants first, then points) until a pass takes at least half of target_s.
+    Returns (evals/s, cores, v, n, evals, seconds)."""
     import numpy as np
 
     import oracle
@@ -91,32 +96,50 @@ def cpu_baseline(bp, w, target_s: float = 8.0):
     kern = {}
     per_t = []
     for ti, t in enumerate(bp.templates):
-        vs = bp.variants[bp.var_off[ti]:bp.var_off[ti + 1]]
         ks = []
-        for v in vs:
+        for v in bp.variants[bp.var_off[ti]:bp.var_off[ti + 1]]:
             if v.key not in kern:
                 kern[v.key] = oracle.Kernel(W.variant_ir(v))
             ks.append(kern[v.key])
         per_t.append(ks)
-    n = 8
-    while True:
+
+    def run(nv, n):
         evals = 0
         t0 = time.perf_counter()
         for ti, t in enumerate(bp.templates):
-            if not per_t[ti]:
+            ks = per_t[ti][:nv]
+            if not ks:
                 continue
             P = len(W.TEMPLATE_PARAMS[t])
             p0 = int(bp.pt_off[ti])
             pts = np.ascontiguousarray(bp.points[p0:p0 + n, :P])
-            oracle.eval_predict_topk(per_t[ti], pts, w, 16, n_threads=cores)
-            evals += len(per_t[ti]) * len(pts)
-        dt = time.perf_counter() - t0
-        if dt >= target_s or n >= 4096:
+            oracle.eval_predict_topk(ks, pts, w, 16, n_threads=cores)
+            evals += len(ks) * len(pts)
+        return evals, time.perf_counter() - t0
+
+    vmax = max(len(k) for k in per_t)
+    nv, n = 8, min(4096, 2 * cores)   # enough points to occupy every core
+    while True:
+        ev, dt = run(nv, n)
+        if dt >= 0.5 * target_s or (nv >= vmax and n >= 4096):
             break
-        n = min(4096, max(n * 2, int(n * target_s / max(dt, 1e-3) * 1.1)))
-    return {"value": evals / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"all {len(bp.variants)} variants x first {n} points of each template "
-                      f"({evals} evals, {dt:.1f} s, OpenMP over points)"}
+        grow = target_s / max(dt, 1e-3) * 1.1
+        if nv < vmax:
+            nv = min(vmax, max(nv * 2, int(nv * grow)))
+        else:
+            n = min(4096, max(n * 2, int(n * grow)))
+    return ev / dt, cores, nv, n, ev, dt
+
+
+def _sample_text(bp, nv, n, ev, dt):
+    vmax = max(bp.var_off[t + 1] - bp.var_off[t] for t in range(len(bp.templates)))
+    which = f"all {len(bp.variants)} variants" if nv >= vmax else f"the first {nv} variants of each template"
+    return f"{which} x first {n} points of each template ({ev} evals, {dt:.1f} s, OpenMP over points)"
+
+
+def cpu_baseline(bp, w, target_s: float = 8.0):
+    value, cores, nv, n, ev, dt = _oracle_sample(bp, w, target_s)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": _sample_text(bp, nv, n, ev, dt)}
 
 
 def run_reference(args):
@@ -132,15 +155,16 @@ def run_reference(args):
     import __graft_entry__
     __graft_entry__.build()
     ctx = B.Context(-1)
-    bp = tuning.build(ctx, args.variants, args.points)
+    coupled = args.workload == "coupled"
+    bp = tuning.build(ctx, args.variants, args.points, variant_seed=12 if coupled else 2, coupled=coupled)
     w = W.draw_weights(32, 1, 4)[0]
-    base = cpu_baseline(bp, w, target_s=args.ref_step_s)
-    # each step: the same bounded sample as the baseline
-    n_pts = int(base["sample"].split("first ")[1].split(" points")[0])
+    # each step: the bounded sample that the probe sizes to about ref_step_s
+    _, cores, n_var, n_pts, ev0, dt0 = _oracle_sample(bp, w, args.ref_step_s)
+    base = {"cores": cores, "sample": _sample_text(bp, n_var, n_pts, ev0, dt0)}
     kern, per_t = {}, []
     for ti, t in enumerate(bp.templates):
         ks = []
-        for v in bp.variants[bp.var_off[ti]:bp.var_off[ti + 1]]:
+        for v in bp.variants[bp.var_off[ti]:bp.var_off[ti + 1]][:n_var]:
             if v.key not in kern:
                 kern[v.key] = oracle.Kernel(W.variant_ir(v))
             ks.append(kern[v.key])
@@ -168,7 +192,8 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD + " (CPU oracle on a bounded sample per step)"},
+            "config": {"workload": (WORKLOAD_COUPLED if coupled else WORKLOAD) +
+                                   " (CPU oracle on a bounded sample per step)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                              "sample": base["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -197,7 +222,9 @@ def run_ours(args):
     ctx = B.Context(local)
     ctx.tune(not args.no_tune, None)
     # weak scaling: every rank ranks its own point batch (independent units, no exchange)
-    bp = tuning.build(ctx, args.variants, args.points, point_seed=sharding.rank_point_seed(3, rank))
+    coupled = args.workload == "coupled"
+    bp = tuning.build(ctx, args.variants, args.points, point_seed=sharding.rank_point_seed(3, rank),
+                      variant_seed=12 if coupled else 2, coupled=coupled)
     w = W.draw_weights(32, 1, 4)[0]
     n = bp.points.shape[0]
     stream = torch.cuda.Stream(dev)
@@ -274,7 +301,8 @@ def run_ours(args):
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = sms * 128 * max_mhz * 1e6           # lane-instruction issue rate at the maximum clock
     achieved = evals * info["work_per_eval"] / (ms / 1e3)
-    traffic = _profile_traffic("eval_predict_topk_batched_10000x4096.md",
+    traffic = _profile_traffic("eval_predict_topk_coupled_10000x4096.md" if coupled else
+                               "eval_predict_topk_batched_10000x4096.md",
                                ("eval.cu", "eval_common.cuh", "pm_table.h", "plan.cpp"))
 
     if rank == 0:
@@ -283,7 +311,8 @@ def run_ours(args):
             "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64 counts, fp32-compensated (FP64-accurate) predict",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "variants": len(bp.variants), "distinct_variants": bp.n_distinct,
+            "config": {"workload": WORKLOAD_COUPLED if coupled else WORKLOAD, "variants": len(bp.variants),
+                       "distinct_variants": bp.n_distinct,
                        "points_per_template": args.points, "evals_per_step": evals, "topk": 16,
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch": {"warps_per_cta": info["nw"], "ctas": info["grid"], "units": info["units"]},
@@ -599,7 +628,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "eval", "predict", "fit", "serve", "calibrate"])
+                    choices=["batched", "eval", "predict", "fit", "serve", "calibrate", "coupled"])
     ap.add_argument("--calib-out", default=None, help="write the full calibration result (JSON) here")
     ap.add_argument("--serve-queries", type=int, default=1000)
     args = ap.parse_args()
@@ -609,7 +638,7 @@ def main():
         run_serve(args)
     elif args.workload == "calibrate":
         run_calibrate(args)
-    elif args.workload != "batched":
+    elif args.workload not in ("batched", "coupled"):
         run_other(args)
     else:
         run_ours(args)

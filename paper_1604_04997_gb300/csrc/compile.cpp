@@ -515,9 +515,20 @@ static void poly_acc(Poly &a, const Poly &b, i128 s) {
 // One case of a factor or of a statement count: literals that select it and its value.
 struct Case {
   std::vector<std::pair<int, bool>> lits;
-  Poly val;
+  Poly val;    // the value is val / den
   i128 bound;  // upper bound of the value over the box
+  i128 den = 1;
 };
+
+static void poly_reduce(Poly &p, i128 &den) {  // divide val and den by their common factor
+  if (p.empty()) { den = 1; return; }
+  i128 g = den;
+  for (auto &kv : p) g = gcd128(g, kv.second);
+  if (g > 1) {
+    for (auto &kv : p) kv.second /= g;
+    den /= g;
+  }
+}
 
 // Interval length max(0, min(U) - max(L)) -> cases.
 static std::vector<Case> interval_cases(Compiler &C, std::vector<QAff> U, std::vector<QAff> L) {
@@ -600,12 +611,398 @@ static std::vector<Case> case_product(const std::vector<Case> &A, const std::vec
         if (!dup) c.lits.push_back(l);
       }
       if (bad) continue;
-      if (a.val.empty() || b.val.empty()) { c.val = Poly(); c.bound = 0; }
-      else { c.val = poly_mul(a.val, b.val); c.bound = a.bound * b.bound; }
+      if (a.val.empty() || b.val.empty()) { c.val = Poly(); c.bound = 0; c.den = 1; }
+      else {
+        c.val = poly_mul(a.val, b.val);
+        c.bound = a.bound * b.bound;
+        c.den = a.den * b.den;
+        poly_reduce(c.val, c.den);
+      }
       out.push_back(c);
     }
   return out;
 }
+
+// ----------------------------------------------------------------------------------- coupled domains
+//
+// Guards that tie loop indices together (j < i, i + j < n, a band |i - j| <= w, a
+// sequential index bounded by a tiled one) do not factor into per-axis intervals.
+// Their count is taken by eliminating one index at a time, innermost first.  For
+// each choice of the index's active bounds (the largest lower bound and the smallest
+// upper bound, ties to the first listed) the index runs over [L, U); the choice and
+// L < U become linear constraints on the indices still to be eliminated, and the
+// summand is summed in closed form with Faulhaber's polynomials,
+//     sum_{x=L}^{U-1} x^k = S_k(U) - S_k(L).
+// When no index is left, the remaining constraints are conditions on the parameters
+// (piece conditions) and the chambers whose conditions hold are added up.  S_k has
+// rational coefficients (S_1(z) = (z^2 - z)/2), so values carry a denominator.
+
+constexpr int VAR0 = 0xC0;             // polynomial factor ids >= VAR0 are loop variables
+typedef std::vector<uint8_t> EMono;    // sorted factor ids
+typedef std::map<EMono, i128> EPoly;
+struct RPoly {                         // num / den, den > 0
+  EPoly num;
+  i128 den = 1;
+};
+
+static void ep_clean(EPoly &p) {
+  for (auto it = p.begin(); it != p.end();) it = it->second ? std::next(it) : p.erase(it);
+}
+static void ep_acc(EPoly &a, const EPoly &b, i128 s) {
+  for (auto &kv : b) a[kv.first] += s * kv.second;
+  ep_clean(a);
+}
+static EPoly ep_const(i128 c) {
+  EPoly r;
+  if (c) r[EMono{}] = c;
+  return r;
+}
+static EPoly ep_mul(const EPoly &a, const EPoly &b) {
+  EPoly r;
+  for (auto &x : a)
+    for (auto &y : b) {
+      EMono m(x.first);
+      m.insert(m.end(), y.first.begin(), y.first.end());
+      if (m.size() > 8) fail(E_UNSUP, "coupled-domain count of degree above 8");
+      std::sort(m.begin(), m.end());
+      r[m] += x.second * y.second;
+    }
+  ep_clean(r);
+  return r;
+}
+static EPoly ep_qaff(const QAff &q, int P) {
+  EPoly r = ep_const(q.c);
+  for (int i = 0; i < 4; i++)
+    if (q.p[i]) r[EMono{(uint8_t)i}] += q.p[i];
+  for (auto &kv : q.at) {
+    if (!kv.second) continue;
+    if (P + kv.first >= VAR0) fail(E_UNSUP, "too many atoms");
+    r[EMono{(uint8_t)(P + kv.first)}] += kv.second;
+  }
+  ep_clean(r);
+  return r;
+}
+static RPoly rp_norm(RPoly r) {
+  ep_clean(r.num);
+  if (r.num.empty()) { r.den = 1; return r; }
+  i128 g = r.den;
+  for (auto &kv : r.num) g = gcd128(g, kv.second);
+  if (g > 1) {
+    for (auto &kv : r.num) kv.second /= g;
+    r.den /= g;
+  }
+  return r;
+}
+static RPoly rp_add(const RPoly &a, const RPoly &b, i128 s) {
+  RPoly r;
+  r.den = a.den / gcd128(a.den, b.den) * b.den;
+  ep_acc(r.num, a.num, r.den / a.den);
+  ep_acc(r.num, b.num, s * (r.den / b.den));
+  return rp_norm(r);
+}
+static RPoly rp_mul(const RPoly &a, const RPoly &b) {
+  RPoly r;
+  r.num = ep_mul(a.num, b.num);
+  r.den = a.den * b.den;
+  return rp_norm(r);
+}
+
+// S_k(z) = sum_{x=0}^{z-1} x^k = (sum_j FH[k][j] z^j) / FH_DEN[k].  S_k(z+1) - S_k(z) = z^k
+// holds as a polynomial identity, so S_k(U) - S_k(L) is the sum over [L, U) for any L <= U.
+static const int64_t FH[5][6] = {{0, 1, 0, 0, 0, 0}, {0, -1, 1, 0, 0, 0}, {0, 1, -3, 2, 0, 0},
+                                 {0, 0, 1, -2, 1, 0}, {0, -1, 0, 10, -15, 6}};
+static const int64_t FH_DEN[5] = {1, 2, 6, 4, 30};
+static RPoly faulhaber(int k, const EPoly &z) {
+  RPoly r;
+  r.den = FH_DEN[k];
+  EPoly pw = ep_const(1);
+  for (int j = 1; j <= k + 1; j++) {
+    pw = ep_mul(pw, z);
+    ep_acc(r.num, pw, FH[k][j]);
+  }
+  return rp_norm(r);
+}
+
+struct Lin {  // sum_v a[v] x_v + e; as a constraint, Lin >= 0
+  std::vector<i128> a;
+  QAff e;
+  bool var_free() const {
+    for (auto x : a) if (x) return false;
+    return true;
+  }
+  bool operator==(const Lin &o) const { return a == o.a && e == o.e; }
+};
+static Lin lin_add(const Lin &x, const Lin &y, i128 s) {
+  Lin r = x;
+  for (size_t v = 0; v < r.a.size(); v++) r.a[v] += s * y.a[v];
+  r.e = q_add(x.e, y.e, s);
+  return r;
+}
+static Lin lin_scale(const Lin &x, i128 s) {
+  Lin r = x;
+  for (auto &v : r.a) v *= s;
+  r.e = q_scale(x.e, s);
+  return r;
+}
+static Lin lin_plus(const Lin &x, i128 c) {
+  Lin r = x;
+  r.e = q_add(x.e, q_const(c), 1);
+  return r;
+}
+static EPoly ep_lin(const Lin &l, int P) {
+  EPoly r = ep_qaff(l.e, P);
+  for (size_t v = 0; v < l.a.size(); v++)
+    if (l.a[v]) r[EMono{(uint8_t)(VAR0 + v)}] += l.a[v];
+  ep_clean(r);
+  return r;
+}
+
+struct Chamber {  // one region of the index space: literals, constraints, summand
+  std::vector<std::pair<int, bool>> lits;
+  std::vector<Lin> cons;
+  RPoly f;
+};
+
+struct CoupledCounter {
+  Compiler &C;
+  size_t m;                 // variables
+  std::vector<int> depth;   // nesting depth of each variable (deeper ones go first)
+
+  // Sound proof that x >= 0 on the chamber: x - c is provably non-negative for one of its
+  // constraints c (or for c = 0), bounding each variable of x - c by its unit-coefficient
+  // single-variable constraints.
+  bool nonneg(const Chamber &t, const Lin &x) const {
+    std::vector<std::vector<QAff>> lo(m), hi(m);  // x_v >= lo, x_v <= hi
+    for (auto &c : t.cons) {
+      int v = -1, nz = 0;
+      for (size_t w = 0; w < m; w++)
+        if (c.a[w]) { v = (int)w; nz++; }
+      if (nz != 1) continue;
+      if (c.a[v] == 1) lo[v].push_back(q_scale(c.e, -1));
+      else if (c.a[v] == -1) hi[v].push_back(c.e);
+    }
+    std::vector<const Lin *> base = {nullptr};
+    for (auto &c : t.cons) base.push_back(&c);
+    for (auto *c : base) {
+      Lin d = c ? lin_add(x, *c, -1) : x;
+      // try every combination of bounds (few in practice)
+      std::vector<const std::vector<QAff> *> opts;
+      std::vector<size_t> vs;
+      bool ok = true;
+      for (size_t v = 0; v < m && ok; v++) {
+        if (!d.a[v]) continue;
+        const auto &o = d.a[v] > 0 ? lo[v] : hi[v];
+        if (o.empty()) ok = false;
+        opts.push_back(&o);
+        vs.push_back(v);
+      }
+      if (!ok) continue;
+      std::vector<size_t> idx(vs.size(), 0);
+      for (int guard = 0; guard < 64; guard++) {
+        QAff q = d.e;
+        for (size_t k = 0; k < vs.size(); k++) q = q_add(q, (*opts[k])[idx[k]], d.a[vs[k]]);
+        if (C.prove(q) == 1) return true;
+        size_t k = 0;
+        while (k < vs.size() && ++idx[k] == opts[k]->size()) idx[k++] = 0;
+        if (k == vs.size()) break;
+      }
+    }
+    return false;
+  }
+  // sum a x + e >= 0 with g = gcd(a) > 1 holds iff sum (a/g) x + floor(e/g) >= 0 (the
+  // left side is a multiple of g); floor(e/g) must stay quasi-affine, else x is kept.
+  Lin tighten(const Lin &x) const {
+    i128 g = 0;
+    for (auto v : x.a) g = gcd128(g, v);
+    if (g <= 1) return x;
+    Lin r = x;
+    for (auto &v : r.a) v /= g;
+    if (x.e.at.empty()) {
+      Aff e;
+      e.c = x.e.c;
+      for (int i = 0; i < 4; i++) e.p[i] = x.e.p[i];
+      r.e = C.floor_of(e, g);
+      return r;
+    }
+    for (int i = 0; i < 4; i++) if (x.e.p[i] % g) return x;
+    for (auto &kv : x.e.at) if (kv.second % g) return x;
+    r.e = q_scale(x.e, 1);
+    for (int i = 0; i < 4; i++) r.e.p[i] /= g;
+    for (auto &kv : r.e.at) kv.second /= g;
+    r.e.c = fdiv(x.e.c, g);
+    return r;
+  }
+  // Add constraint x0 >= 0; false if the chamber is then empty.
+  bool add(Chamber &t, const Lin &x0) {
+    const Lin x = tighten(x0);
+    if (x.var_free()) {
+      int s = C.prove(x.e);
+      if (s == 1) return true;
+      if (s == -1) return false;
+      auto l = C.literal(x.e);
+      for (auto &q : t.lits)
+        if (q.first == l.first) return q.second == l.second;
+      t.lits.push_back({l.first, l.second});
+      return true;
+    }
+    for (auto &c : t.cons)
+      if (c == x) return true;
+    if (nonneg(t, x)) return true;
+    if (nonneg(t, lin_plus(lin_scale(x, -1), -1))) return false;
+    t.cons.push_back(x);
+    return true;
+  }
+  // Can x be eliminated from t: every constraint on x has coefficient +-1, or bounds x
+  // alone by an atom-free parameter expression.
+  bool eligible(const Chamber &t, size_t x) const {
+    bool used = false;
+    for (auto &c : t.cons) {
+      i128 ax = c.a[x];
+      if (!ax) continue;
+      used = true;
+      if (ax == 1 || ax == -1) continue;
+      Lin r = c;
+      r.a[x] = 0;
+      if (!r.var_free() || !r.e.at.empty()) return false;
+    }
+    return used;
+  }
+  std::vector<Chamber> eliminate(const Chamber &t, size_t x) {
+    std::vector<Lin> lows, ups, rest;  // x >= low, x < up
+    for (auto &c : t.cons) {
+      i128 ax = c.a[x];
+      if (!ax) { rest.push_back(c); continue; }
+      Lin r = c;
+      r.a[x] = 0;
+      if (ax == 1) { lows.push_back(lin_scale(r, -1)); continue; }
+      if (ax == -1) { ups.push_back(lin_plus(r, 1)); continue; }
+      Aff e;
+      e.c = r.e.c;
+      for (int i = 0; i < 4; i++) e.p[i] = r.e.p[i];
+      Lin b = r;
+      if (ax > 0) {  // x >= ceil(-e / ax)
+        Aff num = aff_scale(e, -1);
+        num.c += ax - 1;
+        b.e = C.floor_of(num, ax);
+        lows.push_back(b);
+      } else {       // x <= floor(e / |ax|)
+        b.e = q_add(C.floor_of(e, -ax), q_const(1), 1);
+        ups.push_back(b);
+      }
+    }
+    // drop bounds that another bound makes redundant everywhere on the chamber
+    auto prune = [&](std::vector<Lin> &v, bool upper) {
+      std::vector<Lin> kept;
+      for (auto &b : v) {
+        bool drop = false;
+        for (auto &k : kept)
+          if (k == b || nonneg(t, upper ? lin_add(b, k, -1) : lin_add(k, b, -1))) { drop = true; break; }
+        if (drop) continue;
+        std::vector<Lin> k2;
+        for (auto &k : kept)
+          if (!nonneg(t, upper ? lin_add(k, b, -1) : lin_add(b, k, -1))) k2.push_back(k);
+        k2.push_back(b);
+        kept.swap(k2);
+      }
+      v.swap(kept);
+    };
+    prune(ups, true);
+    prune(lows, false);
+    if (ups.empty() || lows.empty()) fail(E_UNSUP, "unbounded loop index");
+    // the summand by powers of x
+    std::vector<RPoly> g;
+    for (auto &kv : t.f.num) {
+      EMono rem;
+      size_t k = 0;
+      for (auto id : kv.first) {
+        if (id == VAR0 + x) k++;
+        else rem.push_back(id);
+      }
+      if (k > 4) fail(E_UNSUP, "coupled-domain summand of degree above 4 in one index");
+      if (g.size() <= k) g.resize(k + 1);
+      g[k].den = t.f.den;
+      g[k].num[rem] += kv.second;
+    }
+    std::vector<Chamber> out;
+    for (size_t iu = 0; iu < ups.size(); iu++)
+      for (size_t il = 0; il < lows.size(); il++) {
+        Chamber n;
+        n.lits = t.lits;
+        n.cons = rest;
+        bool ok = true;
+        for (size_t i2 = 0; i2 < ups.size() && ok; i2++)
+          if (i2 != iu) ok = add(n, lin_plus(lin_add(ups[i2], ups[iu], -1), i2 < iu ? -1 : 0));
+        for (size_t l2 = 0; l2 < lows.size() && ok; l2++)
+          if (l2 != il) ok = add(n, lin_plus(lin_add(lows[il], lows[l2], -1), l2 < il ? -1 : 0));
+        if (ok) ok = add(n, lin_plus(lin_add(ups[iu], lows[il], -1), -1));
+        if (!ok) continue;
+        const EPoly U = ep_lin(ups[iu], C.P), L = ep_lin(lows[il], C.P);
+        RPoly f;
+        for (size_t k = 0; k < g.size(); k++) {
+          if (g[k].num.empty()) continue;
+          f = rp_add(f, rp_mul(rp_norm(g[k]), rp_add(faulhaber((int)k, U), faulhaber((int)k, L), -1)), 1);
+        }
+        if (f.num.empty()) continue;
+        n.f = f;
+        out.push_back(n);
+      }
+    return out;
+  }
+
+  std::vector<Case> count(const std::vector<Lin> &cons, i128 bound) {
+    Chamber t0;
+    for (auto &c : cons) t0.cons.push_back(tighten(c));
+    t0.f.num = ep_const(1);
+    std::vector<Chamber> work = {t0}, done;
+    while (!work.empty()) {
+      Chamber t = work.back();
+      work.pop_back();
+      int x = -1;
+      bool left = false;
+      for (size_t v = 0; v < m; v++) {
+        bool used = false;
+        for (auto &c : t.cons) used = used || c.a[v] != 0;
+        if (!used) continue;
+        left = true;
+        if (eligible(t, v) && (x < 0 || depth[v] > depth[x])) x = (int)v;
+      }
+      if (!left) { done.push_back(t); continue; }
+      if (x < 0) fail(E_UNSUP, "coupled guards with non-unit coefficients on shared indices");
+      for (auto &n : eliminate(t, (size_t)x)) work.push_back(n);
+      if (work.size() + done.size() > 4096) fail(E_UNSUP, "coupled domain splits into too many chambers");
+    }
+    // chambers hold at once for one parameter point: add up those whose literals hold
+    std::vector<int> ids;
+    for (auto &t : done)
+      for (auto &l : t.lits)
+        if (std::find(ids.begin(), ids.end(), l.first) == ids.end()) ids.push_back(l.first);
+    if (ids.size() > (size_t)pmt::MAX_CONDS) fail(E_UNSUP, "more than 10 piece conditions");
+    std::vector<Case> out;
+    for (uint32_t asg = 0; asg < (1u << ids.size()); asg++) {
+      Case cs;
+      for (size_t q = 0; q < ids.size(); q++) cs.lits.push_back({ids[q], ((asg >> q) & 1) != 0});
+      RPoly sum;
+      for (auto &t : done) {
+        bool ok = true;
+        for (auto &l : t.lits) {
+          size_t q = std::find(ids.begin(), ids.end(), l.first) - ids.begin();
+          if ((((asg >> q) & 1) != 0) != l.second) { ok = false; break; }
+        }
+        if (ok) sum = rp_add(sum, t.f, 1);
+      }
+      for (auto &kv : sum.num) {
+        if (kv.first.size() > (size_t)pmt::MAX_DEGREE) fail(E_UNSUP, "count polynomial degree above 4");
+        Mono mo = {0xFF, 0xFF, 0xFF, 0xFF};
+        for (size_t q = 0; q < kv.first.size(); q++) mo[q] = kv.first[q];
+        cs.val[mo] = kv.second;
+      }
+      cs.den = sum.den;
+      cs.bound = cs.val.empty() ? 0 : bound;
+      out.push_back(cs);
+    }
+    return out;
+  }
+};
 
 // ----------------------------------------------------------------------------------- keys and layouts
 
@@ -979,11 +1376,53 @@ static std::vector<Case> stmt_count(Compiler &C, const Stmt &st) {
     lo[j] = C.to_qaff(K.dims[st.dims[j]].lo);
     hi[j] = C.to_qaff(K.dims[st.dims[j]].hi);
   }
+  // Composite axes that a coupling guard cuts through (it weighs their indices unlike
+  // the axis' own guards, as jt <= g against 64 g + l < n) are split into their indices.
+  std::set<uint32_t> split;
+  for (;;) {
   std::vector<int> owner(nd, -1);  // -1 free, -2 single, >=0 composite
   std::vector<std::vector<QAff>> sU(nd), sL(nd);
   std::vector<Case> acc = {Case{{}, Poly{{Mono{0xFF, 0xFF, 0xFF, 0xFF}, 1}}, 1}};
   struct Comp { uint32_t mask; std::vector<int> ord; std::vector<i128> ref; QAff N, J0; std::vector<QAff> U, L; };
   std::vector<Comp> comps;
+  struct Coupling { std::vector<i128> coef; QAff e; };
+  std::vector<Coupling> coupled;   // guards left to the coupled-domain counter
+  std::vector<Coupling> multi;     // every guard on two or more indices
+  // A composite axis: indices in mixed radix, sorted by (|coef|, range); all but the top
+  // one need a constant range [0, R).  The axis index j = J - J0 runs over [0, N), where
+  // J = sum_d (|coef_d| / |coef_min|) x_d.  Returns false if the indices do not qualify.
+  auto open_comp = [&](uint32_t mask, const std::vector<int> &slots, const std::vector<i128> &coef) {
+    if (split.count(mask)) return false;
+    Comp cp;
+    cp.mask = mask;
+    cp.ref = coef;
+    std::vector<std::pair<std::pair<i128, i128>, int>> key;
+    for (int j : slots) {
+      QAff r = q_add(hi[j], lo[j], -1);
+      i128 rv = r.is_const() ? r.c : (i128(1) << 100);
+      key.push_back({{coef[j] < 0 ? -coef[j] : coef[j], rv}, j});
+    }
+    std::sort(key.begin(), key.end());
+    for (auto &kv : key) cp.ord.push_back(kv.second);
+    i128 sg = coef[cp.ord[0]] > 0 ? 1 : -1;
+    for (int j : cp.ord) if ((coef[j] > 0 ? 1 : -1) != sg) return false;
+    i128 a1 = coef[cp.ord[0]] * sg;
+    i128 Nc = 1;
+    for (size_t q = 0; q + 1 < cp.ord.size(); q++) {
+      int j = cp.ord[q];
+      if (!lo[j].is_const() || !hi[j].is_const() || lo[j].c != 0) return false;
+      i128 R = hi[j].c;
+      if (coef[cp.ord[q + 1]] * sg != coef[j] * sg * R) return false;
+      Nc *= R;
+    }
+    int top = cp.ord.back();
+    cp.N = q_scale(q_add(hi[top], lo[top], -1), Nc);
+    cp.J0 = q_scale(lo[top], coef[top] * sg / a1);
+    cp.U.push_back(cp.N);
+    cp.L.push_back(q_const(0));
+    comps.push_back(cp);
+    return true;
+  };
   for (auto &g : st.guards) {
     Aff a = to_aff(K, g.expr);
     std::vector<int> slots;
@@ -1020,58 +1459,30 @@ static std::vector<Case> stmt_count(Compiler &C, const Stmt &st) {
       }
       continue;
     }
+    multi.push_back({coef, eq});
     uint32_t mask = 0;
     for (int j : slots) mask |= 1u << j;
     int gi = -1;
     for (size_t q = 0; q < comps.size(); q++) if (comps[q].mask == mask) gi = (int)q;
-    for (int j : slots) {
-      if (owner[j] == -2) fail(E_UNSUP, "index bounded alone and inside a composite axis");
-      if (owner[j] >= 0 && owner[j] != (gi < 0 ? (int)comps.size() : gi))
-        fail(E_UNSUP, "index shared by two composite axes (coupled guards)");
-    }
+    bool couple = false;
     if (gi < 0) {
-      Comp cp;
-      cp.mask = mask;
-      cp.ref = coef;
-      cp.ord = slots;
-      // mixed radix: sort by (|coef|, range); all but the top need constant [0, R)
-      for (int j : slots) {
-        if (j == -1) continue;
+      for (int j : slots) couple = couple || owner[j] != -1;
+      if (!couple && open_comp(mask, slots, coef)) {
+        gi = (int)comps.size() - 1;
+        for (int j : slots) owner[j] = gi;
+      } else {
+        couple = true;
       }
-      std::vector<std::pair<std::pair<i128, i128>, int>> key;
-      for (int j : slots) {
-        QAff r = q_add(hi[j], lo[j], -1);
-        i128 rv = r.is_const() ? r.c : (i128(1) << 100);
-        key.push_back({{coef[j] < 0 ? -coef[j] : coef[j], rv}, j});
-      }
-      std::sort(key.begin(), key.end());
-      cp.ord.clear();
-      for (auto &kv : key) cp.ord.push_back(kv.second);
-      i128 sg = coef[cp.ord[0]] > 0 ? 1 : -1;
-      for (int j : cp.ord) if ((coef[j] > 0 ? 1 : -1) != sg) fail(E_UNSUP, "composite axis with mixed signs");
-      i128 a1 = coef[cp.ord[0]] * sg;
-      i128 Nc = 1;
-      for (size_t q = 0; q + 1 < cp.ord.size(); q++) {
-        int j = cp.ord[q];
-        if (!lo[j].is_const() || !hi[j].is_const() || lo[j].c != 0)
-          fail(E_UNSUP, "inner index of a composite axis needs a constant range [0, R)");
-        i128 R = hi[j].c;
-        if (coef[cp.ord[q + 1]] * sg != coef[j] * sg * R) fail(E_UNSUP, "guard indices are not in mixed radix");
-        Nc *= R;
-      }
-      int top = cp.ord.back();
-      cp.N = q_scale(q_add(hi[top], lo[top], -1), Nc);
-      cp.J0 = q_scale(lo[top], coef[top] * sg / a1);
-      cp.U.push_back(cp.N);
-      cp.L.push_back(q_const(0));
-      gi = (int)comps.size();
-      comps.push_back(cp);
-      for (int j : slots) owner[j] = gi;
+    } else {
+      int j1 = comps[gi].ord[0];
+      for (int j : slots) couple = couple || coef[j] * comps[gi].ref[j1] != comps[gi].ref[j] * coef[j1];
+    }
+    if (couple) {
+      coupled.push_back({coef, eq});
+      continue;
     }
     Comp &cp = comps[gi];
     int j1 = cp.ord[0];
-    for (int j : slots)
-      if (coef[j] * cp.ref[j1] != cp.ref[j] * coef[j1]) fail(E_UNSUP, "guards on one composite axis are not parallel");
     i128 c1 = coef[j1];
     if (c1 > 0) {  // j >= ceil(-e/c1) - J0
       Aff num = aff_scale(e, -1);
@@ -1081,16 +1492,156 @@ static std::vector<Case> stmt_count(Compiler &C, const Stmt &st) {
       cp.U.push_back(q_add(q_add(C.floor_of(e, -c1), cp.J0, -1), q_const(1), 1));
     }
   }
+  // variables: the indices outside composite axes, then the composite axes
+  std::vector<int> var_of(nd, -1), var_dim, var_comp, var_depth;
+  for (size_t j = 0; j < nd; j++)
+    if (owner[j] < 0) {
+      var_of[j] = (int)var_dim.size();
+      var_dim.push_back((int)j);
+      var_comp.push_back(-1);
+      var_depth.push_back((int)j);
+    }
+  for (size_t q = 0; q < comps.size(); q++) {
+    int v = (int)var_dim.size(), dmax = 0;
+    for (int j : comps[q].ord) { var_of[j] = v; dmax = std::max(dmax, j); }
+    var_dim.push_back(-1);
+    var_comp.push_back((int)q);
+    var_depth.push_back(dmax);
+  }
+  const size_t nv = var_dim.size();
+  // A guard G that cuts a composite axis may be implied by another guard H and the index
+  // ranges (as jt <= g by 16 jt + jj <= 16 g + l): c G - H + c - 1 >= 0 over the ranges for
+  // an integer c >= 1 gives G >= (H - c + 1) / c > -1.  Such a G is dropped.
+  auto implied = [&](const Coupling &G) {
+    for (auto &H : multi) {
+      if (H.coef == G.coef && H.e == G.e) continue;
+      std::set<i128> cs = {1};
+      for (size_t j = 0; j < nd; j++)
+        if (G.coef[j] && H.coef[j] && H.coef[j] % G.coef[j] == 0 && H.coef[j] / G.coef[j] > 0)
+          cs.insert(H.coef[j] / G.coef[j]);
+      for (i128 c : cs) {
+        QAff q = q_add(q_scale(G.e, c), H.e, -1);
+        q.c += c - 1;
+        for (size_t j = 0; j < nd; j++) {
+          i128 a = c * G.coef[j] - H.coef[j];
+          if (a > 0) q = q_add(q, lo[j], a);
+          if (a < 0) q = q_add(q, q_add(hi[j], q_const(1), -1), a);
+        }
+        if (C.prove(q) == 1) return true;
+      }
+    }
+    return false;
+  };
+  // coupling guards over the variables; a composite axis enters as c1 (j + J0)
+  std::vector<Lin> glin;
+  bool redo = false;
+  for (auto &cg : coupled) {
+    Lin L;
+    L.a.assign(nv, 0);
+    L.e = cg.e;
+    bool drop = false;
+    for (size_t q = 0; q < comps.size() && !drop; q++) {
+      const Comp &cp = comps[q];
+      int j1 = cp.ord[0];
+      bool any = false;
+      for (int j : cp.ord) any = any || cg.coef[j] != 0;
+      if (!any) continue;
+      bool cut = false;
+      for (int j : cp.ord) cut = cut || cg.coef[j] * cp.ref[j1] != cp.ref[j] * cg.coef[j1];
+      if (cut && implied(cg)) { drop = true; break; }
+      if (cut) {
+        split.insert(cp.mask);
+        redo = true;
+        continue;
+      }
+      L.a[var_of[j1]] = cg.coef[j1];
+      L.e = q_add(L.e, cp.J0, cg.coef[j1]);
+    }
+    if (drop) continue;
+    for (size_t j = 0; j < nd; j++)
+      if (owner[j] < 0) L.a[var_of[j]] += cg.coef[j];
+    glin.push_back(L);
+  }
+  if (redo) continue;
+  // connected groups of coupled variables
+  std::vector<int> root(nv);
+  for (size_t v = 0; v < nv; v++) root[v] = (int)v;
+  std::function<int(int)> find = [&](int v) { return root[v] == v ? v : root[v] = find(root[v]); };
+  std::vector<char> in_coupled(nv, 0);
+  for (auto &L : glin) {
+    int first = -1;
+    for (size_t v = 0; v < nv; v++) {
+      if (!L.a[v]) continue;
+      in_coupled[v] = 1;
+      if (first < 0) first = (int)v;
+      else root[find((int)v)] = find(first);
+    }
+  }
   for (size_t j = 0; j < nd; j++) {
-    if (owner[j] >= 0) continue;
+    if (owner[j] >= 0 || in_coupled[var_of[j]]) continue;
     std::vector<QAff> U = {hi[j]}, L = {lo[j]};
     for (auto &u : sU[j]) U.push_back(u);
     for (auto &l : sL[j]) L.push_back(l);
     auto f = interval_cases(C, U, L);
     acc = case_product(acc, f);
   }
-  for (auto &cp : comps) acc = case_product(acc, interval_cases(C, cp.U, cp.L));
+  for (size_t q = 0; q < comps.size(); q++)
+    if (!in_coupled[var_of[comps[q].ord[0]]]) acc = case_product(acc, interval_cases(C, comps[q].U, comps[q].L));
+  std::vector<char> seen(nv, 0);
+  for (size_t v0 = 0; v0 < nv; v0++) {
+    if (!in_coupled[v0] || seen[find((int)v0)]) continue;
+    seen[find((int)v0)] = 1;
+    std::vector<int> gvars;
+    for (size_t v = 0; v < nv; v++)
+      if (in_coupled[v] && find((int)v) == find((int)v0)) gvars.push_back((int)v);
+    const size_t m = gvars.size();
+    std::vector<int> local(nv, -1);
+    for (size_t k = 0; k < m; k++) local[gvars[k]] = (int)k;
+    std::vector<Lin> cons;
+    i128 bound = 1;
+    auto bound_con = [&](size_t k, const QAff &b, bool lower) {  // x_k >= b, or x_k < b
+      Lin L;
+      L.a.assign(m, 0);
+      L.a[k] = lower ? 1 : -1;
+      L.e = lower ? q_scale(b, -1) : q_add(b, q_const(1), -1);
+      cons.push_back(L);
+    };
+    for (size_t k = 0; k < m; k++) {
+      const int v = gvars[k];
+      QAff ext;
+      if (var_comp[v] < 0) {
+        const int j = var_dim[v];
+        bound_con(k, lo[j], true);
+        bound_con(k, hi[j], false);
+        for (auto &l : sL[j]) bound_con(k, l, true);
+        for (auto &u : sU[j]) bound_con(k, u, false);
+        ext = q_add(hi[j], lo[j], -1);
+      } else {
+        const Comp &cp = comps[var_comp[v]];
+        for (auto &l : cp.L) bound_con(k, l, true);
+        for (auto &u : cp.U) bound_con(k, u, false);
+        ext = cp.N;
+      }
+      bound *= std::max<i128>(0, C.upper_bound(ext));
+      if (bound > (i128(1) << 100)) bound = i128(1) << 100;
+    }
+    for (auto &L : glin) {
+      bool mine = false;
+      for (size_t v = 0; v < nv; v++) mine = mine || (L.a[v] && local[v] >= 0);
+      if (!mine) continue;
+      Lin M;
+      M.a.assign(m, 0);
+      M.e = L.e;
+      for (size_t v = 0; v < nv; v++)
+        if (L.a[v]) M.a[local[v]] = L.a[v];
+      cons.push_back(M);
+    }
+    CoupledCounter cc{C, m, {}};
+    for (size_t k = 0; k < m; k++) cc.depth.push_back(var_depth[gvars[k]]);
+    acc = case_product(acc, cc.count(cons, bound));
+  }
   return acc;
+  }
 }
 
 struct Term {  // one contribution: a count (as cases) times per-column multiplicities
@@ -1178,12 +1729,21 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
   if (NC > pmt::MAX_CONDS) fail(E_UNSUP, "more than 10 piece conditions");
   int ncols = LD.k + LD.hidden;
 
-  // overflow check (C16): per column, sum of multiplicity * count bound
+  // common denominator D of the counts: the table holds D * count, the evaluators divide
+  i128 D = 1;
+  for (auto &t : terms)
+    for (auto &c : t.cases)
+      if (!c.val.empty()) D = D / gcd128(D, c.den) * c.den;
+  if (D > 4096) fail(E_UNSUP, "count denominator above 4096");
+
+  // overflow check: per column, sum of multiplicity * count bound, times D
   {
     std::vector<i128> bound(ncols, 0);
     for (auto &t : terms) {
       i128 mb = 0;
       for (auto &c : t.cases) mb = std::max(mb, c.bound);
+      if (mb > (i128(1) << 62)) fail(E_RANGE, "a count may exceed 2^62 on the box");
+      mb *= D;
       for (auto &kv : t.colmul) {
         i128 m = kv.second < 0 ? -kv.second : kv.second;
         if (mb > (i128(1) << 62) || (m && mb > ((i128(1) << 62) / m))) fail(E_RANGE, "a count may exceed 2^62 on the box");
@@ -1222,7 +1782,7 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
         if (ok) { hit = &c; break; }
       }
       if (!hit) continue;
-      for (auto &kv : t.colmul) poly_acc(cols[kv.first], hit->val, kv.second);
+      for (auto &kv : t.colmul) poly_acc(cols[kv.first], hit->val, kv.second * (D / hit->den));
     }
     auto it = piece_id.find(cols);
     int id;
@@ -1235,6 +1795,20 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
       id = it->second;
     }
     lut[asg] = (uint8_t)id;
+  }
+
+  // smallest denominator: divide out what every coefficient shares with D
+  {
+    i128 g = D;
+    for (auto &pc : pieces)
+      for (auto &poly : pc)
+        for (auto &kv : poly) g = gcd128(g, kv.second);
+    if (g > 1) {
+      for (auto &pc : pieces)
+        for (auto &poly : pc)
+          for (auto &kv : poly) kv.second /= g;
+      D /= g;
+    }
   }
 
   // values used (params always kept), atom renumbering
@@ -1378,6 +1952,16 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
   W[pmt::H_OFF_POST] = (uint32_t)W.size();
   for (auto &po : LD.post) W.push_back((uint32_t)po[0] | ((uint32_t)hold[po[1]] << 8) | ((uint32_t)hold[po[2]] << 16));
   while (W.size() % 4) W.push_back(0);  // 16-byte multiple for bulk copies
+  {  // D = 2^t d, d odd: exact division is a shift by t and a product with d^-1 mod 2^128
+    int t = 0;
+    uint64_t d = (uint64_t)D;
+    while (!(d & 1)) { d >>= 1; t++; }
+    unsigned __int128 inv = d;   // Newton: each step doubles the correct low bits (d*d = 1 mod 8)
+    for (int it = 0; it < 7; it++) inv *= 2 - (unsigned __int128)d * inv;
+    W[pmt::H_DEN] = (uint32_t)D;
+    W[pmt::H_DEN_SHIFT] = (uint32_t)t;
+    for (int i = 0; i < 4; i++) W[pmt::H_DEN_INV + i] = (uint32_t)(inv >> (32 * i));
+  }
   W[pmt::H_NENTRIES] = nentry;
   W[pmt::H_DEGREE] = degree;
   W[pmt::H_NPRODS] = (uint32_t)prods.size();

@@ -242,6 +242,14 @@ __device__ __forceinline__ bool eval_dot(const uint32_t *__restrict__ T, const i
   }
   S.lo = (uint64_t)acc[0] | ((uint64_t)acc[1] << 32);
   S.hi = (uint64_t)acc[2] | ((uint64_t)acc[3] << 32);
+  if (T[pmt::H_DEN] != 1) {   // S = D * prediction exactly: shift by t, times d^-1 mod 2^128
+    const uint32_t sh = T[pmt::H_DEN_SHIFT] & 63;
+    const uint64_t lo = sh ? (S.lo >> sh) | (S.hi << (64 - sh)) : S.lo;
+    const uint64_t hi = (uint64_t)((int64_t)S.hi >> sh);
+    const uint64_t ilo = ld64(T + pmt::H_DEN_INV), ihi = ld64(T + pmt::H_DEN_INV + 2);
+    S.lo = lo * ilo;
+    S.hi = __umul64hi(lo, ilo) + lo * ihi + hi * ilo;
+  }
   return true;
 }
 

@@ -83,6 +83,10 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
                      (uint64_t)slots[min((w >> 8) & 0xFF, (uint32_t)pmt::MAX_SLOTS - 1) * ss]);
   }
   const uint4 *en = (const uint4 *)(T + T[pmt::H_OFF_ENTRIES]) + pc.z;
+  // exact division by the table's denominator (D * count < 2^62, so no wrap before it)
+  const bool den = T[pmt::H_DEN] != 1;
+  const uint32_t den_sh = T[pmt::H_DEN_SHIFT] & 63;
+  const uint64_t den_inv = ld64(T + pmt::H_DEN_INV);
   uint64_t acc = 0;
   for (uint32_t e = 0; e < pc.w; e++) {
     const uint4 E = en[e];
@@ -90,7 +94,7 @@ __device__ __forceinline__ bool eval_table(const uint32_t *__restrict__ T, const
     const uint64_t coef = (uint64_t)E.x | ((uint64_t)E.y << 32);
     acc += coef * (uint64_t)slots[min(sl, (uint32_t)pmt::MAX_SLOTS - 1) * ss];
     if (E.z & pmt::ENTRY_LAST) {
-      const int64_t val = (int64_t)acc;
+      const int64_t val = den ? (int64_t)((uint64_t)((int64_t)acc >> den_sh) * den_inv) : (int64_t)acc;
       const uint32_t hold = (E.z >> 16) & 0xF;
       if (hold) slots[(pmt::HOLD_SLOT + hold - 1) * ss] = val;
       emit((int)(E.z & 0xFF), val);

@@ -8,7 +8,8 @@
 //   2. bits: condition j holds iff const_j + sum_t coef_jt * v[idx_jt] >= 0;
 //   3. piece = lut[bits];
 //   4. the piece's products (monomials of degree >= 2) are formed once, then each
-//      column value = sum of integer coef * (value or product) over its entries (exact int64);
+//      column value = sum of integer coef * (value or product) over its entries (exact int64),
+//      divided exactly by the table's denominator D (usually 1);
 //   5. post-ops: column = min(held value A, held value B)   (min(loads, stores)).
 // Columns that no segment names are zero.  Hidden columns (index >= k) only feed
 // post-ops.
@@ -29,8 +30,14 @@ enum Header {
   H_MAGIC = 0, H_WORDS, H_NPARAMS, H_NATOMS, H_NCONDS, H_NPIECES, H_K, H_NHIDDEN, H_NPOST,
   H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_PRODS, H_OFF_ENTRIES, H_OFF_POST,
   H_BOX_LO = 16, H_BOX_HI = 20, H_NENTRIES = 24, H_DEGREE = 25, H_NPRODS = 26, H_MAXPROD = 27,
-  HEADER_WORDS = 28
+  H_DEN = 28, H_DEN_SHIFT = 29, H_DEN_INV = 32, HEADER_WORDS = 36
 };
+
+// Denominator.  Counts over coupled domains (j < i, bands, ...) are sums of powers with
+// rational coefficients, so entries hold D * count and each column value is divided
+// exactly by D = 2^t d (d odd): shifted right by t, then multiplied by d^-1 mod 2^128
+// (H_DEN_INV, four words; its low 64 bits are d^-1 mod 2^64).  D = 1 for most kernels.
+// A column's D * count stays below 2^62.
 
 // Per-lane evaluation slots (int64): values 0..V-1 (parameters, then atoms), the
 // piece's products V..V+J-1, four slots that hold post-op inputs, and the constant 1.

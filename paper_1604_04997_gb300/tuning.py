@@ -40,15 +40,17 @@ def compile_variants(ctx: B.Context, variants: Sequence[W.Variant], lo: int, hi:
 
 
 def build(ctx: B.Context, n_variants: int = 10000, n_points: int = 4096, variant_seed: int = 2,
-          point_seed: int = 3, lo: int = W.BOX_LO, hi: int = W.BOX_HI) -> Batched:
+          point_seed: int = 3, lo: int = W.BOX_LO, hi: int = W.BOX_HI, coupled: bool = False) -> Batched:
     """The batched tuning workload: variants drawn with replacement from the tuning
-    space over the eight templates; per template n_points log-uniform points."""
-    drawn = W.draw_variants(n_variants, variant_seed)
-    groups = W.group_by_template(drawn)
-    pts = W.template_points(point_seed, n_points, lo, hi)
+    space over the eight templates (or, with coupled=True, over the coupled-domain
+    templates: triangles and bands); per template n_points log-uniform points."""
+    templates = W.COUPLED_TEMPLATES if coupled else W.TEMPLATES
+    drawn = W.draw_coupled_variants(n_variants, variant_seed) if coupled else W.draw_variants(n_variants, variant_seed)
+    groups = W.group_by_template(drawn, templates)
+    pts = W.template_points(point_seed, n_points, lo, hi, templates)
     cache: Dict = {}
     variants, tables, var_off, pt_rows, pt_off = [], [], [0], [], [0]
-    for t in W.TEMPLATES:
+    for t in templates:
         vs = [drawn[i] for i in groups[t]]
         variants += vs
         tables += compile_variants(ctx, vs, lo, hi, 32, cache)
@@ -57,7 +59,7 @@ def build(ctx: B.Context, n_variants: int = 10000, n_points: int = 4096, variant
         p[:, :pts[t].shape[1]] = pts[t]
         pt_rows.append(p)
         pt_off.append(pt_off[-1] + n_points)
-    return Batched(list(W.TEMPLATES), variants, np.array(tables, dtype=np.int32), np.array(var_off, dtype=np.int32),
+    return Batched(list(templates), variants, np.array(tables, dtype=np.int32), np.array(var_off, dtype=np.int32),
                    np.concatenate(pt_rows), np.array(pt_off, dtype=np.int64), len(cache))
 
 

@@ -8,6 +8,7 @@ import numpy as np
 H_MAGIC, H_WORDS, H_NPARAMS, H_NATOMS, H_NCONDS, H_NPIECES, H_K, H_NHIDDEN, H_NPOST = range(9)
 H_OFF_ATOMS, H_OFF_CONDS, H_OFF_LUT, H_OFF_PIECES, H_OFF_PRODS, H_OFF_ENTRIES, H_OFF_POST = range(9, 16)
 H_BOX_LO, H_BOX_HI = 16, 20
+H_DEN = 28
 
 
 def _s32(x):
@@ -35,6 +36,7 @@ class Table:
         self.k, self.hidden = w[H_K], w[H_NHIDDEN]
         self.box_lo = [_s32(w[H_BOX_LO + i]) for i in range(self.P)]
         self.box_hi = [_s32(w[H_BOX_HI + i]) for i in range(self.P)]
+        self.den = w[H_DEN]   # entries hold den * count
 
     def atoms(self):
         w, o = self.w, self.w[H_OFF_ATOMS]
@@ -120,6 +122,8 @@ class Table:
             acc += coef * slots[sl]
             if pk & (1 << 20):
                 col, h = pk & 0xFF, (pk >> 16) & 0xF
+                assert acc % self.den == 0 and abs(acc) < (1 << 62)
+                acc //= self.den
                 cols[col] = acc
                 if h:
                     hold[h - 1] = acc
@@ -155,4 +159,5 @@ def program_dot(prog, table, n):
         for q in range(n_post):
             e = prog[post_off + 8 * q: post_off + 8 * q + 8]
             S += _wide(e[:4]) * min(hold[e[4] & 3], hold[(e[4] >> 8) & 3])
-    return S
+    assert S % table.den == 0
+    return S // table.den

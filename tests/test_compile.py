@@ -103,8 +103,11 @@ def test_magic_division():
 
 
 @pytest.mark.parametrize("ir,code", [
-    # coupled guard: i + j < n is not a per-axis form
-    ("kernel c\nparam n\ndim i g0 0 n\ndim j seq 0 n\nstmt s i,j\nguard i+j < n\nflop f32 add 1\nend\n", -3),
+    # coupled guard with no index of unit coefficient: no closed-form chamber sum
+    ("kernel c\nparam n\ndim i g0 0 n\ndim j seq 0 n\nstmt s i,j\nguard 2*i+3*j < n\nflop f32 add 1\nend\n", -3),
+    # a coupled triangle whose count reaches n^4 / 24 with n up to 2^20: beyond 2^62 / D
+    ("kernel c\nparam n\ndim a g0 0 n\ndim b seq 0 n\ndim c seq 0 n\ndim d seq 0 n\n"
+     "stmt s a,b,c,d\nguard b < a\nguard c < b\nguard d < c\nflop f32 add 1000\nend\n", -4),
     ("kernel c\nparam n\ndim i g0 0 n\nstmt s i\nload a[i]\nend\n", -2),
     # n^3 * n with n up to 2^20 leaves int64
     ("kernel c\nparam n\ndim a g0 0 n\ndim b seq 0 n\ndim c seq 0 n\ndim d seq 0 n\n"
@@ -158,3 +161,87 @@ def test_probe_tables_match_oracle(ctx):
         for n in sizes:
             ref = oracle.Kernel(ir).features(np.array([n]), 32, "brute")[0]
             assert T.evaluate(list(n)) == list(ref), (small.name, n)
+
+
+# ----------------------------------------------------------------------------- coupled domains
+
+def _check_table(T, k, pts, method):
+    ref = k.features(pts, 32, method)
+    for p, f in zip(pts, ref):
+        assert T.evaluate([int(x) for x in p]) == list(f), p
+
+
+@pytest.mark.parametrize("t", W.COUPLED_TEMPLATES)
+def test_coupled_templates(ctx, t):
+    """Triangles and bands, every variant of the template on the box [1, 65536]: small
+    sizes against brute force, log-uniform points against the per-axis oracle.  The
+    counts are sums of powers over chambers, so the tables carry a denominator."""
+    P = len(W.TEMPLATE_PARAMS[t])
+    rng = np.random.default_rng(31)
+    small = np.arange(1, 34).reshape(-1, 1) if P == 1 else \
+        np.array([(a, b) for a in (1, 2, 5, 17, 33) for b in (1, 2, 9, 40)])
+    vs = [v for v in W.coupled_variants() if v.template == t]
+    for v in vs[::3] if t == "syrk" else vs:
+        ir = W.variant_ir(v)
+        tid, info = ctx.compile_counts(ir, 32, [1] * P, [65536] * P)
+        T = Table(ctx.table_image(tid))
+        assert T.den > 1 and info["n_pieces"] <= 8
+        k = oracle.Kernel(ir)
+        _check_table(T, k, small[::3] if t == "syrk" else small, "brute")
+        _check_table(T, k, W.draw_points(P, 8, int(rng.integers(1 << 30)), 1, 65536), "struct")
+
+
+_TET = """kernel tet
+param n
+array a global f32 n,n
+dim i g0 0 n
+dim j seq 0 n
+dim k seq 0 n
+stmt s i,j,k
+guard j < i
+guard k < j
+load a[i,k]
+flop f32 mul 1
+end
+"""
+
+_BLOCKED = """kernel btr
+param n
+array a global f32 n,n
+dim g g0 0 ceil(n/16)
+dim jt seq 0 ceil(n/16)
+dim l l0 0 16
+dim jj seq 0 16
+stmt s g,jt,l,jj
+guard jt <= g
+guard 16*g+l < n
+guard 16*jt+jj < n
+guard 16*jt+jj <= 16*g+l
+load a[16*g+l,16*jt+jj]
+flop f32 mul 1
+end
+"""
+
+
+def test_coupled_shapes(ctx):
+    """A three-index chain k < j < i (C(n,3) points: cubic, denominator 6), a guard with
+    a non-unit coefficient on one index (2j < i), and a blocked triangle whose tile
+    guard jt <= g is implied by the element guard (kept as one collapsed index pair)."""
+    for ir, lo, hi, pieces in ((_TET, 1, 4096, None), (_TET.replace("guard k < j", "guard 2*k < j"), 1, 4096, None),
+                               (_BLOCKED, 1, 65536, 1)):
+        tid, info = ctx.compile_counts(ir, 32, [lo], [hi])
+        T = Table(ctx.table_image(tid))
+        assert pieces is None or info["n_pieces"] == pieces
+        k = oracle.Kernel(ir)
+        _check_table(T, k, np.arange(1, 30).reshape(-1, 1), "brute")
+        _check_table(T, k, np.array([[97], [1000], [4095], [4096]] + ([[65535]] if hi > 4096 else [])), "struct")
+    T = Table(ctx.table_image(ctx.compile_counts(_TET, 32, [1], [4096])[0]))
+    assert T.den == 6 and T.evaluate([100])[4] == 100 * 99 * 98 // 6
+
+
+def test_coupled_unsupported(ctx):
+    """Guards that leave no index with unit coefficients are refused, not miscounted."""
+    ir = _TET.replace("guard j < i\nguard k < j", "guard 2*i+3*j < n")
+    with pytest.raises(B.PMError) as e:
+        ctx.compile_counts(ir, 32, [1], [4096])
+    assert e.value.code == -3

@@ -97,3 +97,13 @@ def test_program_small_box_keeps_runtime_post_ops(ctx):
     for v in W.tiny_variants() + [v for v in W.all_variants() if v.template in ("stencil", "transpose")][:6]:
         left += _check(ctx, v, 1, 96, rng, n_points=40)[0]
     assert left > 0   # and some are not
+
+
+@pytest.mark.parametrize("t", W.COUPLED_TEMPLATES)
+def test_program_coupled_denominator(ctx, t):
+    """Tables with a denominator D (coupled domains): the program's 128-bit sum is
+    D times the prediction and divides exactly."""
+    rng = np.random.default_rng(19)
+    vs = [v for v in W.coupled_variants() if v.template == t]
+    for v in [vs[i] for i in rng.choice(len(vs), 5, replace=False)]:
+        _check(ctx, v, 1, 65536, rng, n_points=16)
