@@ -41,7 +41,8 @@ typedef int32_t pm_status;
 #define PM_OK 0
 #define PM_ERR_INVALID_ARG -1
 #define PM_ERR_PARSE -2           /* malformed kernel description */
-#define PM_ERR_UNSUPPORTED -3     /* a form the per-axis counter does not cover (coupled guards ...) */
+#define PM_ERR_UNSUPPORTED -3     /* a form the counter does not cover (coupled guards without a
+                                      unit-coefficient index, degree > 4, > 10 piece conditions ...) */
 #define PM_ERR_OVERFLOW_RANGE -4  /* a count or atom could leave int64/int32 inside the declared box */
 #define PM_ERR_NOMEM -5
 #define PM_ERR_BUSY -6            /* serve: request can never fit the memory budget */
@@ -93,10 +94,12 @@ typedef struct {
  * IR (`ir`, `len` bytes, not necessarily NUL-terminated), into a table of
  * piecewise quasi-polynomials valid on the parameter box
  * param_lo[i] <= n_i <= param_hi[i] (host arrays of n_params entries).
- * Implements Alg. 1 (n_ops = sum_i |pi_i(D_i)| n_ops,i) with per-axis point
- * counting, the access categorisation of Sec. 2.1 (size, direction, amortized
- * stride fraction via the footprint of Alg. 2) and the min(loads, stores)
- * property.  The table stays resident in the context (host and device).
+ * Implements Alg. 1 (n_ops = sum_i |pi_i(D_i)| n_ops,i) with exact point counting
+ * (per-axis intervals; coupled domains such as j <= i or bands by index elimination
+ * with closed-form power sums, giving a table denominator), the access
+ * categorisation of Sec. 2.1 (size, direction, amortized stride fraction via the
+ * footprint of Alg. 2) and the min(loads, stores) property.  The table stays
+ * resident in the context (host and device).
  * Errors: PM_ERR_PARSE, PM_ERR_UNSUPPORTED, PM_ERR_OVERFLOW_RANGE, PM_ERR_INVALID_ARG. */
 pm_status pm_compile_counts(pm_ctx *ctx, const char *ir, size_t len, int32_t layout,
                             const int64_t *h_param_lo, const int64_t *h_param_hi,

@@ -3,16 +3,18 @@
 // Alg. 1 (Sec. 3.2): the count of a per-instruction property is
 //     n_ops = sum_i |pi_i(D_i)| * n_ops,i
 // where |pi_i(D_i)| is the number of integer points of instruction i's loop
-// domain.  The paper obtains |pi_i(D_i)| symbolically with isl/barvinok.  Here the
-// IR is restricted so that every domain is a box intersected with guards that
-// each bound either one loop index or one "composite axis" (indices combined in
-// mixed radix, such as x = T*g + l of a tiled axis).  The count then factors into
-// per-axis interval lengths max(0, min(U...) - max(L...)) whose bounds are
-// quasi-affine in the parameters (atoms floor((a.n+b)/c)).  Expanding the min/max
-// choices gives pieces selected by affine conditions on the atoms; conditions that
-// hold or fail everywhere on the declared parameter box are resolved at compile
-// time.  Each piece is a quasi-polynomial in the atoms, kept as exact int64
-// monomials per feature column.
+// domain.  The paper obtains |pi_i(D_i)| symbolically with isl/barvinok.  Here a
+// domain is a box intersected with guards that bound one loop index, one
+// "composite axis" (indices combined in mixed radix, such as x = T*g + l of a tiled
+// axis), or several indices at once (coupled domains: triangles, bands).  Free
+// axes contribute interval lengths max(0, min(U...) - max(L...)) whose bounds are
+// quasi-affine in the parameters (atoms floor((a.n+b)/c)); coupled groups are
+// counted by eliminating one index at a time with closed-form power sums (see
+// "coupled domains" below), whose rational coefficients share one denominator per
+// table.  Expanding the min/max choices gives pieces selected by affine conditions
+// on the atoms; conditions that hold or fail everywhere on the declared parameter
+// box are resolved at compile time.  Each piece is a quasi-polynomial in the atoms,
+// kept as exact int64 monomials per feature column.
 //
 // Access categories follow Sec. 2.1: access size (32/64/128 bit), direction and
 // the amortized stride fraction, whose denominator is the lid(0) stride and whose
