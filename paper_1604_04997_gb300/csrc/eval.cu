@@ -301,7 +301,7 @@ __device__ __forceinline__ void merge_lists(const int64_t *ks, int n, int stride
   }
 }
 
-constexpr int K2_BUF = 8;  // buffered insertion candidates per lane
+constexpr int K2_BUF = 4;  // buffered insertion candidates per lane
 
 // One CTA takes a work unit (a chunk of NW*32 points of one template, a slice of its
 // variants).  Each lane owns one point; all warps walk the slice's variants in order,
@@ -314,8 +314,11 @@ constexpr int K2_BUF = 8;  // buffered insertion candidates per lane
 // insertion path runs rarely.  A chunk split into S variant slices is finished by the
 // last of its S units (partial lists in a scratch buffer, a fence and an atomic
 // counter; no waiting).
+// Launch bounds ask for 24 / NW CTAs per SM (at most 80 registers a thread): with the
+// 37 KB of shared memory a 4-warp CTA takes, six CTAs fit, one more than the register
+// use of an unbounded build allows.
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) k_eval_predict_topk(K2Args a) {
+__global__ void __launch_bounds__(NW * 32, 24 / NW) k_eval_predict_topk(K2Args a) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t *tbuf = (uint32_t *)smem;                                  // [2][TB_WORDS]
   int64_t *slots = (int64_t *)(tbuf + 2 * TB_WORDS);                  // [NW][24 slots][32 lanes]
