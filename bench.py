@@ -475,10 +475,21 @@ def run_other(args):
         Wo = torch.empty((M, 32), dtype=torch.float64, device=dev)
         fn = lambda: ctx.fit_weights(F, T, Wo, B.FIT_RELATIVE, B.PREC_BF16X3, 3, stream=stream)
         ms, ck = _clocks_and_time(fn, args.steps, args.warmup, stream, None)
+        fn_ff = lambda: ctx.fit_weights(F, T, Wo, B.FIT_RELATIVE, B.PREC_FP64, 3, stream=stream)
+        ms_ff, _ = _clocks_and_time(fn_ff, max(2, args.steps // 2), args.warmup, stream, None)
+        peak_tc = float(_peaks().get("bf16_tflops", 1979.0))
+        gram_flops = 2.0 * 32 * 32 * R * M          # the 64 Gram matrices' useful flops
         line = dict(base, metric="weight fits/s (200,000 rows x 32 features, 64 models, 3 refinement steps)",
                     value=M / (ms / 1e3), unit="model fits/s", ms_per_step=ms, higher_is_better=True,
-                    dtype="float-float Gram, FP64 Cholesky, exact residual products",
-                    config={"workload": "200,000 x 32 int64 features, 64 device models, relative objective"},
+                    dtype="Gram exact on tcgen05 from bf16 digits (47-bit fixed point), FP64 Cholesky, "
+                          "exact residual products",
+                    config={"workload": "200,000 x 32 int64 features, 64 device models, relative objective",
+                            "float_float_gram_ms_per_step": ms_ff},
+                    roofline={"bound": "tensor", "achieved": gram_flops / (ms / 1e3) / 1e12, "peak": peak_tc,
+                              "unit": "TFLOP/s", "frac": gram_flops / (ms / 1e3) / 1e12 / peak_tc, "traffic": None,
+                              "kernel": "pm_fit_weights (whole call; the Gram kernel is a third of it)",
+                              "note": "useful Gram flops 2 k^2 R M over the whole fit; the digit split executes "
+                                      "49 digit-pair products per useful product on the tensor pipe"},
                     clocks=ck, gpu_launches=None)
     print(json.dumps(line))
     ctx.close()

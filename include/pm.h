@@ -196,8 +196,10 @@ typedef struct {
 
 /* Fit M weight vectors at once: d_F int64 [R][k], d_T fp64 [R][M] (measured
  * times > 0), d_W_out fp64 [M][k], h_report [M] (host).  Each column of F is
- * scaled by a power of two; Gram products A^T A use split products with FP32
- * accumulation (precision PM_PREC_BF16X3) or compensated FP32 (PM_PREC_FP64);
+ * scaled by a power of two; the Gram matrices A^T A are formed exactly from a 47-bit
+ * fixed-point image of A split into seven bf16 digits, on the tensor cores with FP32
+ * accumulation that stays exact (precision PM_PREC_BF16X3), or with float-float
+ * products and compensated FP32 sums (PM_PREC_FP64; about 2^-44 relative);
  * the k x k systems are solved by FP64 Cholesky and refined with FP64 residuals
  * (refine_steps, e.g. 3).  Synchronises `stream` to fill h_report.
  * Returns PM_OK or PM_WARN_RANK_DEFICIENT. */

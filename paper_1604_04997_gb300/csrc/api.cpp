@@ -317,7 +317,7 @@ extern "C" pm_status pm_fit_weights(pm_ctx *c, const int64_t *F, int64_t R, int3
   h.rr = h.upd + 64;
   h.bb = h.rr + 64;
   cudaStream_t st = (cudaStream_t)stream;
-  CU(pmd::launch_fit(F, R, k, T, M, objective, refine_steps, scr, W_out, &h, c->d_status, st));
+  CU(pmd::launch_fit(F, R, k, T, M, objective, precision, refine_steps, scr, W_out, &h, c->d_status, st));
   CU(cudaStreamSynchronize(st));
   s = pm_sync_status(c, stream);
   if (s) return s;

@@ -6,7 +6,8 @@
 // [1/2, 1).  The normal equations A^T A x = A^T b (b = 1, or b = t_m) are formed
 // in float-float arithmetic on the FP32 pipes (entries split exactly into hi + lo
 // pairs, error-free products by FMA, compensated sums; about 2^-44 relative) per row
-// chunk, chunks summed in FP64;
+// chunk, chunks summed in FP64 (precision PM_PREC_FP64), or exactly on the tensor
+// cores from bf16 digits of a 47-bit fixed-point image of A (PM_PREC_BF16X3, gram_tc.cu);
 // the k x k systems are factored by FP64 Cholesky.  Iterative refinement then
 // recovers the accuracy: r = b - A x is formed from the exact fixed-point product
 // F w (the prediction kernel's arithmetic) and an FP64 division, the correction
@@ -421,8 +422,8 @@ static char *carve(char *&p, size_t bytes) {
   return r;
 }
 
-cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int steps,
-                       void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st) {
+cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int precision,
+                       int steps, void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st) {
   char *p = (char *)scratch;
   unsigned long long *cmax = (unsigned long long *)carve(p, 256);
   unsigned *amax = (unsigned *)carve(p, (size_t)M * FIT_MAXK * 4);
@@ -457,11 +458,19 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / std::max(1, M) + 1, (R + 255) / 256));
   const int64_t rpc = (R + chunks - 1) / chunks;
   k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, rf, R, k, M, rpc, amax);
-  k_gram<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Ul, rf, bt, R, k, M, rpc, amax, G, rhs);
-  k_chol_solve<<<M, 32, 0, st>>>(G, rhs, k, M, cmax, x, info, ratio);
   const int groups = (M + ATQ_MODELS - 1) / ATQ_MODELS;
   const int achunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / groups + 1, (R + 255) / 256));
   const int64_t arpc = (R + achunks - 1) / achunks;
+  if (precision == PM_PREC_BF16X3) {
+    // Gram on the tensor cores (exact digits of the 47-bit fixed-point A); right-hand
+    // side A^T b = U^T (rowfactor b) with the float-float product kernel
+    if ((e = launch_gram_tc(U, Ul, rf, R, k, M, amax, G, status, st)) != cudaSuccess) return e;
+    k_atq<<<dim3(achunks, groups), FIT_THREADS, 0, st>>>(U, Ul, objective == PM_FIT_RELATIVE ? rf : bt, R, k, M,
+                                                         arpc, amax, rhs);
+  } else {
+    k_gram<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, Ul, rf, bt, R, k, M, rpc, amax, G, rhs);
+  }
+  k_chol_solve<<<M, 32, 0, st>>>(G, rhs, k, M, cmax, x, info, ratio);
   for (int it = 0; it < steps; it++) {
     k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
     if ((e = launch_predict(F, R, k, W_out, M, PM_PREC_FP64, P, st)) != cudaSuccess) return e;

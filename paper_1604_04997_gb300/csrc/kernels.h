@@ -91,7 +91,10 @@ struct FitHost {            // pinned host buffers filled by the fit (per model)
   double *ratio, *upd, *rr, *bb;
 };
 size_t fit_scratch_bytes(int64_t R, int k, int M);
-cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int steps,
-                       void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st);
+cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int precision,
+                       int steps, void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st);
+// exact tensor-core Gram matrices of the fit (adds into G, upper triangle, [M][32][32])
+cudaError_t launch_gram_tc(const float *Uh, const float *Ul, const float2 *rf, int64_t R, int k, int M,
+                           const unsigned *amax, double *G, int *status, cudaStream_t st);
 
 }  // namespace pmd

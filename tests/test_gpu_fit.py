@@ -19,12 +19,14 @@ def env():
     ctx.close()
 
 
-def _fit(ctx, dev, F, T, objective=B.FIT_RELATIVE, steps=3):
+def _fit(ctx, dev, F, T, objective=B.FIT_RELATIVE, steps=3, precision=None):
+    """precision PREC_BF16X3 (default): Gram matrices on the tensor cores from exact
+    digits; PREC_FP64: float-float Gram on the FP32 pipes."""
     import torch
     M = T.shape[1]
     Wd = torch.empty((M, F.shape[1]), dtype=torch.float64, device=dev)
     rc, rep = ctx.fit_weights(torch.from_numpy(F).to(dev), torch.from_numpy(np.ascontiguousarray(T)).to(dev), Wd,
-                              objective, B.PREC_BF16X3, steps)
+                              objective, B.PREC_BF16X3 if precision is None else precision, steps)
     return rc, rep, Wd.cpu().numpy()
 
 
@@ -36,13 +38,15 @@ def _scaled_err(F, T, m, w, wref, objective):
     return np.linalg.norm((w - wref) * sc) / np.linalg.norm(wref * sc)
 
 
+@pytest.mark.parametrize("precision", ["bf16x3", "fp64"])
 @pytest.mark.parametrize("objective", ["relative", "absolute"])
-def test_fit_matches_qr(env, objective):
+def test_fit_matches_qr(env, objective, precision):
     ctx, dev = env
     F = W.fit_features(20000, 32, 5)
     wt = W.draw_weights(32, 6, 6)
     T = W.synth_timings(F, wt, 6)
-    rc, rep, Wg = _fit(ctx, dev, F, T, B.FIT_RELATIVE if objective == "relative" else B.FIT_ABSOLUTE)
+    rc, rep, Wg = _fit(ctx, dev, F, T, B.FIT_RELATIVE if objective == "relative" else B.FIT_ABSOLUTE,
+                       precision=B.PREC_BF16X3 if precision == "bf16x3" else B.PREC_FP64)
     assert rc == 0
     for m in range(6):
         wref, rank, cond, res = oracle.fit(F, T[:, m], objective)
@@ -130,3 +134,24 @@ def test_fit_full_size_sampled_models(env):
     for m in (0, 9, 21, 33, 40, 51, 60, 63):
         wref, rank, cond, res = oracle.fit(F, T[:, m], "relative")
         assert _scaled_err(F, T, m, Wg[m], wref, "relative") <= 1e-8
+
+
+@pytest.mark.parametrize("R", [1, 63, 4097, 8192 + 130])
+def test_fit_tensor_gram_ragged_rows_and_k12(env, R):
+    """Row counts off the 64-row stages and 4096-row chunks (including a single row
+    and fewer rows than columns), and a 12-column problem: the tensor-core Gram and
+    the float-float Gram give the same fit (both refined against the exact residual)."""
+    ctx, dev = env
+    for k in (32, 12):
+        F = W.fit_features(max(R, 40), 32, 20 + R)[:R, :k].copy()
+        F[:, 0] += 1                                    # no all-zero row
+        T = W.synth_timings(F, W.draw_weights(k, 3, 21), 22)
+        rc1, rep1, W1 = _fit(ctx, dev, F, T, precision=B.PREC_BF16X3)
+        rc2, rep2, W2 = _fit(ctx, dev, F, T, precision=B.PREC_FP64)
+        if R >= k:
+            assert rc1 == rc2
+        for m in range(3):
+            if R >= k:
+                assert rep1[m]["rank"] == rep2[m]["rank"]
+            p1, p2 = oracle.predict(F, W1[m][None])[:, 0], oracle.predict(F, W2[m][None])[:, 0]
+            assert np.allclose(p1, p2, rtol=1e-7, atol=0), (k, m)
