@@ -59,9 +59,9 @@ __global__ void __launch_bounds__(K1_THREADS) k_eval_counts(const uint32_t *__re
   const int64_t nvalid = min((int64_t)K1_THREADS, n_points - p0);
   int64_t *dst = out + ((int64_t)blockIdx.y * n_points + p0) * K;
   const int total = (int)nvalid * K;
-  for (int i = tid; i < total; i += K1_THREADS) {
+  for (int i = tid; i < total; i += K1_THREADS) {   // streaming stores: the rows are not reread
     int r = i / K, c = i - r * K;
-    dst[i] = stage[r * (K + 1) + c];
+    __stcs(dst + i, stage[r * (K + 1) + c]);
   }
 }
 
