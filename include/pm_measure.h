@@ -4,7 +4,7 @@
  * The weights of T = sum_i alpha_i p_i(n) are fitted per device from timings of
  * "measurement kernels" chosen to exercise the counted properties (Sec. 4.1), timed
  * as in Sec. 4.2 (repeated runs, the first few dropped, the minimum kept), and the
- * model is then judged on held-out "test kernels" (Sec. 5).  Each configuration
+ * model is then evaluated on held-out "test kernels" (Sec. 5).  Each configuration
  * here has an IR description (paper_1604_04997_gb300.workloads.probe_ir) whose
  * loads, stores, flops, barriers and work-group counts are exactly what the CUDA
  * kernel performs per work-item.

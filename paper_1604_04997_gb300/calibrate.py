@@ -1,4 +1,4 @@
-"""Fit the run-time model to this GPU and judge it on held-out kernels (Sec. 4, Sec. 5).
+"""Fit the run-time model to this GPU and evaluate it on held-out kernels (Sec. 4, Sec. 5).
 
 Measurement kernels (Sec. 4.1) exercise the counted properties: streaming copies and
 sums, strided and filled-stride accesses, transposes, tiled and naive matrix
