@@ -301,6 +301,7 @@ def run_ours(args):
     max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_ops = sms * 128 * max_mhz * 1e6           # lane-instruction issue rate at the maximum clock
     achieved = evals * info["work_per_eval"] / (ms / 1e3)
+    measured_ops = B.pmm_int_issue_rate()          # integer multiply-add / xor / add chains, every lane
     traffic = _profile_traffic("eval_predict_topk_coupled_10000x4096.md" if coupled else
                                "eval_predict_topk_batched_10000x4096.md",
                                ("eval.cu", "eval_common.cuh", "pm_table.h", "plan.cpp"))
@@ -325,7 +326,10 @@ def run_ours(args):
                          "unit": "T lane-ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                          "kernel": "k_eval_predict_topk",
                          "ops_per_eval": info["work_per_eval"],
-                         "peak_note": f"{sms} SMs x 128 lanes x {max_mhz:.0f} MHz (issue bound, derived)"},
+                         "peak_note": f"{sms} SMs x 128 lanes x {max_mhz:.0f} MHz (issue bound, derived)",
+                         "measured_peak": measured_ops / 1e12, "frac_of_measured": achieved / measured_ops,
+                         "measured_peak_note": "integer issue-rate probe (pmm_int_issue_rate): independent "
+                                               "32-bit multiply-add, xor and add chains in every lane"},
             "clocks": ck,
         }
         if not args.no_cpu_baseline:

@@ -68,6 +68,14 @@ typedef struct {
 pm_status pmm_time(const pmm_config *cfg, int32_t runs, int32_t skip, double *h_min_ms, double *h_mean_ms,
                    void *stream);
 
+/* Integer issue rate of this GPU, the denominator's counterpart for integer-bound
+ * kernels: every lane of a fully occupied grid advances independent chains of 32-bit
+ * multiply-add, xor and add (the instruction mix of the counting and ranking kernels);
+ * the best of five CUDA-event timings gives lane operations (PTX instructions) per
+ * second in *h_lane_ops_per_s.  Synchronises `stream`.  PM_OK, PM_ERR_INVALID_ARG,
+ * PM_ERR_NOMEM or PM_ERR_CUDA. */
+pm_status pmm_int_issue_rate(double *h_lane_ops_per_s, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,7 @@ def lib():
             "pm_serve_stop": ([vp], i32),
             "pmm_time": ([ctypes.POINTER(PmmConfig), i32, i32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), vp], i32),
+            "pmm_int_issue_rate": ([ctypes.POINTER(ctypes.c_double), vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -117,7 +118,7 @@ def exported_symbols() -> Sequence[str]:
             "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
             "pm_eval_predict_topk", "pm_tune",
             "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
-            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time")
+            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time", "pmm_int_issue_rate")
 
 
 def _check(rc: int, ok=(PM_OK,)) -> int:
@@ -265,6 +266,13 @@ def pmm_time(kind: str, variant: int = 0, k: int = 0, gx: int = 256, gy: int = 1
     mn, me = ctypes.c_double(), ctypes.c_double()
     _check(lib().pmm_time(ctypes.byref(cfg), runs, skip, ctypes.byref(mn), ctypes.byref(me), _stream(stream)))
     return mn.value, me.value
+
+
+def pmm_int_issue_rate(stream=None) -> float:
+    """Measured integer issue rate of the current GPU (lane operations per second)."""
+    v = ctypes.c_double()
+    _check(lib().pmm_int_issue_rate(ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def make_query(model: int, topk: int, tables: np.ndarray, points: np.ndarray, top_idx: np.ndarray,

@@ -54,3 +54,15 @@ def test_quick_calibration(ctx):
             assert sorted(row["predicted_order"]) == list(range(len(row["candidates"])))
             assert row["top1_slowdown"] >= 0 and row["top2_slowdown"] <= row["top1_slowdown"]
             assert row["predicted_s"] == sorted(row["predicted_s"])
+
+
+def test_integer_issue_rate_probe():
+    """The integer issue-rate probe: positive, below the derived bound of 128 lane
+    operations per SM per clock at the maximum clock, and repeatable."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    props = torch.cuda.get_device_properties(0)
+    bound = props.multi_processor_count * 128 * 2.2e9
+    a, b = B.pmm_int_issue_rate(), B.pmm_int_issue_rate()
+    assert 0.05 * bound < a <= bound and abs(a - b) <= 0.1 * a
