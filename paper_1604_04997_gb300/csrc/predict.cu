@@ -46,32 +46,55 @@ __device__ void load_rows(PredictSmem &S, const int64_t *F, int64_t r0, int64_t 
   }
 }
 
-// signed 64 x signed 64 -> 128-bit accumulate
-__device__ __forceinline__ void acc_add_signed(Acc128 &a, int64_t v, int64_t W) {
-  const uint64_t x = (uint64_t)v, w = (uint64_t)W;
-  const uint64_t plo = x * w;
-  const uint64_t phi = __umul64hi(x, w) - (W < 0 ? x : 0ull) - (v < 0 ? w : 0ull);
-  const uint64_t nl = a.lo + plo;
-  a.hi += phi + (nl < plo ? 1ull : 0ull);
-  a.lo = nl;
+// A += v W (mod 2^128), v and W signed 64-bit, A four 32-bit limbs: the unsigned
+// product from three carry chains of 32-bit multiply-adds (limb products v0 W0, v0 W1,
+// v1 W0, v1 W1), then the corrections of the signed operands (v = v_u - 2^64 when
+// negative, likewise W), which subtract the other operand from the upper 64 bits.
+__device__ __forceinline__ void acc_mad(uint32_t (&A)[4], int64_t v, int64_t W) {
+  const uint32_t v0 = (uint32_t)v, v1 = (uint32_t)((uint64_t)v >> 32);
+  const uint32_t w0 = (uint32_t)W, w1 = (uint32_t)((uint64_t)W >> 32);
+  asm("mad.lo.cc.u32  %0, %4, %6, %0;\n\t"
+      "madc.lo.cc.u32 %1, %4, %7, %1;\n\t"
+      "madc.lo.cc.u32 %2, %5, %7, %2;\n\t"
+      "madc.hi.u32    %3, %5, %7, %3;\n\t"
+      "mad.hi.cc.u32  %1, %4, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %4, %7, %2;\n\t"
+      "addc.u32       %3, %3, 0;\n\t"
+      "mad.lo.cc.u32  %1, %5, %6, %1;\n\t"
+      "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+      "addc.u32       %3, %3, 0;\n\t"
+      : "+r"(A[0]), "+r"(A[1]), "+r"(A[2]), "+r"(A[3])
+      : "r"(v0), "r"(v1), "r"(w0), "r"(w1));
+  if (v < 0) asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %3;\n\t" : "+r"(A[2]), "+r"(A[3]) : "r"(w0), "r"(w1));
+  if (W < 0) asm("sub.cc.u32 %0, %0, %2;\n\tsubc.u32 %1, %1, %3;\n\t" : "+r"(A[2]), "+r"(A[3]) : "r"(v0), "r"(v1));
 }
 
 // Each thread: rows warp + 8 q (q < 4), models lane + 32 j (j < 2).
 __device__ __forceinline__ void tile_fixed(const PredictSmem &S, int k, Acc128 acc[4][2]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t a[4][2][4];
 #pragma unroll
   for (int q = 0; q < 4; q++)
 #pragma unroll
-    for (int j = 0; j < 2; j++) acc[q][j].zero();
+    for (int j = 0; j < 2; j++)
+#pragma unroll
+      for (int l = 0; l < 4; l++) a[q][j][l] = 0;
   for (int i = 0; i < k; i++) {
     const int64_t w0 = S.w[i][lane], w1 = S.w[i][lane + 32];
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       const int64_t v = S.f[warp + 8 * q][i];
-      acc_add_signed(acc[q][0], v, w0);
-      acc_add_signed(acc[q][1], v, w1);
+      acc_mad(a[q][0], v, w0);
+      acc_mad(a[q][1], v, w1);
     }
   }
+#pragma unroll
+  for (int q = 0; q < 4; q++)
+#pragma unroll
+    for (int j = 0; j < 2; j++) {
+      acc[q][j].lo = (uint64_t)a[q][j][0] | ((uint64_t)a[q][j][1] << 32);
+      acc[q][j].hi = (uint64_t)a[q][j][2] | ((uint64_t)a[q][j][3] << 32);
+    }
 }
 
 __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_ff(const int64_t *__restrict__ F, int64_t R, int k,
