@@ -245,3 +245,18 @@ def test_coupled_unsupported(ctx):
     with pytest.raises(B.PMError) as e:
         ctx.compile_counts(ir, 32, [1], [4096])
     assert e.value.code == -3
+
+
+def test_coupled_layout12(ctx):
+    """The 12-column layout of coupled-domain tables (denominator included) against the
+    oracle's 12-column features."""
+    for t in W.COUPLED_TEMPLATES:
+        v = [v for v in W.coupled_variants() if v.template == t][5]
+        ir = W.variant_ir(v)
+        P = len(W.TEMPLATE_PARAMS[t])
+        tid, _ = ctx.compile_counts(ir, 12, [1] * P, [65536] * P)
+        T = Table(ctx.table_image(tid))
+        pts = W.draw_points(P, 10, 77, 1, 4096)
+        ref = oracle.Kernel(ir).features(pts, 12, "struct")
+        for p, f in zip(pts, ref):
+            assert T.evaluate([int(x) for x in p]) == list(f), (v.name, p)

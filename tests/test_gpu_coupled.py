@@ -112,3 +112,21 @@ def test_coupled_serve(env):
             assert np.allclose(tt[:m], times[got], rtol=1e-12, atol=0)
     finally:
         ctx.serve_stop()
+
+
+def test_coupled_counts_layout12(env):
+    """Materialised 12-column counts of coupled-domain tables (exact division by the
+    table denominator in the 12-column kernel) against the oracle."""
+    import torch
+    ctx, dev = env
+    for t in W.COUPLED_TEMPLATES:
+        vs = [v for v in W.coupled_variants() if v.template == t][::7]
+        P = len(W.TEMPLATE_PARAMS[t])
+        ids = [ctx.compile_counts(W.variant_ir(v), 12, [1] * P, [65536] * P)[0] for v in vs]
+        pts = W.draw_points(P, 130, 78, 1, 65536)
+        out = torch.full((len(ids), len(pts), 12), -7, dtype=torch.int64, device=dev)
+        ctx.eval_counts(ids, torch.from_numpy(pts).to(dev), out)
+        ctx.sync_status()
+        got = out.cpu().numpy()
+        for i, v in enumerate(vs):
+            assert np.array_equal(got[i], oracle.Kernel(W.variant_ir(v)).features(pts, 12, "struct")), v.name
