@@ -260,3 +260,32 @@ def test_coupled_layout12(ctx):
         ref = oracle.Kernel(ir).features(pts, 12, "struct")
         for p, f in zip(pts, ref):
             assert T.evaluate([int(x) for x in p]) == list(f), (v.name, p)
+
+
+def test_denominator_cancels(ctx):
+    """Two triangles j < i and j > i feeding the same columns sum to n(n-1): integer
+    coefficients, so the table's denominator reduces to 1; one triangle alone keeps 2."""
+    body = """kernel offdiag
+param n
+array a global f32 n,n
+dim i g0 0 n
+dim j seq 0 n
+stmt lo i,j
+guard j < i
+load a[i,j]
+flop f32 add 1
+end
+stmt up i,j
+guard j > i
+load a[i,j]
+flop f32 add 1
+end
+"""
+    T = Table(ctx.table_image(ctx.compile_counts(body, 32, [1], [65536])[0]))
+    assert T.den == 1
+    k = oracle.Kernel(body)
+    for n in (1, 2, 3, 100, 65536):
+        assert T.evaluate([n]) == list(k.features([[n]], 32, "struct")[0])
+        assert T.evaluate([n])[3] == n * (n - 1)
+    one = body.split("stmt up")[0]
+    assert Table(ctx.table_image(ctx.compile_counts(one, 32, [1], [65536])[0])).den == 2
