@@ -321,7 +321,7 @@ def run_ours(args):
             "e2e": {"value": evals * ws / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(bp.points.nbytes),
                     "d2h_bytes_per_step": int(n * 16 * (4 + 8))},
-            "gpu_launches": args.steps,
+            "gpu_launches": 2 * args.steps,   # per step: the weight prepass and the fused ranking kernel
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T lane-ops/s", "frac": achieved / peak_ops, "traffic": traffic,
                          "kernel": "k_eval_predict_topk",
