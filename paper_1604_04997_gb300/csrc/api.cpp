@@ -14,6 +14,7 @@
 #include "pm.h"
 #include "pm_internal.h"
 #include "pm_table.h"
+#include "trace.h"
 
 int pm_compile_table(const char *ir, size_t len, int layout, const int64_t *plo, const int64_t *phi,
                      std::vector<uint32_t> &words, int info[8], std::string &msg);
@@ -156,6 +157,7 @@ static pm_status upload_table(pm_ctx *c, int id) {
 
 extern "C" pm_status pm_compile_counts(pm_ctx *c, const char *ir, size_t len, int32_t layout, const int64_t *lo,
                                        const int64_t *hi, int32_t *out_id, pm_table_info *info) {
+  PM_TRACE("pm_compile_counts");
   if (!c || !ir || !lo || !hi || !out_id) return pm_set_error(PM_ERR_INVALID_ARG, "null argument");
   if (layout != PM_LAYOUT_12 && layout != PM_LAYOUT_32) return pm_set_error(PM_ERR_INVALID_ARG, "layout must be 12 or 32");
   std::vector<uint32_t> words;
@@ -214,6 +216,7 @@ pm_status ctx_table_offsets(pm_ctx *c, const int32_t *ids, int n, int *P, int *K
 
 extern "C" pm_status pm_eval_counts(pm_ctx *c, const int32_t *ids, int32_t n_tables, const int64_t *d_points,
                                     int64_t n_points, int64_t *d_counts, void *stream) {
+  PM_TRACE("pm_eval_counts");
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (n_tables < 0 || n_points < 0 || (n_tables && !ids)) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
@@ -233,6 +236,7 @@ extern "C" pm_status pm_eval_counts(pm_ctx *c, const int32_t *ids, int32_t n_tab
 
 extern "C" pm_status pm_predict(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *W, int32_t M,
                                 int32_t precision, double *T, void *stream) {
+  PM_TRACE("pm_predict");
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (R < 0 || k <= 0 || M <= 0) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
@@ -248,6 +252,7 @@ extern "C" pm_status pm_predict(pm_ctx *c, const int64_t *F, int64_t R, int32_t 
 
 extern "C" pm_status pm_predict_argmin(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *W,
                                        int32_t M, int32_t precision, int64_t *arg, double *mn, void *stream) {
+  PM_TRACE("pm_predict_argmin");
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (R < 0 || k <= 0 || k > 40 || M <= 0 || M > 64) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
@@ -281,6 +286,7 @@ extern "C" pm_status pm_eval_predict_topk(pm_ctx *c, const int32_t *tables, cons
                                           int32_t n_templates, const int64_t *d_points, const int64_t *pt_off,
                                           const double *d_w, int32_t topk, int32_t *d_top_idx, double *d_top_t,
                                           void *stream) {
+  PM_TRACE("pm_eval_predict_topk");
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (n_templates <= 0 || !tables || !var_off || !pt_off || !d_points || !d_w || !d_top_idx || !d_top_t)
@@ -297,6 +303,7 @@ extern "C" pm_status pm_eval_predict_topk(pm_ctx *c, const int32_t *tables, cons
 extern "C" pm_status pm_fit_weights(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *T, int32_t M,
                                     int32_t objective, int32_t precision, int32_t refine_steps, double *W_out,
                                     pm_fit_report *rep, void *stream) {
+  PM_TRACE("pm_fit_weights");
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (R <= 0 || k <= 0 || k > 32 || M <= 0 || M > 64 || refine_steps < 0 || refine_steps > 50)

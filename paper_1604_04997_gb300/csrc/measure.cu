@@ -14,6 +14,7 @@
 #include "pm.h"
 #include "pm_internal.h"
 #include "pm_measure.h"
+#include "trace.h"
 
 namespace {
 
@@ -250,6 +251,7 @@ unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 extern "C" pm_status pmm_time(const pmm_config *cfg, int32_t runs, int32_t skip, double *h_min_ms, double *h_mean_ms,
                               void *stream) {
+  PM_TRACE("pmm_time");
   if (!cfg || !h_min_ms || !h_mean_ms) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: null argument");
   const pmm_config c = *cfg;
   if (runs <= skip || skip < 0 || runs > 1000) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_time: need 0 <= skip < runs <= 1000");
@@ -451,6 +453,7 @@ __global__ void __launch_bounds__(256) k_int_issue(uint32_t *out, int iters) {
 }  // namespace
 
 extern "C" pm_status pmm_int_issue_rate(double *h_lane_ops_per_s, void *stream) {
+  PM_TRACE("pmm_int_issue_rate");
   if (!h_lane_ops_per_s) return pm_set_error_c(PM_ERR_INVALID_ARG, "pmm_int_issue_rate: null argument");
   cudaStream_t st = (cudaStream_t)stream;
   int dev = 0, sms = 148, per_sm = 1;

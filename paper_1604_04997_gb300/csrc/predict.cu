@@ -17,6 +17,7 @@
 #include "kernels.h"
 #include "pm.h"
 #include "pm_internal.h"
+#include "trace.h"
 
 namespace pmd {
 
@@ -278,6 +279,7 @@ static std::atomic<void *> g_argmin_addr[STATIC_MAX_DEVICES];
 
 extern "C" pm_status pm_predict_argmin_static(const int64_t *d_F, int64_t R, int32_t k, const double *d_W,
                                               int32_t M, int64_t *d_arg, double *d_min, void *stream) {
+  PM_TRACE("pm_predict_argmin_static");
   using namespace pmd;
   if (R < 0 || k <= 0 || k > PR_MAXK || M <= 0 || M > PR_MAXM)
     return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: need R >= 0, 0 < k <= 40, 0 < M <= 64");

@@ -34,6 +34,7 @@
 #include "pm.h"
 #include "pm_internal.h"
 #include "pm_table.h"
+#include "trace.h"
 
 using Clock = std::chrono::steady_clock;
 
@@ -154,6 +155,7 @@ static pm_status cu_err(cudaError_t e, const char *what) {
 // the serve lock; holds ctx->mu while it reads table offsets and the arena pointer, so
 // a concurrent pm_compile_counts cannot move the arena under a launch.
 static pm_status launch_batch(ServeState *S, Batch *B) {
+  PM_TRACE("pm_serve_batch");
   pm_ctx *c = S->ctx;
   uint8_t *h = S->h_region + B->off;
   uint8_t *d = S->d_region + B->off;
@@ -354,6 +356,7 @@ extern "C" pm_status pm_serve_set_weights(pm_ctx *c, const double *h_W, int32_t 
 }
 
 extern "C" pm_status pm_serve_start(pm_ctx *c, const pm_serve_config *cfg) {
+  PM_TRACE("pm_serve_start");
   pm_status g = ctx_device_guard(c);
   if (g) return g;
   if (!cfg) return pm_set_error(PM_ERR_INVALID_ARG, "null config");
@@ -481,6 +484,7 @@ void serve_destroy(pm_ctx *c) {
 }
 
 extern "C" pm_status pm_serve_stop(pm_ctx *c) {
+  PM_TRACE("pm_serve_stop");
   if (!c) return pm_set_error(PM_ERR_INVALID_ARG, "null context");
   ServeState *S = c->serve;
   if (!S || !S->running) return PM_OK;
