@@ -105,6 +105,17 @@ pm_status pm_compile_counts(pm_ctx *ctx, const char *ir, size_t len, int32_t lay
                             const int64_t *h_param_lo, const int64_t *h_param_hi,
                             int32_t *out_table_id, pm_table_info *out_info);
 
+/* Register a table from its image (h_words, n_words 32-bit words, as pm_table_image
+ * wrote it), e.g. one saved earlier, without compiling the IR again; *out_table_id
+ * receives its id in this context.  The image is checked on the host before anything
+ * reaches the device: header limits, every section offset inside the image, condition
+ * terms, the piece table, product operands, entry slots and columns, post-op holds,
+ * the atoms' divisors and magic numbers and their int32 numerator range over the
+ * declared box, and the denominator's inverse.  PM_ERR_INVALID_ARG (with the failed
+ * check in pm_last_error) for an image that fails.  The counts are those of the
+ * compiled table the image came from. */
+pm_status pm_table_load(pm_ctx *ctx, const uint32_t *h_words, size_t n_words, int32_t *out_table_id);
+
 /* Copy the host image of a compiled table (n_words 32-bit words) into h_buf. */
 pm_status pm_table_image(pm_ctx *ctx, int32_t table_id, uint32_t *h_buf, size_t cap_words,
                          size_t *out_words);

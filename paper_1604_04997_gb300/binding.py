@@ -104,6 +104,7 @@ def lib():
             "pmm_time": ([ctypes.POINTER(PmmConfig), i32, i32, ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_double), vp], i32),
             "pmm_int_issue_rate": ([ctypes.POINTER(ctypes.c_double), vp], i32),
+            "pm_table_load": ([vp, vp, ctypes.c_size_t, ctypes.POINTER(i32)], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -118,7 +119,7 @@ def exported_symbols() -> Sequence[str]:
             "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
             "pm_eval_predict_topk", "pm_tune",
             "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
-            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time", "pmm_int_issue_rate")
+            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time", "pmm_int_issue_rate", "pm_table_load")
 
 
 def _check(rc: int, ok=(PM_OK,)) -> int:
@@ -177,6 +178,14 @@ class Context:
         _check(lib().pm_compile_counts(self.h, b, len(b), layout, lo_a.ctypes.data, hi_a.ctypes.data,
                                        ctypes.byref(tid), ctypes.byref(info)))
         return tid.value, {f: getattr(info, f) for f, _ in TableInfo._fields_}
+
+    def table_load(self, words) -> int:
+        """Register a table from its image (as table_image returns it); the image is
+        checked on the host and refused with PMError if it is not a valid table."""
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        tid = ctypes.c_int32()
+        _check(lib().pm_table_load(self.h, w.ctypes.data, w.size, ctypes.byref(tid)))
+        return tid.value
 
     def table_image(self, tid: int) -> np.ndarray:
         n = ctypes.c_size_t()

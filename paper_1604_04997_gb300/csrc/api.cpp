@@ -183,6 +183,27 @@ extern "C" pm_status pm_compile_counts(pm_ctx *c, const char *ir, size_t len, in
   return PM_OK;
 }
 
+bool pm_table_valid(const uint32_t *w, size_t n, std::string &why);   // table_check.cpp
+
+extern "C" pm_status pm_table_load(pm_ctx *c, const uint32_t *words, size_t n_words, int32_t *out_id) {
+  PM_TRACE("pm_table_load");
+  if (!c || !words || !out_id) return pm_set_error(PM_ERR_INVALID_ARG, "null argument");
+  std::string why;
+  if (!pm_table_valid(words, n_words, why)) return pm_set_error(PM_ERR_INVALID_ARG, "table image rejected: " + why);
+  std::lock_guard<std::mutex> lk(c->mu);
+  int id = (int)c->tables.size();
+  c->tables.emplace_back(words, words + n_words);
+  c->dev_off.push_back(-1);
+  if (c->device >= 0) {
+    pm_status g = ctx_device_guard(c);
+    if (g) return g;
+    pm_status u = upload_table(c, id);
+    if (u) return u;
+  }
+  *out_id = id;
+  return PM_OK;
+}
+
 extern "C" pm_status pm_table_image(pm_ctx *c, int32_t id, uint32_t *buf, size_t cap, size_t *out_words) {
   if (!c || id < 0 || id >= (int)c->tables.size()) return pm_set_error(PM_ERR_NOT_FOUND, "no such table");
   const auto &w = c->tables[id];
