@@ -446,12 +446,21 @@ def run_other(args):
         T = torch.empty((R, M), dtype=torch.float64, device=dev)
         arg = torch.empty(M, dtype=torch.int64, device=dev)
         mn = torch.empty(M, dtype=torch.float64, device=dev)
+        n_groups = 4096
+        idx16 = torch.empty(n_groups * M * 16, dtype=torch.int64, device=dev)
+        t16 = torch.empty(n_groups * M * 16, dtype=torch.float64, device=dev)
+        seg_one = np.array([0, R], dtype=np.int64)
+        seg_many = np.linspace(0, R, n_groups + 1).astype(np.int64)
         times = {}
         for name, prec, fn in (
                 ("bf16x3_T", B.PREC_BF16X3, lambda: ctx.predict(F, Wm, T, B.PREC_BF16X3, stream=stream)),
                 ("bf16x3_argmin", B.PREC_BF16X3,
                  lambda: ctx.predict_argmin(F, Wm, arg, mn, B.PREC_BF16X3, stream=stream)),
-                ("fp64_T", B.PREC_FP64, lambda: ctx.predict(F, Wm, T, B.PREC_FP64, stream=stream))):
+                ("fp64_T", B.PREC_FP64, lambda: ctx.predict(F, Wm, T, B.PREC_FP64, stream=stream)),
+                ("fp64_topk16_one_group", B.PREC_FP64,
+                 lambda: ctx.predict_topk(F, Wm, seg_one, 16, idx16, t16, stream=stream)),
+                ("fp64_topk16_4096_groups", B.PREC_FP64,
+                 lambda: ctx.predict_topk(F, Wm, seg_many, 16, idx16, t16, stream=stream))):
             times[name] = _clocks_and_time(fn, args.steps, args.warmup, stream, None)   # F, T > L2
         ms, ck = times["bf16x3_T"]
         nbytes = R * 32 * 8 + R * M * 8
@@ -463,7 +472,10 @@ def run_other(args):
                     config={"workload": "1,000,000 feature rows x 32 int64 features x 64 weight vectors",
                             "bytes_per_step": nbytes, "l2": "inputs (256 MB) and output (512 MB) larger than L2",
                             "argmin_only_ms": ms_arg, "argmin_only_gbs": nb_arg / (ms_arg / 1e3) / 1e9,
-                            "fp64_accurate_ms": times["fp64_T"][0]},
+                            "fp64_accurate_ms": times["fp64_T"][0],
+                            "fp64_accurate_top16_ms": {"one group of 1e6 rows": times["fp64_topk16_one_group"][0],
+                                                       "4096 groups of ~244 rows":
+                                                           times["fp64_topk16_4096_groups"][0]}},
                     roofline={"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                               "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
                               "traffic": _profile_traffic("predict_tc_1e6x32x64.md", ("predict_tc.cu",)),

@@ -147,6 +147,25 @@ pm_status pm_predict_argmin(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t 
                             const double *d_W, int32_t M, int32_t precision, int64_t *d_arg,
                             double *d_min, void *stream);
 
+/* Top-k rows per (group, model) over materialised features (configuration selection,
+ * Sec. 6.1: for each problem size, the variants with the smallest predicted time).
+ * Group g consists of the positions [h_seg_off[g], h_seg_off[g+1]) (h_seg_off: host,
+ * int64 [G+1], non-decreasing, h_seg_off[0] >= 0); position p names row d_rows[p]
+ * (device int64 list, e.g. the rows t * n_points + p of one point p of a
+ * [tables][points][k] counts array), or row p itself when d_rows is NULL (then
+ * h_seg_off[G] <= R).  Out: d_top_idx int64 [G][M][topk] row indices and d_top_t fp64
+ * [G][M][topk] times, ascending by (time, row); a group with fewer than topk rows
+ * fills the rest with -1 and +inf.  The times are bit for bit those pm_predict writes
+ * at PM_PREC_FP64 (the only precision accepted here); 1 <= topk <= 16, k <= 40,
+ * M <= 64.  A listed row outside [0, R) is skipped and makes pm_sync_status return
+ * PM_ERR_INVALID_ARG.  A row listed twice in a group may be returned twice.
+ * Groups of more than 1,024 positions use context scratch memory (16 bytes per
+ * (1,024 positions, model, k-entry)). */
+pm_status pm_predict_topk(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t k, const double *d_W,
+                          int32_t M, int32_t precision, const int64_t *h_seg_off, int32_t G,
+                          const int64_t *d_rows, int32_t topk, int64_t *d_top_idx, double *d_top_t,
+                          void *stream);
+
 /* Allocation-free variant of pm_predict_argmin (PM_PREC_FP64), for callers that
  * cannot allocate device memory: code running while another allocator owns the
  * GPU's memory, latency-critical loops that must not trigger cudaMalloc's implicit

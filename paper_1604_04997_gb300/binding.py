@@ -105,6 +105,7 @@ def lib():
                           ctypes.POINTER(ctypes.c_double), vp], i32),
             "pmm_int_issue_rate": ([ctypes.POINTER(ctypes.c_double), vp], i32),
             "pm_table_load": ([vp, vp, ctypes.c_size_t, ctypes.POINTER(i32)], i32),
+            "pm_predict_topk": ([vp, vp, ctypes.c_int64, i32, vp, i32, i32, vp, i32, vp, i32, vp, vp, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -119,7 +120,8 @@ def exported_symbols() -> Sequence[str]:
             "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
             "pm_eval_predict_topk", "pm_tune",
             "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
-            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time", "pmm_int_issue_rate", "pm_table_load")
+            "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time", "pmm_int_issue_rate", "pm_table_load",
+            "pm_predict_topk")
 
 
 def _check(rc: int, ok=(PM_OK,)) -> int:
@@ -210,6 +212,14 @@ class Context:
     def predict_argmin(self, F, W, arg, mn, precision: int = PREC_FP64, stream=None):
         _check(lib().pm_predict_argmin(self.h, _ptr(F), F.shape[0], F.shape[1], _ptr(W), W.shape[0], precision,
                                        _ptr(arg), _ptr(mn), _stream(stream)))
+
+    def predict_topk(self, F, W, seg_off, topk, top_idx, top_t, rows=None, precision: int = PREC_FP64, stream=None):
+        """Top-k rows per (group, model); seg_off: host int64 [G+1] group offsets into
+        rows (device int64 row list) or, with rows None, into F's rows."""
+        so = np.ascontiguousarray(seg_off, dtype=np.int64)
+        _check(lib().pm_predict_topk(self.h, _ptr(F), F.shape[0], F.shape[1], _ptr(W), W.shape[0], precision,
+                                     so.ctypes.data, so.size - 1, _ptr(rows), topk, _ptr(top_idx), _ptr(top_t),
+                                     _stream(stream)))
 
     def eval_predict_topk(self, tables, var_off, points, pt_off, w, topk, top_idx, top_t, stream=None):
         t = np.ascontiguousarray(tables, dtype=np.int32)

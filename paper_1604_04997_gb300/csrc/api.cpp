@@ -100,6 +100,7 @@ extern "C" pm_status pm_sync_status(pm_ctx *c, void *stream) {
   if (s & pmd::ST_BAD_TABLE) return pm_set_error(PM_ERR_INVALID_ARG, "malformed table reached the device");
   if (s & pmd::ST_TIMEOUT) return pm_set_error(PM_ERR_TIMEOUT, "a device wait ran out");
   if (s & pmd::ST_BAD_INPUT) return pm_set_error(PM_ERR_INVALID_ARG, "a timing is not positive and finite");
+  if (s & pmd::ST_BAD_ROW) return pm_set_error(PM_ERR_INVALID_ARG, "a listed row lies outside [0, R)");
   return PM_OK;
 }
 
@@ -284,6 +285,60 @@ extern "C" pm_status pm_predict_argmin(pm_ctx *c, const int64_t *F, int64_t R, i
   pm_status s = ctx_scratch(c, pmd::argmin_scratch_bytes(M, pmd::argmin_parts()), &scr);
   if (s) return s;
   CU(pmd::launch_predict_argmin(F, R, k, W, M, precision, scr, arg, mn, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+extern "C" pm_status pm_predict_topk(pm_ctx *c, const int64_t *F, int64_t R, int32_t k, const double *W, int32_t M,
+                                     int32_t precision, const int64_t *h_seg_off, int32_t G, const int64_t *d_rows,
+                                     int32_t topk, int64_t *d_top_idx, double *d_top_t, void *stream) {
+  PM_TRACE("pm_predict_topk");
+  pm_status g = ctx_device_guard(c);
+  if (g) return g;
+  if (R < 0 || k <= 0 || k > 40 || M <= 0 || M > 64 || G < 0 || topk < 1 || topk > pmd::TOPK_MAX)
+    return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes (need 0 < k <= 40, 0 < M <= 64, G >= 0, 1 <= topk <= 16)");
+  if (precision != PM_PREC_FP64) return pm_set_error(PM_ERR_INVALID_ARG, "pm_predict_topk supports PM_PREC_FP64");
+  if (G == 0) return PM_OK;
+  if (!h_seg_off || !W || !d_top_idx || !d_top_t || (!F && R > 0)) return pm_set_error(PM_ERR_INVALID_ARG, "null buffer");
+  if (h_seg_off[0] < 0) return pm_set_error(PM_ERR_INVALID_ARG, "group offsets must start at 0 or above");
+  for (int32_t i = 0; i < G; i++)
+    if (h_seg_off[i + 1] < h_seg_off[i]) return pm_set_error(PM_ERR_INVALID_ARG, "group offsets must be non-decreasing");
+  if (!d_rows && h_seg_off[G] > R) return pm_set_error(PM_ERR_INVALID_ARG, "without a row list the groups must lie in [0, R)");
+  // work units: groups cut into chunks of TOPK_CHUNK positions; a one-chunk group
+  // (an empty one too) is written directly, the others through partial lists
+  std::vector<pmd::TopkUnit> units;
+  std::vector<pmd::TopkMerge> merges;
+  int64_t parts = 0;
+  for (int32_t i = 0; i < G; i++) {
+    const int64_t p0 = h_seg_off[i], p1 = h_seg_off[i + 1];
+    const int64_t nch = std::max<int64_t>(1, (p1 - p0 + pmd::TOPK_CHUNK - 1) / pmd::TOPK_CHUNK);
+    if (nch == 1) {
+      units.push_back(pmd::TopkUnit{p0, p1, i, -1});
+      continue;
+    }
+    if (parts + nch > INT32_MAX) return pm_set_error(PM_ERR_INVALID_ARG, "too many rows");
+    merges.push_back(pmd::TopkMerge{i, (int32_t)parts, (int32_t)nch, 0});
+    for (int64_t q = 0; q < nch; q++)
+      units.push_back(pmd::TopkUnit{p0 + q * pmd::TOPK_CHUNK, std::min(p1, p0 + (q + 1) * pmd::TOPK_CHUNK), i,
+                                    (int32_t)(parts + q)});
+    parts += nch;
+  }
+  if (units.size() > (size_t)INT32_MAX) return pm_set_error(PM_ERR_INVALID_ARG, "too many groups");
+  const size_t ub = units.size() * sizeof(pmd::TopkUnit), mb = merges.size() * sizeof(pmd::TopkMerge);
+  std::vector<uint8_t> meta(ub + mb);
+  std::memcpy(meta.data(), units.data(), ub);
+  if (mb) std::memcpy(meta.data() + ub, merges.data(), mb);
+  void *d_meta = nullptr, *scr = nullptr;
+  pm_status s = ctx_dcopy(c, meta.data(), meta.size(), &d_meta);
+  if (s) return s;
+  const size_t pb = (size_t)parts * M * topk * sizeof(double);
+  if (parts) {
+    s = ctx_scratch(c, 2 * pb, &scr);
+    if (s) return s;
+  }
+  CU(pmd::launch_predict_topk(F, R, k, W, M, d_rows, (const pmd::TopkUnit *)d_meta, (int)units.size(),
+                              (const pmd::TopkMerge *)((uint8_t *)d_meta + ub), (int)merges.size(), topk,
+                              (double *)scr, (int64_t *)((uint8_t *)scr + pb), d_top_idx, d_top_t, c->d_status,
+                              (cudaStream_t)stream));
   return PM_OK;
 }
 

@@ -6,7 +6,7 @@
 namespace pmd {
 
 // bits of the device status word
-enum StatusBits { ST_OUT_OF_BOX = 1, ST_BAD_TABLE = 2, ST_TIMEOUT = 4, ST_BAD_INPUT = 8 };
+enum StatusBits { ST_OUT_OF_BOX = 1, ST_BAD_TABLE = 2, ST_TIMEOUT = 4, ST_BAD_INPUT = 8, ST_BAD_ROW = 16 };
 
 // K1 (eval.cu)
 cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, int n_tables, const int64_t *points,
@@ -54,6 +54,18 @@ size_t argmin_scratch_bytes(int M, int n_part);
 int argmin_parts();
 cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const double *W, int M, int precision,
                                   void *scratch, int64_t *arg, double *mn, cudaStream_t st);
+
+// top-k rows per (group, model): work units of at most TOPK_CHUNK positions of one
+// group; a group of one unit is written directly (part < 0), the partial lists of the
+// others ([part][M][topk]) are merged per group (TopkMerge)
+constexpr int TOPK_MAX = 16;
+constexpr int64_t TOPK_CHUNK = 1024;
+struct TopkUnit { int64_t p0, p1; int32_t g, part; };
+struct TopkMerge { int32_t g, part0, n_parts, pad; };
+cudaError_t launch_predict_topk(const int64_t *F, int64_t R, int k, const double *W, int M, const int64_t *rows,
+                                const TopkUnit *units, int n_units, const TopkMerge *merges, int n_merges, int topk,
+                                double *part_t, int64_t *part_r, int64_t *top_idx, double *top_t, int *status,
+                                cudaStream_t st);
 
 // predict_tc.cu (tensor cores, three-term bf16 split)
 int tc_parts(int sms);

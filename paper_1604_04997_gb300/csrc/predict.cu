@@ -263,6 +263,173 @@ cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const doub
   return launch_argmin_parts(F, R, k, W, M, scratch, argmin_parts(), arg, mn, st);
 }
 
+// ---------------------------------------------------------------- top-k rows per (group, model)
+
+// Configuration selection over materialised features (Sec. 6.1): for every group of
+// rows and every model, the topk rows with the smallest predicted time, ordered by
+// (time, row).  The times are those k_predict_ff writes, bit for bit.  A warp keeps one
+// sorted list per model it owns, entry i in lane i; a tile's 32 candidates are tested
+// against the list's last entry and only the passing ones are inserted, smallest first.
+
+constexpr double TK_INF = __builtin_huge_val();
+
+// Insert this lane's candidate (t, r), if ok, into the warp's list (lt, lr) of topk
+// entries.  Warp-uniform call; every lane returns with the merged list.  Every
+// shuffle and ballot is executed by all 32 lanes (none sits behind a short-circuit).
+__device__ __forceinline__ void warp_list_merge(double &lt, int64_t &lr, double t, int64_t r, bool ok, int topk,
+                                                int lane) {
+  constexpr unsigned FULL = 0xffffffffu;
+  double kt = __shfl_sync(FULL, lt, topk - 1);     // the list's last entry: the threshold
+  int64_t kr = __shfl_sync(FULL, lr, topk - 1);
+  bool pass = ok && arg_less(t, r, kt, kr);
+  unsigned mask = __ballot_sync(FULL, pass);
+  for (int round = 0; mask && round < 32; round++) {   // one insertion per round; the winning lane drops out
+    double bt = pass ? t : TK_INF;
+    int64_t br = pass ? r : INT64_MAX;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double ot = __shfl_xor_sync(FULL, bt, o);
+      const int64_t orr = __shfl_xor_sync(FULL, br, o);
+      if (arg_less(ot, orr, bt, br)) { bt = ot; br = orr; }
+    }
+    const int win = __ffs(__ballot_sync(FULL, pass && t == bt && r == br)) - 1;
+    const int pos = __popc(__ballot_sync(FULL, lane < topk && arg_less(lt, lr, bt, br)));   // <= topk - 1
+    const double ut = __shfl_up_sync(FULL, lt, 1);
+    const int64_t ur = __shfl_up_sync(FULL, lr, 1);
+    if (lane > pos) { lt = ut; lr = ur; }
+    else if (lane == pos) { lt = bt; lr = br; }
+    if (lane == win) pass = false;
+    kt = __shfl_sync(FULL, lt, topk - 1);
+    kr = __shfl_sync(FULL, lr, topk - 1);
+    pass = pass && arg_less(t, r, kt, kr);
+    mask = __ballot_sync(FULL, pass);
+  }
+}
+
+constexpr int TK_MODELS_PER_WARP = PR_MAXM / PR_WARPS;   // 8
+
+size_t predict_topk_smem() { return sizeof(PredictSmem) + sizeof(double) * PR_ROWS * PR_MAXM + sizeof(int64_t) * PR_ROWS; }
+
+__global__ void __launch_bounds__(PR_WARPS * 32) k_predict_topk(const int64_t *__restrict__ F, int64_t R, int k,
+                                                                const double *__restrict__ W, int M,
+                                                                const int64_t *__restrict__ rows,
+                                                                const TopkUnit *__restrict__ units, int n_units,
+                                                                int topk, double *__restrict__ part_t,
+                                                                int64_t *__restrict__ part_r,
+                                                                int64_t *__restrict__ top_idx,
+                                                                double *__restrict__ top_t, int *status) {
+  extern __shared__ __align__(16) uint8_t smem_raw[];
+  PredictSmem &S = *(PredictSmem *)smem_raw;
+  double(*tT)[PR_MAXM] = (double(*)[PR_MAXM])(smem_raw + sizeof(PredictSmem));
+  int64_t *tR = (int64_t *)(smem_raw + sizeof(PredictSmem) + sizeof(double) * PR_ROWS * PR_MAXM);
+  load_weights(S, W, M, k);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const TopkUnit U = units[u];
+    double lt[TK_MODELS_PER_WARP];
+    int64_t lr[TK_MODELS_PER_WARP];
+#pragma unroll
+    for (int j = 0; j < TK_MODELS_PER_WARP; j++) { lt[j] = TK_INF; lr[j] = INT64_MAX; }
+    for (int64_t t0 = U.p0; t0 < U.p1; t0 += PR_ROWS) {
+      __syncthreads();
+      // rows of this tile: positions t0 .. t0+31 of the unit, through the row list if any
+      for (int i = threadIdx.x; i < PR_ROWS * k; i += blockDim.x) {
+        const int r = i / k, c = i - r * k;
+        const int64_t pos = t0 + r;
+        int64_t row = -1;
+        if (pos < U.p1) {
+          row = rows ? rows[pos] : pos;
+          if (row < 0 || row >= R) {
+            if (c == 0) atomicOr(status, ST_BAD_ROW);
+            row = -1;
+          }
+        }
+        S.f[r][c] = row >= 0 ? F[row * k + c] : 0;
+        if (c == 0) tR[r] = row;
+      }
+      __syncthreads();
+      Acc128 acc[4][2];
+      tile_fixed(S, k, acc);
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+          const int m = lane + 32 * j;
+          tT[warp + 8 * q][m] = m < M ? key_value(acc_key(acc[q][j]), S.E[m]) : 0.0;
+        }
+      __syncthreads();
+      const int64_t row = tR[lane];
+#pragma unroll
+      for (int j = 0; j < TK_MODELS_PER_WARP; j++) {
+        const int m = warp + PR_WARPS * j;
+        if (m < M) warp_list_merge(lt[j], lr[j], tT[lane][m], row, row >= 0, topk, lane);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < TK_MODELS_PER_WARP; j++) {
+      const int m = warp + PR_WARPS * j;
+      if (m >= M || lane >= topk) continue;
+      if (U.part < 0) {
+        const int64_t o = ((int64_t)U.g * M + m) * topk + lane;
+        top_idx[o] = lr[j] == INT64_MAX ? -1 : lr[j];
+        top_t[o] = lt[j];
+      } else {
+        const int64_t o = ((int64_t)U.part * M + m) * topk + lane;
+        part_t[o] = lt[j];
+        part_r[o] = lr[j];
+      }
+    }
+  }
+}
+
+// Groups split over several units: one CTA per group merges the units' sorted lists.
+__global__ void __launch_bounds__(PR_WARPS * 32) k_topk_merge(const TopkMerge *__restrict__ merges, int M, int topk,
+                                                              const double *__restrict__ part_t,
+                                                              const int64_t *__restrict__ part_r,
+                                                              int64_t *__restrict__ top_idx,
+                                                              double *__restrict__ top_t) {
+  const TopkMerge G = merges[blockIdx.x];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = (int64_t)G.n_parts * topk;
+  for (int m = warp; m < M; m += PR_WARPS) {
+    double lt = TK_INF;
+    int64_t lr = INT64_MAX;
+    for (int64_t c0 = 0; c0 < n; c0 += 32) {
+      const int64_t c = c0 + lane;
+      double t = TK_INF;
+      int64_t r = INT64_MAX;
+      if (c < n) {
+        const int64_t o = (((int64_t)G.part0 + c / topk) * M + m) * topk + c % topk;
+        t = part_t[o];
+        r = part_r[o];
+      }
+      warp_list_merge(lt, lr, t, r, r != INT64_MAX, topk, lane);
+    }
+    if (lane < topk) {
+      const int64_t o = ((int64_t)G.g * M + m) * topk + lane;
+      top_idx[o] = lr == INT64_MAX ? -1 : lr;
+      top_t[o] = lt;
+    }
+  }
+}
+
+cudaError_t launch_predict_topk(const int64_t *F, int64_t R, int k, const double *W, int M, const int64_t *rows,
+                                const TopkUnit *units, int n_units, const TopkMerge *merges, int n_merges, int topk,
+                                double *part_t, int64_t *part_r, int64_t *top_idx, double *top_t, int *status,
+                                cudaStream_t st) {
+  if (k > PR_MAXK || M > PR_MAXM || topk < 1 || topk > TOPK_MAX) return cudaErrorInvalidValue;
+  if (n_units <= 0) return cudaSuccess;
+  const size_t sm = predict_topk_smem();
+  cudaFuncSetAttribute(k_predict_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int grid = std::min(n_units, num_sms() * 2);
+  k_predict_topk<<<grid, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r,
+                                                  top_idx, top_t, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || n_merges == 0) return e;
+  k_topk_merge<<<n_merges, PR_WARPS * 32, 0, st>>>(merges, M, topk, part_t, part_r, top_idx, top_t);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- allocation-free argmin
 
 // Partial results of pm_predict_argmin_static live in this fixed device array instead
