@@ -273,9 +273,22 @@ cudaError_t launch_predict_argmin(const int64_t *F, int64_t R, int k, const doub
 
 constexpr double TK_INF = __builtin_huge_val();
 
-// Insert this lane's candidate (t, r), if ok, into the warp's list (lt, lr) of topk
-// entries.  Warp-uniform call; every lane returns with the merged list.  Every
-// shuffle and ballot is executed by all 32 lanes (none sits behind a short-circuit).
+// One compare-exchange stage across lanes lane and lane ^ j: this lane keeps the
+// smaller (take_min) or the larger (t, r) pair of the two.
+__device__ __forceinline__ void lane_cmp_swap(double &t, int64_t &r, int j, bool take_min) {
+  const double ot = __shfl_xor_sync(0xffffffffu, t, j);
+  const int64_t orr = __shfl_xor_sync(0xffffffffu, r, j);
+  if (arg_less(ot, orr, t, r) == take_min) { t = ot; r = orr; }
+}
+
+// Merge this lane's candidate (t, r), if ok, into the warp's sorted list (lt, lr):
+// entry i in lane i for i < topk, (+inf, INT64_MAX) in the other lanes.  Warp-uniform
+// call; every shuffle and ballot is executed by all 32 lanes (none sits behind a
+// short-circuit or a lane-dependent branch).  Candidates not below the list's last
+// entry are dropped; one or two survivors are inserted one at a time (warp argmin,
+// then a shift), more are sorted by a bitonic network and merged in one pass (the
+// elementwise minimum of the list and the reversed candidates holds the 32 smallest
+// as a bitonic sequence, which a 5-stage bitonic merge sorts).
 __device__ __forceinline__ void warp_list_merge(double &lt, int64_t &lr, double t, int64_t r, bool ok, int topk,
                                                 int lane) {
   constexpr unsigned FULL = 0xffffffffu;
@@ -283,6 +296,20 @@ __device__ __forceinline__ void warp_list_merge(double &lt, int64_t &lr, double 
   int64_t kr = __shfl_sync(FULL, lr, topk - 1);
   bool pass = ok && arg_less(t, r, kt, kr);
   unsigned mask = __ballot_sync(FULL, pass);
+  if (__popc(mask) > 2) {
+    double ct = pass ? t : TK_INF;
+    int64_t cr = pass ? r : INT64_MAX;
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1)
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1) lane_cmp_swap(ct, cr, j, ((lane & j) == 0) == ((lane & kk) == 0));
+    const double rt = __shfl_sync(FULL, ct, 31 - lane);
+    const int64_t rr = __shfl_sync(FULL, cr, 31 - lane);
+    if (arg_less(rt, rr, lt, lr)) { lt = rt; lr = rr; }
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) lane_cmp_swap(lt, lr, j, (lane & j) == 0);
+    mask = 0;
+  }
   for (int round = 0; mask && round < 32; round++) {   // one insertion per round; the winning lane drops out
     double bt = pass ? t : TK_INF;
     int64_t br = pass ? r : INT64_MAX;
@@ -304,6 +331,7 @@ __device__ __forceinline__ void warp_list_merge(double &lt, int64_t &lr, double 
     pass = pass && arg_less(t, r, kt, kr);
     mask = __ballot_sync(FULL, pass);
   }
+  if (lane >= topk) { lt = TK_INF; lr = INT64_MAX; }
 }
 
 constexpr int TK_MODELS_PER_WARP = PR_MAXM / PR_WARPS;   // 8
