@@ -892,17 +892,23 @@ struct CoupledCounter {
         ups.push_back(b);
       }
     }
-    // drop bounds that another bound makes redundant everywhere on the chamber
+    // drop bounds that another bound makes redundant wherever the other variables may
+    // be: the proof may use only the constraints without x (those with x hold on the
+    // chamber's points, not on its projection, so a bound they dominate there can still
+    // cut the range of the other variables)
+    Chamber tr;
+    tr.lits = t.lits;
+    tr.cons = rest;
     auto prune = [&](std::vector<Lin> &v, bool upper) {
       std::vector<Lin> kept;
       for (auto &b : v) {
         bool drop = false;
         for (auto &k : kept)
-          if (k == b || nonneg(t, upper ? lin_add(b, k, -1) : lin_add(k, b, -1))) { drop = true; break; }
+          if (k == b || nonneg(tr, upper ? lin_add(b, k, -1) : lin_add(k, b, -1))) { drop = true; break; }
         if (drop) continue;
         std::vector<Lin> k2;
         for (auto &k : kept)
-          if (!nonneg(t, upper ? lin_add(k, b, -1) : lin_add(b, k, -1))) k2.push_back(k);
+          if (!nonneg(tr, upper ? lin_add(k, b, -1) : lin_add(b, k, -1))) k2.push_back(k);
         k2.push_back(b);
         kept.swap(k2);
       }
@@ -1119,6 +1125,13 @@ static void footprint(const Kernel &K, int arr, const int64_t *par, std::vector<
       if (hi[j] <= lo[j]) empty = true;
     }
     if (empty) continue;
+    // the walk below visits every point of the box: keep it bounded (the templates and
+    // the measurement kernels stay near 2^21 points at this instance)
+    i128 pts = 1;
+    for (size_t j = 0; j < nd; j++) {
+      pts *= hi[j] - lo[j];
+      if (pts > (i128(1) << 25)) fail(E_UNSUP, "statement domain too large at the classification instance");
+    }
     // guards and offsets as affine functions of the statement's dims at this instance
     std::vector<Aff> g;
     for (auto &gu : st.guards) g.push_back(to_aff(K, gu.expr));
@@ -1197,6 +1210,11 @@ static std::vector<std::vector<int>> classify(const Kernel &K) {
         if (x < size && bm[(size_t)x]) last = x;
         if (x - last < se) filled++;
       }
+      // no accessed cell (an empty domain), or a parametric stride that vanishes at
+      // the classification instance: the Sec. 2.1 fraction is undefined there
+      if (cells == 0 || filled == 0)
+        fail(E_UNSUP, "stride class undefined: the access touches no cell, or its lane stride is 0, "
+                      "with every parameter = 128");
       int c;
       if (!param && sv <= 4) {
         i128 j = (sv * cells + filled - 1) / filled;

@@ -1,0 +1,180 @@
+"""The count compiler on malformed and mutated IR, on CPU.
+
+Every input ends in a status, never a crash or a hang; every table the compiler
+accepts counts exactly what the oracle's brute-force enumeration counts.  Includes
+the inputs that once broke it: an access with no cell at the classification
+instance (a division by zero), a statement domain of ~10^13 points at that instance
+(an endless walk), and a coupled guard whose bound on one index was dropped by a
+proof that used that same index's constraints (an extra group counted).
+"""
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1604_04997_gb300 import binding as B
+from paper_1604_04997_gb300 import workloads as W
+from table_interp import Table
+
+STATUS = {-2, -3, -4}   # parse error, unsupported form, range overflow
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    c = B.Context(-1)
+    yield c
+    c.close()
+
+
+def _compile(ctx, ir, P=1, lo=1, hi=65536):
+    return ctx.compile_counts(ir, 32, [lo] * P, [hi] * P)
+
+
+def _exact_or_refused(ctx, ir, P, points):
+    try:
+        tid, _ = _compile(ctx, ir, P)
+    except B.PMError as e:
+        assert e.code in STATUS, e
+        return False
+    T = Table(ctx.table_image(tid))
+    ref = oracle.Kernel(ir).features(np.array(points), 32, "brute")
+    for p, f in zip(points, ref):
+        assert T.evaluate(list(p)) == list(f), p
+    return True
+
+
+def test_empty_footprint_is_refused(ctx):
+    ir = """kernel t
+param n
+array a global f32 n,n
+dim g g0 0 ceil(n/64)
+dim l l0 0 64
+dim jo seq 0 n
+dim ji seq 0 -21474836481
+stmt mac g,l,jo,ji
+load a[64*g+l,jo+ji]
+end
+"""
+    with pytest.raises(B.PMError) as e:
+        _compile(ctx, ir)
+    assert e.value.code == -3 and "stride class" in str(e.value)
+
+
+def test_huge_classification_domain_is_refused(ctx):
+    ir = """kernel t
+param n
+array a global f32 n,n
+dim g g0 0 ceil(n/128)
+dim l l0 0 128
+dim ti seq 0 6713769118
+stmt mac g,l,ti
+guard ti < n
+load a[128*g+l,ti]
+end
+"""
+    with pytest.raises(B.PMError) as e:
+        _compile(ctx, ir)
+    assert e.value.code == -3 and "too large" in str(e.value)
+
+
+def test_bound_dominated_only_through_its_own_index(ctx):
+    """256 g + 2 ro + l < n with ro in {0}: once counted one group too many."""
+    ir = """kernel t
+param n
+array x global f64 n
+dim g g0 0 ceil(n/256)
+dim ro seq 0 1
+dim l l0 0 256
+stmt body g,ro,l
+guard 256*g+2*ro+l < n
+load x[256*g+l]
+end
+"""
+    _exact_or_refused(ctx, ir, 1, [[n] for n in (1, 2, 3, 40, 255, 256, 257, 600)])
+
+
+def test_coupled_guard_with_unequal_tile_coefficient(ctx):
+    """Triangular matvec whose tile guard was mutated to g + l < n."""
+    ir = W.variant_ir(W.Variant("trmv", 64, 1, 8, False, 64)).replace("guard 64*g+l < n", "guard 1*g+l < n", 1)
+    assert "1*g+l" in ir
+    _exact_or_refused(ctx, ir, 1, [[n] for n in (1, 9, 38, 64, 65, 130)])
+
+
+_NUM = re.compile(r"(?<![A-Za-z_0-9])\d+")
+_OPS = ["<", "<=", ">", ">="]
+
+
+def _mutate(rng, text):
+    lines = text.split("\n")
+    for _ in range(rng.integers(1, 4)):
+        k = rng.integers(len(lines))
+        ln = lines[k]
+        r = rng.random()
+        if r < 0.6 and not ln.startswith("array"):
+            ms = list(_NUM.finditer(ln))
+            if ms:
+                m = ms[rng.integers(len(ms))]
+                v = int(rng.integers(0, 4)) if rng.random() < 0.4 else int(rng.integers(0, 40))
+                ln = ln[:m.start()] + str(v) + ln[m.end():]
+        elif r < 0.85 and ln.startswith("guard"):
+            for o in ("<=", ">=", "<", ">"):
+                if f" {o} " in ln:
+                    ln = ln.replace(f" {o} ", f" {_OPS[rng.integers(4)]} ", 1)
+                    break
+        elif ln.startswith("guard"):
+            ln = ln.replace("+", "-", 1) if rng.random() < 0.5 else ln.replace("-", "+", 1)
+        lines[k] = ln
+    return "\n".join(lines)
+
+
+def test_mutated_templates_exact_or_refused(ctx):
+    """Seeded mutations of template IR (constants, comparison operators, signs): each
+    compiles to a table equal to brute force at random small points, or is refused."""
+    rng = np.random.default_rng(2024)
+    srcs = [W.variant_ir(W.canonical(t)) for t in W.TEMPLATES]
+    srcs += [W.variant_ir(v) for v in W.coupled_variants()[::6]]
+    accepted = 0
+    for _ in range(160):
+        ir = _mutate(rng, srcs[rng.integers(len(srcs))])
+        P = len(re.search(r"^param (.*)$", ir, re.M).group(1).split())
+        pts = rng.integers(1, 41, size=(3, P)).tolist()
+        accepted += _exact_or_refused(ctx, ir, P, pts)
+    assert accepted > 60
+
+
+def test_garbled_text_always_gives_a_status(ctx):
+    """Byte-level damage (deleted spans, inserted tokens, duplicated or dropped lines,
+    huge numbers): every call returns, with a table or a status."""
+    rng = np.random.default_rng(7)
+    srcs = [W.variant_ir(W.canonical(t)) for t in W.TEMPLATES]
+    toks = ["0", "-1", "n", "i", "+", "*", "/", "<", ">=", "floor(", ")", ",", "\n", "dim", "stmt", "end", "guard",
+            "load", "param", "barrier", "x4", "1099511627776", "2147483648", "seq", "l0", "[", "]"]
+    codes = set()
+    for _ in range(400):
+        s = srcs[rng.integers(len(srcs))]
+        for _ in range(rng.integers(1, 4)):
+            op = rng.integers(5)
+            if op == 0:
+                a = rng.integers(len(s))
+                s = s[:a] + s[a + rng.integers(1, 8):]
+            elif op == 1:
+                a = rng.integers(len(s) + 1)
+                s = s[:a] + toks[rng.integers(len(toks))] + s[a:]
+            elif op == 2:
+                a = rng.integers(len(s) + 1)
+                s = s[:a] + str(int(rng.integers(-10 ** 12, 10 ** 12))) + s[a:]
+            else:
+                L = s.split("\n")
+                k = rng.integers(len(L))
+                L.insert(k, L[k]) if op == 3 else L.pop(k)
+                s = "\n".join(L)
+        try:
+            _compile(ctx, s, 4)
+            codes.add(0)
+        except B.PMError as e:
+            assert e.code in STATUS | {-1}, e
+            codes.add(e.code)
+    assert {0, -2} <= codes
