@@ -754,7 +754,7 @@ static int classify(orc_kernel *k) {
         mark_ctx mc = {A, bm[A], sz, 0};
         for (int t = 0; t < k->n_st && !err; t++) {
           i128 nin;
-          if (enumerate_stmt(k, t, p1, (int64_t)1 << 34, mark_visit, &mc, &nin) < 0) err = -2;
+          if (enumerate_stmt(k, t, p1, (int64_t)1 << 25, mark_visit, &mc, &nin) < 0) err = -2;
         }
         if (mc.bad) err = -5;
         for (i128 x = 0; x < sz; x++) cells[A] += bm[A][x];
@@ -767,6 +767,9 @@ static int classify(orc_kernel *k) {
         if (x - last < se) filled++;
       }
       i128 num = cells[A];
+      /* no accessed cell, or a lane stride of 0 at the instance: the Sec. 2.1 fraction
+         is undefined there, so the access is refused */
+      if (num == 0 || filled == 0) { err = -3; break; }
       int cls;
       if (!param && sv <= 4) {
         i128 j = (sv * num + filled - 1) / filled;

@@ -400,3 +400,19 @@ def test_table1_column_order_reading():
 def test_parser_rejects(bad):
     with pytest.raises(oracle.OracleError):
         oracle.Kernel(bad)
+
+
+def test_classification_refuses_an_access_with_no_cell():
+    """An access inside a loop that is empty at the classification instance has no
+    Sec. 2.1 stride fraction: refused (it once divided by zero)."""
+    ir = """kernel t
+param n
+array a global f32 8*n
+dim g g0 17 ceil(n/1024)
+dim l l0 0 64
+stmt body g,l
+load a[8*(64*g+l)]
+end
+"""
+    with pytest.raises(oracle.OracleError):
+        oracle.Kernel(ir).features(np.array([[40]]), 32, "brute")
