@@ -178,3 +178,29 @@ def test_garbled_text_always_gives_a_status(ctx):
             assert e.code in STATUS | {-1}, e
             codes.add(e.code)
     assert {0, -2} <= codes
+
+
+def test_injected_coupled_guards_exact_or_refused(ctx):
+    """Extra guards coupling two or three indices of a statement (coefficients in
+    -2..2, a parameter, a shifted parameter or a constant on the right) added to the
+    coupled and tiled templates: every accepted table equals brute force."""
+    rng = np.random.default_rng(41)
+    srcs = [W.variant_ir(v) for v in W.coupled_variants()[::5]]
+    srcs += [W.variant_ir(W.canonical(t)) for t in ("matmul", "stencil", "transpose")]
+    accepted = 0
+    for _ in range(90):
+        s = srcs[rng.integers(len(srcs))]
+        lines = s.split("\n")
+        params = re.search(r"^param (.*)$", s, re.M).group(1).split()
+        stmts = [(i, ln.split()[2].split(",")) for i, ln in enumerate(lines) if ln.startswith("stmt ")]
+        i, dims = stmts[rng.integers(len(stmts))]
+        if len(dims) < 2:
+            continue
+        pick = rng.choice(dims, int(rng.integers(2, min(3, len(dims)) + 1)), replace=False)
+        lhs = "+".join(f"{int(rng.choice([-2, -1, 1, 1, 2]))}*{d}" for d in pick).replace("+-", "-")
+        p = params[rng.integers(len(params))]
+        rhs = [p, f"{p}-{int(rng.integers(0, 5))}", str(int(rng.integers(0, 40))), f"2*{p}"][rng.integers(4)]
+        lines.insert(i + 1, f"guard {lhs} {_OPS[rng.integers(4)]} {rhs}")
+        ir = "\n".join(lines)
+        accepted += _exact_or_refused(ctx, ir, len(params), rng.integers(1, 33, size=(3, len(params))).tolist())
+    assert accepted > 10
