@@ -1443,6 +1443,7 @@ static std::vector<Case> stmt_count(Compiler &C, const Stmt &st) {
     comps.push_back(cp);
     return true;
   };
+  bool split_redo = false;
   for (auto &g : st.guards) {
     Aff a = to_aff(K, g.expr);
     std::vector<int> slots;
@@ -1467,7 +1468,11 @@ static std::vector<Case> stmt_count(Compiler &C, const Stmt &st) {
     }
     if (slots.size() == 1) {
       int j = slots[0];
-      if (owner[j] >= 0) fail(E_UNSUP, "index bounded alone and inside a composite axis");
+      if (owner[j] >= 0) {  // bounded alone and inside a composite axis: split the axis
+        split.insert(comps[owner[j]].mask);
+        split_redo = true;
+        break;
+      }
       owner[j] = -2;
       i128 c = coef[j];
       if (c > 0) {  // x >= ceil(-e/c)
@@ -1512,6 +1517,7 @@ static std::vector<Case> stmt_count(Compiler &C, const Stmt &st) {
       cp.U.push_back(q_add(q_add(C.floor_of(e, -c1), cp.J0, -1), q_const(1), 1));
     }
   }
+  if (split_redo) continue;
   // variables: the indices outside composite axes, then the composite axes
   std::vector<int> var_of(nd, -1), var_dim, var_comp, var_depth;
   for (size_t j = 0; j < nd; j++)

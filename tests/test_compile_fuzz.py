@@ -204,3 +204,77 @@ def test_injected_coupled_guards_exact_or_refused(ctx):
         ir = "\n".join(lines)
         accepted += _exact_or_refused(ctx, ir, len(params), rng.integers(1, 33, size=(3, len(params))).tolist())
     assert accepted > 10
+
+
+def test_lane_mask_inside_a_tiled_axis(ctx):
+    """64 g + l < n together with l < 20 (a lane mask) and l >= 3: the tiled axis is
+    split into its indices and counted by the coupled-domain counter (such kernels
+    were refused before); exact at ragged and full tiles."""
+    ir = """kernel t
+param n
+array x global f32 n
+dim g g0 0 ceil(n/64)
+dim l l0 0 64
+stmt body g,l
+guard 64*g+l < n
+guard l < 20
+guard l >= 3
+load x[64*g+l]
+flop f32 add 1
+end
+"""
+    assert _exact_or_refused(ctx, ir, 1, [[n] for n in (1, 3, 4, 19, 20, 21, 64, 65, 84, 100, 128, 1000)])
+
+
+def _random_kernel(rng):
+    P = int(rng.integers(1, 3))
+    params = ["n", "m"][:P]
+    pick = lambda: params[rng.integers(P)]
+    T = int(rng.choice([4, 8, 16]))
+    dims = [("g", "g0", "0", f"ceil({pick()}/{T})"), ("l", "l0", "0", str(T))]
+    for i in range(int(rng.integers(1, 4))):
+        hi = [pick(), str(int(rng.integers(1, 9))), f"ceil({pick()}/{int(rng.integers(2, 5))})",
+              f"{pick()}+{int(rng.integers(0, 3))}"][rng.integers(4)]
+        dims.append((f"s{i}", "seq", "0" if rng.random() < 0.8 else str(int(rng.integers(0, 3))), hi))
+    ext = "64*n+64" if P == 1 else "64*n+64*m+64"
+    lines = ["kernel r", "param " + " ".join(params), f"array a global f32 {ext}", f"array b global f32 {ext}"]
+    lines += [f"dim {d[0]} {d[1]} {d[2]} {d[3]}" for d in dims]
+    for si in range(int(rng.integers(1, 3))):
+        used = ["g", "l"] + [d[0] for d in dims[2:] if rng.random() < 0.7]
+        lines.append(f"stmt st{si} " + ",".join(used))
+        if rng.random() < 0.8:
+            lines.append(f"guard {T}*g+l < {pick()}")
+        for _ in range(int(rng.integers(0, 3))):
+            vs = rng.choice(used, int(rng.integers(1, min(3, len(used)) + 1)), replace=False)
+            lhs = "+".join(f"{int(rng.choice([-1, 1, 1, 2]))}*{v}" for v in vs).replace("+-", "-")
+            rhs = [pick(), f"{pick()}-{int(rng.integers(0, 4))}", str(int(rng.integers(0, 20))),
+                   f"{pick()}+{int(rng.integers(0, 4))}"][rng.integers(4)]
+            lines.append(f"guard {lhs} {_OPS[rng.integers(4)]} {rhs}")
+        lines.append(f"flop f32 add {int(rng.integers(1, 3))}")
+        idx = "+".join(f"{int(rng.integers(1, 3))}*{v}" for v in used)
+        lines.append(f"load a[{T}*g+l]" if rng.random() < 0.5 else f"load a[{idx}]")
+        if rng.random() < 0.5:
+            lines.append(f"store b[{T}*g+l]")
+        lines.append("end")
+    return "\n".join(lines) + "\n", P
+
+
+def test_random_kernels_exact_or_refused(ctx):
+    """Random kernels (tiled group and local axes, sequential loops with affine,
+    ceil or constant bounds, guards over one to three indices, strided accesses):
+    each accepted table equals brute force."""
+    rng = np.random.default_rng(62)
+    accepted = 0
+    for _ in range(150):
+        ir, P = _random_kernel(rng)
+        try:
+            tid, _ = ctx.compile_counts(ir, 32, [1] * P, [4096] * P)
+        except B.PMError as e:
+            assert e.code in STATUS, e
+            continue
+        accepted += 1
+        T = Table(ctx.table_image(tid))
+        pts = rng.integers(1, 25, size=(3, P))
+        for p, f in zip(pts, oracle.Kernel(ir).features(pts, 32, "brute")):
+            assert T.evaluate([int(x) for x in p]) == list(f), (ir, p)
+    assert accepted > 50
