@@ -156,6 +156,19 @@ static pm_status upload_table(pm_ctx *c, int id) {
 
 // ------------------------------------------------------------------------------------- counting
 
+// Upload the newly added table id (the last one) to the device arena; on failure the
+// table is taken back out, so that no id refers to a table without device words.
+static pm_status register_on_device(pm_ctx *c, int id) {
+  if (c->device < 0) return PM_OK;
+  pm_status s = ctx_device_guard(c);
+  if (!s) s = upload_table(c, id);
+  if (s) {
+    c->tables.pop_back();
+    c->dev_off.pop_back();
+  }
+  return s;
+}
+
 extern "C" pm_status pm_compile_counts(pm_ctx *c, const char *ir, size_t len, int32_t layout, const int64_t *lo,
                                        const int64_t *hi, int32_t *out_id, pm_table_info *info) {
   PM_TRACE("pm_compile_counts");
@@ -170,12 +183,7 @@ extern "C" pm_status pm_compile_counts(pm_ctx *c, const char *ir, size_t len, in
   int id = (int)c->tables.size();
   c->tables.push_back(std::move(words));
   c->dev_off.push_back(-1);
-  if (c->device >= 0) {
-    pm_status g = ctx_device_guard(c);
-    if (g) return g;
-    pm_status u = upload_table(c, id);
-    if (u) return u;
-  }
+  if (pm_status u = register_on_device(c, id)) return u;
   *out_id = id;
   if (info) {
     info->n_params = inf[0]; info->n_atoms = inf[1]; info->n_conds = inf[2]; info->n_pieces = inf[3];
@@ -195,12 +203,7 @@ extern "C" pm_status pm_table_load(pm_ctx *c, const uint32_t *words, size_t n_wo
   int id = (int)c->tables.size();
   c->tables.emplace_back(words, words + n_words);
   c->dev_off.push_back(-1);
-  if (c->device >= 0) {
-    pm_status g = ctx_device_guard(c);
-    if (g) return g;
-    pm_status u = upload_table(c, id);
-    if (u) return u;
-  }
+  if (pm_status u = register_on_device(c, id)) return u;
   *out_id = id;
   return PM_OK;
 }
@@ -228,6 +231,7 @@ pm_status ctx_table_offsets(pm_ctx *c, const int32_t *ids, int n, int *P, int *K
     if (*P < 0) { *P = p; *K = k; }
     if (P && *P != p) return pm_set_error(PM_ERR_INVALID_ARG, "tables differ in parameter count");
     if (*K != k) return pm_set_error(PM_ERR_INVALID_ARG, "tables differ in layout");
+    if (c->device >= 0 && c->dev_off[id] < 0) return pm_set_error(PM_ERR_INVALID_ARG, "table not on the device");
     off[i] = c->dev_off[id];
   }
   void *d = nullptr;
