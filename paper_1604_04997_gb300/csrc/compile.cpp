@@ -1762,19 +1762,21 @@ static Result compile(const std::string &text, int layout, const int64_t *plo, c
       if (!c.val.empty()) D = D / gcd128(D, c.den) * c.den;
   if (D > 4096) fail(E_UNSUP, "count denominator above 4096");
 
-  // overflow check: per column, sum of multiplicity * count bound, times D
+  // overflow check: per column, the sum of multiplicity * count bound, times D, stays
+  // below 2^62, so every value D * count the evaluators form is below 2^62
   {
+    const i128 lim = i128(1) << 62;
     std::vector<i128> bound(ncols, 0);
     for (auto &t : terms) {
       i128 mb = 0;
       for (auto &c : t.cases) mb = std::max(mb, c.bound);
-      if (mb > (i128(1) << 62)) fail(E_RANGE, "a count may exceed 2^62 on the box");
+      if (mb >= lim) fail(E_RANGE, "a count may reach 2^62 on the box");
       mb *= D;
       for (auto &kv : t.colmul) {
         i128 m = kv.second < 0 ? -kv.second : kv.second;
-        if (mb > (i128(1) << 62) || (m && mb > ((i128(1) << 62) / m))) fail(E_RANGE, "a count may exceed 2^62 on the box");
+        if (m && mb >= (lim + m - 1) / m) fail(E_RANGE, "a count may reach 2^62 on the box");   // m * mb >= 2^62
         bound[kv.first] += m * mb;
-        if (bound[kv.first] > (i128(1) << 62)) fail(E_RANGE, "a count may exceed 2^62 on the box");
+        if (bound[kv.first] >= lim) fail(E_RANGE, "a count may reach 2^62 on the box");
       }
     }
   }

@@ -278,3 +278,27 @@ def test_random_kernels_exact_or_refused(ctx):
         for p, f in zip(pts, oracle.Kernel(ir).features(pts, 32, "brute")):
             assert T.evaluate([int(x) for x in p]) == list(f), (ir, p)
     assert accepted > 50
+
+
+def test_count_of_exactly_2_62_is_refused(ctx):
+    """A count that reaches 2^62 at the box corner (65,536 x 65,536 x 16,384 x 65,536
+    points) is refused; one point less on n is accepted."""
+    ir = """kernel r
+param n m
+array a global f32 64*n+64*m+64
+dim g g0 0 ceil(m/8)
+dim l l0 0 8
+dim s0 seq 2 n+2
+dim s1 seq 0 ceil(n/4)
+dim s2 seq 0 n
+stmt st0 g,l,s0,s1,s2
+guard 8*g+l < n
+flop f32 add 1
+store a[8*g+l]
+end
+"""
+    with pytest.raises(B.PMError) as e:
+        ctx.compile_counts(ir, 32, [1, 1], [65536, 65536])
+    assert e.value.code == -4
+    tid, _ = ctx.compile_counts(ir, 32, [1, 1], [65535, 65536])
+    assert Table(ctx.table_image(tid)).evaluate([65535, 65536])[3] == 65535 ** 3 * 16384   # (g, l), s0, s2: 65535; s1: 16384
