@@ -107,3 +107,34 @@ def test_program_coupled_denominator(ctx, t):
     vs = [v for v in W.coupled_variants() if v.template == t]
     for v in [vs[i] for i in rng.choice(len(vs), 5, replace=False)]:
         _check(ctx, v, 1, 65536, rng, n_points=16)
+
+
+def test_program_random_kernels(ctx):
+    """Random kernels (tiled axes, sequential loops, guards over one to three
+    indices, strided accesses) on random boxes: each table's program equals the
+    weighted counts at the box corners and inside, for signed and unsigned weights."""
+    from test_compile_fuzz import _random_kernel
+    rng = np.random.default_rng(72)
+    checked = 0
+    for _ in range(120):
+        ir, P = _random_kernel(rng)
+        lo, hi = int(rng.choice([0, 1, 64])), int(rng.choice([96, 4096, 65536]))
+        try:
+            tid, _ = ctx.compile_counts(ir, 32, [lo] * P, [hi] * P)
+        except B.PMError:
+            continue
+        words = ctx.table_image(tid)
+        T = Table(words)
+        prog, tgt, con = k2_program(words)
+        corners = [[lo if (m >> i) & 1 else hi for i in range(P)] for m in range(1 << P)]
+        pts = corners + [[int(x) for x in rng.integers(lo, hi + 1, size=P)] for _ in range(6)]
+        for trial in range(2):
+            Wcol = [int(x) for x in rng.integers(-(1 << 55), 1 << 55, size=32)]
+            if trial == 0:
+                Wcol = [abs(x) for x in Wcol]
+            fill(prog, tgt, con, Wcol)
+            for n in pts:
+                ref = sum(Wcol[c] * x for c, x in enumerate(T.evaluate(n, check_magic=False)))
+                assert program_dot(prog, T, n) == ref, (ir, lo, hi, n)
+        checked += 1
+    assert checked > 40
