@@ -7,6 +7,8 @@
 // Error <= 2^-(E_m+1) sum_i |F_ri| + 2^-56 |T|, i.e. about 2^-59 (max|w|/min|w|)
 // of sum_i |F_ri w_mi|.  (64-bit integer <-> float conversions, which would be
 // needed per term by a float-float scheme, run on the FP64 pipe of this GPU.)
+// The same products feed a per-model argmin over rows and a top-k per (group, model)
+// (configuration selection, Sec. 6.1) without writing T.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
