@@ -225,3 +225,40 @@ def test_checkpoint_corruption_detected(ctx, tmp_path):
     open(bad, "wb").write(bytes(raw[:20]))
     with pytest.raises(ValueError):
         CK.load(bad, ctx)
+
+
+def test_named_arrays_round_trip(ctx, tmp_path):
+    arrs = {"a": np.arange(12, dtype=np.int64).reshape(3, 4), "b": np.array([1.5, -2.0], dtype=np.float32),
+            "c": np.zeros((0, 5), dtype=np.int32), "d": np.array(7, dtype=np.uint8), "e": np.array([True, False])}
+    path = os.path.join(tmp_path, "arr.pmck")
+    CK.save(path, ctx, [], arrays=arrs)
+    ck = CK.load(path, ctx)
+    assert ck.table_ids == [] and ck.weights is None and set(ck.arrays) == set(arrs)
+    for k, v in arrs.items():
+        assert ck.arrays[k].dtype == v.dtype and np.array_equal(ck.arrays[k], v), k
+    with pytest.raises(ValueError, match="not storable"):
+        CK.save(path, ctx, [], arrays={"s": np.array(["x"])})
+
+
+def test_tuning_space_resumes(ctx, tmp_path):
+    """A whole tuning space (variants of every template, duplicate draws sharing a
+    table, both offset arrays, the points) and its weights, saved and loaded into a
+    fresh context: the same space, each variant's table image unchanged."""
+    from paper_1604_04997_gb300 import tuning
+    b = tuning.build(ctx, n_variants=60, n_points=20, variant_seed=31, point_seed=32)
+    w = W.draw_weights(32, 4, 33)
+    path = os.path.join(tmp_path, "space.pmck")
+    tuning.save_space(path, ctx, b, w)
+    ctx2 = B.Context(-1)
+    try:
+        b2, w2 = tuning.load_space(path, ctx2)
+        assert b2.templates == b.templates and b2.variants == b.variants
+        assert np.array_equal(b2.var_off, b.var_off) and np.array_equal(b2.pt_off, b.pt_off)
+        assert np.array_equal(b2.points, b.points) and np.array_equal(w2, w)
+        assert b2.n_distinct == len(set(b.tables.tolist()))
+        for t1, t2 in zip(b.tables, b2.tables):
+            assert np.array_equal(ctx.table_image(int(t1)), ctx2.table_image(int(t2)))
+        # duplicates still share one table
+        assert len(set(b2.tables.tolist())) == len(set(b.tables.tolist()))
+    finally:
+        ctx2.close()
