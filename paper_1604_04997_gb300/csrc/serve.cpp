@@ -142,10 +142,35 @@ struct ServeState {
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> free_events;
   int next_stream = 0;
-  // statistics
+  // statistics: every latency since the last reset, or (past LAT_CAP of them) a
+  // uniform sample of LAT_CAP, kept by reservoir sampling
   std::vector<float> lat_us;
+  uint64_t lat_seen = 0, lat_rng = 0;
   uint64_t n_batches = 0, n_queries = 0, n_cand = 0;
 };
+
+constexpr size_t LAT_CAP = size_t(1) << 22;
+
+// splitmix64 (Steele, Lea and Flood, 2014): a counter-based 64-bit generator
+static uint64_t splitmix64(uint64_t &state) {
+  uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Record one latency: the first LAT_CAP are kept; the i-th after that (0-based
+// count i of all seen) replaces a random kept one with probability LAT_CAP / (i + 1),
+// which keeps a uniform sample of all seen (reservoir sampling, Vitter's Algorithm R).
+static void record_latency(ServeState *S, float us) {
+  if (S->lat_us.size() < LAT_CAP) {
+    S->lat_us.push_back(us);
+  } else {
+    const uint64_t k = splitmix64(S->lat_rng) % (S->lat_seen + 1);
+    if (k < LAT_CAP) S->lat_us[(size_t)k] = us;
+  }
+  S->lat_seen++;
+}
 
 static pm_status cu_err(cudaError_t e, const char *what) {
   return pm_set_error(PM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -286,8 +311,7 @@ static void finish_batch(ServeState *S, Batch *B) {
   for (size_t j = 0; j < B->qs.size(); j++) {
     auto it = S->tickets.find(B->qs[j].ticket);
     if (it != S->tickets.end()) { it->second.done = true; it->second.result = res[j]; }
-    S->lat_us.push_back(
-        (float)std::chrono::duration<double, std::micro>(now - B->qs[j].t_submit).count());
+    record_latency(S, (float)std::chrono::duration<double, std::micro>(now - B->qs[j].t_submit).count());
     S->n_queries++;
     S->n_cand += (uint64_t)B->qs[j].q.n_cand;
   }
@@ -470,6 +494,7 @@ extern "C" pm_status pm_serve_stats(pm_ctx *c, int32_t reset, pm_serve_stats_t *
   }
   if (reset) {
     S->lat_us.clear();
+    S->lat_seen = 0;
     S->n_queries = S->n_batches = S->n_cand = 0;
   }
   return PM_OK;
