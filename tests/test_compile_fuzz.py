@@ -302,3 +302,65 @@ end
     assert e.value.code == -4
     tid, _ = ctx.compile_counts(ir, 32, [1, 1], [65535, 65536])
     assert Table(ctx.table_image(tid)).evaluate([65535, 65536])[3] == 65535 ** 3 * 16384   # (g, l), s0, s2: 65535; s1: 16384
+
+
+def _rich_kernel(rng):
+    P = int(rng.integers(1, 3))
+    params = ["n", "m"][:P]
+    pick = lambda: params[rng.integers(P)]
+    T = int(rng.choice([4, 8, 16]))
+    dims = [("g", "g0", "0", f"ceil({pick()}/{T})"), ("l", "l0", "0", str(T))]
+    for i in range(int(rng.integers(1, 3))):
+        hi = [pick(), str(int(rng.integers(1, 6))), f"ceil({pick()}/{int(rng.integers(2, 5))})"][rng.integers(3)]
+        dims.append((f"s{i}", "seq", "0", hi))
+    ext = "64*n+64" if P == 1 else "64*n+64*m+64"
+    lines = ["kernel r", "param " + " ".join(params), f"array a global f32 {ext}", f"array d global f64 {ext}",
+             f"array sh local f32 {4 * T}"]
+    lines += [f"dim {d[0]} {d[1]} {d[2]} {d[3]}" for d in dims]
+    seqs = [d[0] for d in dims[2:]]
+    for si in range(int(rng.integers(1, 4))):
+        used = ["g", "l"] + [x for x in seqs if rng.random() < 0.7]
+        lines.append(f"stmt st{si} " + ",".join(used))
+        if rng.random() < 0.8:
+            lines.append(f"guard {T}*g+l < {pick()}")
+        if rng.random() < 0.5:
+            vs = rng.choice(used, int(rng.integers(1, min(3, len(used)) + 1)), replace=False)
+            lhs = "+".join(f"{int(rng.choice([-1, 1, 1]))}*{v}" for v in vs).replace("+-", "-")
+            lines.append(f"guard {lhs} {_OPS[rng.integers(4)]} {[pick(), str(int(rng.integers(0, 12)))][rng.integers(2)]}")
+        for _ in range(int(rng.integers(1, 3))):
+            lines.append(f"flop {rng.choice(['f32', 'f64'])} {rng.choice(['add', 'mul', 'div', 'pow', 'spec'])} "
+                         f"{int(rng.integers(1, 4))}")
+        lines.append([f"load a[{T}*g+l]", f"load d[{T}*g+l]", f"load a[{2 * T}*g+2*l] x2", f"load a[{4 * T}*g+4*l] x4",
+                      f"load a[{int(rng.integers(2, 5))}*({T}*g+l)]"][rng.integers(5)])
+        if rng.random() < 0.5:
+            lines.append("store sh[l]")
+        if rng.random() < 0.5:
+            lines.append(f"load sh[{T}+l]")
+        if rng.random() < 0.4:
+            lines.append(f"store d[{T}*g+l]")
+        lines.append("end")
+        if rng.random() < 0.5 and seqs:
+            lines.append(f"barrier b{si} " + ",".join(["g"] + [x for x in seqs if rng.random() < 0.6]))
+    return "\n".join(lines) + "\n", P
+
+
+def test_rich_random_kernels_exact_or_refused(ctx):
+    """Random kernels with barriers, local memory, 64- and 128-bit and strided global
+    accesses, f64 and every flop kind, in both layouts: each accepted table equals
+    brute force."""
+    rng = np.random.default_rng(91)
+    accepted = 0
+    for _ in range(100):
+        ir, P = _rich_kernel(rng)
+        layout = 32 if rng.random() < 0.7 else 12
+        try:
+            tid, _ = ctx.compile_counts(ir, layout, [1] * P, [4096] * P)
+        except B.PMError as e:
+            assert e.code in STATUS, e
+            continue
+        accepted += 1
+        T = Table(ctx.table_image(tid))
+        pts = rng.integers(1, 25, size=(3, P))
+        for p, f in zip(pts, oracle.Kernel(ir).features(pts, layout, "brute")):
+            assert T.evaluate([int(x) for x in p]) == list(f), (ir, layout, p)
+    assert accepted > 40
