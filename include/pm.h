@@ -150,11 +150,11 @@ pm_status pm_predict_argmin(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t 
 /* Top-k rows per (group, model) over materialised features (configuration selection,
  * Sec. 6.1: for each problem size, the variants with the smallest predicted time).
  * Group g consists of the positions [h_seg_off[g], h_seg_off[g+1]) (h_seg_off: host,
- * int64 [G+1], non-decreasing, h_seg_off[0] >= 0); position p names row d_rows[p]
- * (device int64 list of at least h_seg_off[G] entries, owned by the caller, e.g. the
- * rows t * n_points + p of one point p of a
- * [tables][points][k] counts array), or row p itself when d_rows is NULL (then
- * h_seg_off[G] <= R).  Out: d_top_idx int64 [G][M][topk] row indices and d_top_t fp64
+ * int64 [G+1], non-decreasing, h_seg_off[0] >= 0).  Position p names row d_rows[p]
+ * (a device int64 list of at least h_seg_off[G] entries, owned by the caller; e.g.
+ * the rows t * n_points + p of one point p of a [tables][points][k] counts array),
+ * or row p itself when d_rows is NULL (then h_seg_off[G] <= R).
+ * Out: d_top_idx int64 [G][M][topk] row indices and d_top_t fp64
  * [G][M][topk] times, ascending by (time, row); a group with fewer than topk rows
  * fills the rest with -1 and +inf.  The times are bit for bit those pm_predict writes
  * at PM_PREC_FP64 (the only precision accepted here); 1 <= topk <= 16, k <= 40,
