@@ -4,8 +4,9 @@ Every input ends in a status, never a crash or a hang; every table the compiler
 accepts counts exactly what the oracle's brute-force enumeration counts.  Includes
 the inputs that once broke it: an access with no cell at the classification
 instance (a division by zero), a statement domain of ~10^13 points at that instance
-(an endless walk), and a coupled guard whose bound on one index was dropped by a
-proof that used that same index's constraints (an extra group counted).
+(an endless walk), a coupled guard whose bound on one index was dropped by a proof
+that used that same index's constraints (an extra group counted), and a count of
+exactly 2^62 at a box corner (let through by the range check).
 """
 import re
 
