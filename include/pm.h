@@ -270,6 +270,9 @@ typedef struct {
   int64_t n_batches;
   int64_t n_candidates;
   double p50_us, p99_us, max_us, mean_us;
+  int64_t n_rejected;   /* submissions refused with PM_ERR_BUSY (can never fit the budget) */
+  int64_t h2d_bytes;    /* bytes copied host -> device by the launched batches */
+  int64_t d2h_bytes;    /* bytes copied device -> host by the launched batches */
 } pm_serve_stats_t;
 
 /* Make the weights of n_models device models resident (h_W fp64 [n_models][32], finite).

@@ -69,7 +69,8 @@ PMM_KINDS = ("empty", "copy", "sum4", "index", "vsa", "filled", "arith", "transp
 class ServeStats(ctypes.Structure):
     _fields_ = [("n_queries", ctypes.c_int64), ("n_batches", ctypes.c_int64), ("n_candidates", ctypes.c_int64),
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
-                ("mean_us", ctypes.c_double)]
+                ("mean_us", ctypes.c_double), ("n_rejected", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+                ("d2h_bytes", ctypes.c_int64)]
 
 
 def lib():

@@ -147,6 +147,7 @@ struct ServeState {
   std::vector<float> lat_us;
   uint64_t lat_seen = 0, lat_rng = 0;
   uint64_t n_batches = 0, n_queries = 0, n_cand = 0;
+  uint64_t n_rejected = 0, h2d_bytes = 0, d2h_bytes = 0;
 };
 
 constexpr size_t LAT_CAP = size_t(1) << 22;
@@ -283,6 +284,10 @@ static void worker_loop(ServeState *S) {
     lk.lock();
     S->flight.push_back(B);
     S->n_batches++;
+    if (rc == PM_OK) {
+      S->h2d_bytes += B->lay.out_idx;                  // the batch's copy-in
+      S->d2h_bytes += B->lay.keys - B->lay.status;     // and copy-out
+    }
     S->cv_flight.notify_all();
   }
   S->worker_done = true;
@@ -429,7 +434,13 @@ extern "C" pm_status pm_serve_submit(pm_ctx *c, const pm_query *q, uint64_t *tic
   if (q->n_cand < 0 || q->n_cand > (int64_t(1) << 30)) return pm_set_error(PM_ERR_INVALID_ARG, "bad n_cand");
   if (!q->h_top_idx || !q->h_top_t || (q->n_cand > 0 && (!q->h_tables || !q->h_points)))
     return pm_set_error(PM_ERR_INVALID_ARG, "null buffer");
-  if (query_bytes(q->n_cand) > S->region.cap) return pm_set_error(PM_ERR_BUSY, "query can never fit the memory budget");
+  if (query_bytes(q->n_cand) > S->region.cap) {
+    {
+      std::lock_guard<std::mutex> lk(S->m);
+      S->n_rejected++;
+    }
+    return pm_set_error(PM_ERR_BUSY, "query can never fit the memory budget");
+  }
   {
     std::lock_guard<std::mutex> lk(c->mu);
     const int32_t nt = (int32_t)c->tables.size();
@@ -481,6 +492,9 @@ extern "C" pm_status pm_serve_stats(pm_ctx *c, int32_t reset, pm_serve_stats_t *
   out->n_queries = (int64_t)S->n_queries;
   out->n_batches = (int64_t)S->n_batches;
   out->n_candidates = (int64_t)S->n_cand;
+  out->n_rejected = (int64_t)S->n_rejected;
+  out->h2d_bytes = (int64_t)S->h2d_bytes;
+  out->d2h_bytes = (int64_t)S->d2h_bytes;
   if (!S->lat_us.empty()) {
     std::vector<float> v = S->lat_us;
     std::sort(v.begin(), v.end());
@@ -496,6 +510,7 @@ extern "C" pm_status pm_serve_stats(pm_ctx *c, int32_t reset, pm_serve_stats_t *
     S->lat_us.clear();
     S->lat_seen = 0;
     S->n_queries = S->n_batches = S->n_cand = 0;
+    S->n_rejected = S->h2d_bytes = S->d2h_bytes = 0;
   }
   return PM_OK;
 }

@@ -289,3 +289,15 @@ end
         assert T.evaluate([n])[3] == n * (n - 1)
     one = body.split("stmt up")[0]
     assert Table(ctx.table_image(ctx.compile_counts(one, 32, [1], [65536])[0])).den == 2
+
+
+def test_serve_stats_struct_matches_the_binding(ctx):
+    """pm_serve_stats on a context without a serve loop clears the whole C struct:
+    the binding's struct must cover it exactly (guard bytes past it stay intact) and
+    every field reads zero."""
+    import ctypes
+    n = ctypes.sizeof(B.ServeStats)
+    buf = (ctypes.c_uint8 * (n + 32))(*([0xAB] * (n + 32)))
+    assert B.lib().pm_serve_stats(ctx.h, 0, ctypes.cast(buf, ctypes.POINTER(B.ServeStats))) == 0
+    assert all(b == 0 for b in buf[:n]) and all(b == 0xAB for b in buf[n:])
+    assert all(v == 0 for v in ctx.serve_stats().values()) and "n_rejected" in ctx.serve_stats()
