@@ -124,6 +124,7 @@ pm_status pm_table_image(pm_ctx *ctx, int32_t table_id, uint32_t *h_buf, size_t 
  * parameter points: d_points int64 [n_points][P] (P = the tables' common
  * parameter count), d_counts int64 [n_tables][n_points][k] (k = the tables'
  * common layout).  Exact int64 (Sec. 2: p_i re-evaluated for changed n).
+ * n_points <= 2^37; any number of tables (launched 65,535 at a time).
  * A point outside a table's box yields zeros and sets PM_ERR_OUT_OF_BOX. */
 pm_status pm_eval_counts(pm_ctx *ctx, const int32_t *h_table_ids, int32_t n_tables,
                          const int64_t *d_points, int64_t n_points, int64_t *d_counts, void *stream);

@@ -248,13 +248,18 @@ extern "C" pm_status pm_eval_counts(pm_ctx *c, const int32_t *ids, int32_t n_tab
   if (n_tables < 0 || n_points < 0 || (n_tables && !ids)) return pm_set_error(PM_ERR_INVALID_ARG, "bad sizes");
   if (n_tables == 0 || n_points == 0) return PM_OK;
   if (!d_points || !d_counts) return pm_set_error(PM_ERR_INVALID_ARG, "null device buffer");
-  if (n_points > (int64_t(1) << 40)) return pm_set_error(PM_ERR_INVALID_ARG, "too many points");
+  // the launch puts points on grid x (128 per block) and tables on grid y (at most 65,535)
+  if (n_points > (int64_t(1) << 37)) return pm_set_error(PM_ERR_INVALID_ARG, "too many points");
   int P, K;
   const int64_t *d_off;
   pm_status s = ctx_table_offsets(c, ids, n_tables, &P, &K, &d_off);
   if (s) return s;
-  CU(pmd::launch_eval_counts(c->arena, d_off, n_tables, d_points, n_points, P, K, d_counts, c->d_status,
-                             (cudaStream_t)stream));
+  constexpr int32_t MAX_GRID_Y = 65535;
+  for (int32_t t0 = 0; t0 < n_tables; t0 += MAX_GRID_Y) {
+    const int32_t nt = std::min(MAX_GRID_Y, n_tables - t0);
+    CU(pmd::launch_eval_counts(c->arena, d_off + t0, nt, d_points, n_points, P, K,
+                               d_counts + (int64_t)t0 * n_points * K, c->d_status, (cudaStream_t)stream));
+  }
   return PM_OK;
 }
 
