@@ -591,7 +591,8 @@ def run_serve(args):
     def summ(st, wall, n):
         return {"p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1), "max_us": round(st["max_us"], 1),
                 "batches": st["n_batches"], "queries_per_batch": round(st["n_queries"] / max(1, st["n_batches"]), 2),
-                "evals_per_s": st["n_candidates"] / wall, "queries": n}
+                "evals_per_s": st["n_candidates"] / wall, "queries": n, "rejected": st["n_rejected"],
+                "h2d_mb": round(st["h2d_bytes"] / 1e6, 2), "d2h_mb": round(st["d2h_bytes"] / 1e6, 2)}
 
     line = {"metric": "served candidate evaluations/s (Poisson 2,000 queries/s, 1-50,000 candidates each, "
                       "FP64-accurate top-16 per query)",
