@@ -299,9 +299,11 @@ pm_status pm_serve_submit(pm_ctx *ctx, const pm_query *q, uint64_t *ticket);
  * returned something other than PM_PENDING (then PM_ERR_NOT_FOUND). */
 pm_status pm_serve_poll(pm_ctx *ctx, uint64_t ticket, int32_t timeout_us);
 /* Counters and submit-to-completion latencies since the last reset (reset != 0 clears
- * them after reading).  The percentiles and the mean are exact over the first
- * 4,194,304 queries since the reset and then taken over a uniform random sample of
- * that many of them, so a long-running server holds at most 16 MB of latencies. */
+ * them after reading).  max_us and mean_us are exact over every query since the reset.
+ * The percentiles are exact over the first 4,194,304 queries since the reset and then
+ * taken over a uniform random sample of that many of them, so a long-running server
+ * holds at most 16 MB of latencies.  The percentiles are computed after the serve
+ * lock is released, so a stats call does not stall admission. */
 pm_status pm_serve_stats(pm_ctx *ctx, int32_t reset, pm_serve_stats_t *out);
 /* Finish every queued and running query, then stop the threads and free the serve
  * memory.  Unpolled tickets stay pollable until the next pm_serve_start. */

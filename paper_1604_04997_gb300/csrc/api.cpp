@@ -254,9 +254,9 @@ extern "C" pm_status pm_eval_counts(pm_ctx *c, const int32_t *ids, int32_t n_tab
   const int64_t *d_off;
   pm_status s = ctx_table_offsets(c, ids, n_tables, &P, &K, &d_off);
   if (s) return s;
-  constexpr int32_t MAX_GRID_Y = 65535;
-  for (int32_t t0 = 0; t0 < n_tables; t0 += MAX_GRID_Y) {
-    const int32_t nt = std::min(MAX_GRID_Y, n_tables - t0);
+  constexpr int64_t MAX_GRID_Y = 65535;
+  for (int64_t t0 = 0; t0 < n_tables; t0 += MAX_GRID_Y) {
+    const int nt = (int)std::min<int64_t>(MAX_GRID_Y, n_tables - t0);
     CU(pmd::launch_eval_counts(c->arena, d_off + t0, nt, d_points, n_points, P, K,
                                d_counts + (int64_t)t0 * n_points * K, c->d_status, (cudaStream_t)stream));
   }

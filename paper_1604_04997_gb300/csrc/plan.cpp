@@ -33,8 +33,8 @@ static constexpr int SLICE_VARIANTS = 128;
 //   condition with t terms:   2 per 64-bit multiply-add, 2 for sum and compare    2t + 2
 //   monomial product:         one 64-bit multiply                                 3
 //   coefficient entry:        64-bit multiply and add                             5
-//   non-empty column:         Dot2 term (split 4, products 4, TwoSum 6, comp. 1)  15
-//   post-op min(loads, stores): compare-select 2 + Dot2 term                      17
+//   non-empty column:         its weighted term of the exact fixed-point dot        15
+//   post-op min(loads, stores): compare-select 2 + its weighted term             17
 //   box check, piece lookup, top-k compare                                        10
 static double table_work(const std::vector<uint32_t> &w) {
   const int P = (int)w[pmt::H_NPARAMS], A = (int)w[pmt::H_NATOMS], NC = (int)w[pmt::H_NCONDS];
@@ -52,7 +52,7 @@ static double table_work(const std::vector<uint32_t> &w) {
     const uint32_t *en = w.data() + w[pmt::H_OFF_ENTRIES] + pmt::ENTRY_WORDS * pc[2];
     for (uint32_t e = 0; e < pc[3]; e++, en += pmt::ENTRY_WORDS) {
       per += 5.0;                                          // 64-bit multiply-add
-      if (en[2] & pmt::ENTRY_LAST) per += 15.0;            // Dot2 term of the column
+      if (en[2] & pmt::ENTRY_LAST) per += 15.0;            // weighted term of the column
     }
   }
   return ops + per / np;

@@ -480,7 +480,7 @@ extern "C" pm_status pm_predict_argmin_static(const int64_t *d_F, int64_t R, int
   using namespace pmd;
   if (R < 0 || k <= 0 || k > PR_MAXK || M <= 0 || M > PR_MAXM)
     return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: need R >= 0, 0 < k <= 40, 0 < M <= 64");
-  if (!d_F || !d_W || !d_arg || !d_min) return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: null pointer");
+  if ((!d_F && R > 0) || !d_W || !d_arg || !d_min) return pm_set_error_c(PM_ERR_INVALID_ARG, "pm_predict_argmin_static: null pointer");
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= STATIC_MAX_DEVICES)
     return pm_set_error_c(PM_ERR_CUDA, "pm_predict_argmin_static: no usable current device");

@@ -146,6 +146,7 @@ struct ServeState {
   // uniform sample of LAT_CAP, kept by reservoir sampling
   std::vector<float> lat_us;
   uint64_t lat_seen = 0, lat_rng = 0;
+  double lat_max = 0, lat_sum = 0;   // exact over every latency since the last reset
   uint64_t n_batches = 0, n_queries = 0, n_cand = 0;
   uint64_t n_rejected = 0, h2d_bytes = 0, d2h_bytes = 0;
 };
@@ -171,6 +172,8 @@ static void record_latency(ServeState *S, float us) {
     if (k < LAT_CAP) S->lat_us[(size_t)k] = us;
   }
   S->lat_seen++;
+  S->lat_max = std::max(S->lat_max, (double)us);
+  S->lat_sum += us;
 }
 
 static pm_status cu_err(cudaError_t e, const char *what) {
@@ -488,29 +491,42 @@ extern "C" pm_status pm_serve_stats(pm_ctx *c, int32_t reset, pm_serve_stats_t *
   std::memset(out, 0, sizeof(*out));
   ServeState *S = c->serve;
   if (!S) return PM_OK;
-  std::lock_guard<std::mutex> lk(S->m);
-  out->n_queries = (int64_t)S->n_queries;
-  out->n_batches = (int64_t)S->n_batches;
-  out->n_candidates = (int64_t)S->n_cand;
-  out->n_rejected = (int64_t)S->n_rejected;
-  out->h2d_bytes = (int64_t)S->h2d_bytes;
-  out->d2h_bytes = (int64_t)S->d2h_bytes;
-  if (!S->lat_us.empty()) {
-    std::vector<float> v = S->lat_us;
-    std::sort(v.begin(), v.end());
-    auto pct = [&](double p) { return (double)v[std::min(v.size() - 1, (size_t)(p * (double)(v.size() - 1) + 0.5))]; };
+  // copy (or take) the record under the lock; the percentiles are found after it is
+  // released, so that a stats call does not hold up admission or the completion thread
+  std::vector<float> v;
+  uint64_t seen;
+  double mx, sum;
+  {
+    std::lock_guard<std::mutex> lk(S->m);
+    out->n_queries = (int64_t)S->n_queries;
+    out->n_batches = (int64_t)S->n_batches;
+    out->n_candidates = (int64_t)S->n_cand;
+    out->n_rejected = (int64_t)S->n_rejected;
+    out->h2d_bytes = (int64_t)S->h2d_bytes;
+    out->d2h_bytes = (int64_t)S->d2h_bytes;
+    seen = S->lat_seen;
+    mx = S->lat_max;
+    sum = S->lat_sum;
+    if (reset) {
+      v.swap(S->lat_us);
+      S->lat_seen = 0;
+      S->lat_max = S->lat_sum = 0;
+      S->n_queries = S->n_batches = S->n_cand = 0;
+      S->n_rejected = S->h2d_bytes = S->d2h_bytes = 0;
+    } else {
+      v = S->lat_us;
+    }
+  }
+  if (!v.empty()) {
+    auto pct = [&](double p) {
+      const size_t i = std::min(v.size() - 1, (size_t)(p * (double)(v.size() - 1) + 0.5));
+      std::nth_element(v.begin(), v.begin() + (std::ptrdiff_t)i, v.end());
+      return (double)v[i];
+    };
     out->p50_us = pct(0.50);
     out->p99_us = pct(0.99);
-    out->max_us = v.back();
-    double s = 0;
-    for (float x : v) s += x;
-    out->mean_us = s / (double)v.size();
-  }
-  if (reset) {
-    S->lat_us.clear();
-    S->lat_seen = 0;
-    S->n_queries = S->n_batches = S->n_cand = 0;
-    S->n_rejected = S->h2d_bytes = S->d2h_bytes = 0;
+    out->max_us = mx;
+    out->mean_us = sum / (double)seen;
   }
   return PM_OK;
 }

@@ -41,26 +41,13 @@ def compile_variants(ctx: B.Context, variants: Sequence[W.Variant], lo: int, hi:
 
 def build(ctx: B.Context, n_variants: int = 10000, n_points: int = 4096, variant_seed: int = 2,
           point_seed: int = 3, lo: int = W.BOX_LO, hi: int = W.BOX_HI, coupled: bool = False) -> Batched:
-    """The batched tuning workload: variants drawn with replacement from the tuning
-    space over the eight templates (or, with coupled=True, over the coupled-domain
-    templates: triangles and bands); per template n_points log-uniform points."""
-    templates = W.COUPLED_TEMPLATES if coupled else W.TEMPLATES
-    drawn = W.draw_coupled_variants(n_variants, variant_seed) if coupled else W.draw_variants(n_variants, variant_seed)
-    groups = W.group_by_template(drawn, templates)
-    pts = W.template_points(point_seed, n_points, lo, hi, templates)
+    """The batched tuning workload of workloads.batched_space, compiled in ctx
+    (duplicate variants share one table)."""
+    sp = W.batched_space(n_variants, n_points, variant_seed, point_seed, lo, hi, coupled)
     cache: Dict = {}
-    variants, tables, var_off, pt_rows, pt_off = [], [], [0], [], [0]
-    for t in templates:
-        vs = [drawn[i] for i in groups[t]]
-        variants += vs
-        tables += compile_variants(ctx, vs, lo, hi, 32, cache)
-        var_off.append(len(tables))
-        p = np.zeros((n_points, 4), dtype=np.int64)
-        p[:, :pts[t].shape[1]] = pts[t]
-        pt_rows.append(p)
-        pt_off.append(pt_off[-1] + n_points)
-    return Batched(list(templates), variants, np.array(tables, dtype=np.int32), np.array(var_off, dtype=np.int32),
-                   np.concatenate(pt_rows), np.array(pt_off, dtype=np.int64), len(cache))
+    tables = compile_variants(ctx, sp.variants, lo, hi, 32, cache)
+    return Batched(sp.templates, sp.variants, np.array(tables, dtype=np.int32), sp.var_off, sp.points, sp.pt_off,
+                   len(cache))
 
 
 def save_space(path: str, ctx: B.Context, b: Batched, weights: np.ndarray = None) -> None:

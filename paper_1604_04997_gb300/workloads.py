@@ -478,6 +478,38 @@ def template_points(seed: int, n_points: int, lo: int = BOX_LO, hi: int = BOX_HI
             for i, t in enumerate(templates)}
 
 
+@dataclasses.dataclass
+class Space:
+    """A batched tuning space before compilation: variants in template-major order,
+    CSR offsets per template, and each template's points padded to 4 parameters."""
+    templates: List[str]
+    variants: List[Variant]
+    var_off: np.ndarray      # int32 [T+1]
+    points: np.ndarray       # int64 [total][4]
+    pt_off: np.ndarray       # int64 [T+1]
+
+
+def batched_space(n_variants: int = 10000, n_points: int = 4096, variant_seed: int = 2, point_seed: int = 3,
+                  lo: int = BOX_LO, hi: int = BOX_HI, coupled: bool = False) -> Space:
+    """The batched tuning workload: variants drawn with replacement from the tuning
+    space over the eight templates (or, with coupled=True, over the coupled-domain
+    templates), grouped by template; n_points log-uniform points per template."""
+    templates = COUPLED_TEMPLATES if coupled else TEMPLATES
+    drawn = draw_coupled_variants(n_variants, variant_seed) if coupled else draw_variants(n_variants, variant_seed)
+    groups = group_by_template(drawn, templates)
+    pts = template_points(point_seed, n_points, lo, hi, templates)
+    variants, var_off, rows, pt_off = [], [0], [], [0]
+    for t in templates:
+        variants += [drawn[i] for i in groups[t]]
+        var_off.append(len(variants))
+        p = np.zeros((n_points, 4), dtype=np.int64)
+        p[:, :pts[t].shape[1]] = pts[t]
+        rows.append(p)
+        pt_off.append(pt_off[-1] + n_points)
+    return Space(list(templates), variants, np.array(var_off, dtype=np.int32), np.concatenate(rows),
+                 np.array(pt_off, dtype=np.int64))
+
+
 def draw_weights(k: int, n_models: int, seed: int, lo: float = 1e-12, hi: float = 1e-9) -> np.ndarray:
     """Per-device weight vectors, uniform in [lo, hi] (units: seconds per operation)."""
     rng = np.random.default_rng(seed)

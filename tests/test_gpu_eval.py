@@ -71,6 +71,22 @@ def test_many_tables_ragged(env, n_points):
         assert np.array_equal(got[i], oracle.Kernel(W.variant_ir(v)).features(pts, 32, "struct")), v.name
 
 
+def test_more_tables_than_one_launch_holds(env):
+    """pm_eval_counts launches at most 65,535 tables at a time (the grid's y limit):
+    70,000 entries (two distinct tables, alternating in runs) on 3 points cross that
+    boundary, and every table's row block equals the oracle's counts."""
+    ctx, dev = env
+    vs = [W.canonical("stencil"), [v for v in W.all_variants() if v.template == "stencil"][7]]
+    ids = tuning.compile_variants(ctx, vs, 64, 65536)
+    pts = np.array([[64], [1000], [65536]], dtype=np.int64)
+    ref = [oracle.Kernel(W.variant_ir(v)).features(pts, 32, "struct") for v in vs]
+    which = (np.arange(70000) // 7) % 2          # runs of 7, so both sides of 65,535 differ
+    got = _eval(ctx, dev, [ids[i] for i in which], pts)
+    assert got.shape == (70000, 3, 32)
+    for i in (0, 1):
+        assert (got[which == i] == ref[i][None]).all()
+
+
 def test_layout12(env):
     ctx, dev = env
     import torch

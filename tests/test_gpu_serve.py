@@ -149,9 +149,11 @@ def test_serve_empty_query_and_errors(env):
     n = 2_000_000
     big_t = np.full(n, int(b.tables[0]), dtype=np.int32)
     big_p = np.full((n, 4), 100, dtype=np.int64)
+    rejected = ctx.serve_stats()["n_rejected"]
     with pytest.raises(B.PMError) as e:
         ctx.serve_submit(B.make_query(0, 4, big_t, big_p, idx, tt))
     assert e.value.code == -6
+    assert ctx.serve_stats()["n_rejected"] == rejected + 1
 
 
 def test_serve_small_budget_queues_and_stats(env):
@@ -167,9 +169,15 @@ def test_serve_small_budget_queues_and_stats(env):
         for q, (idx, tt) in zip(qs, res):
             _check(_oracle_times(b, q, Wm), 16, idx, tt)
         st = ctx.serve_stats(reset=True)
-        assert st["n_queries"] == len(qs) and st["n_candidates"] == sum(len(q.variant) for q in qs)
+        n_cand = sum(len(q.variant) for q in qs)
+        assert st["n_queries"] == len(qs) and st["n_candidates"] == n_cand
         assert 0 < st["p50_us"] <= st["p99_us"] <= st["max_us"]
-        assert ctx.serve_stats()["n_queries"] == 0
+        assert 0 < st["mean_us"] <= st["max_us"]
+        # every candidate's point (32 B) went up, every query's results came back
+        assert st["h2d_bytes"] >= 32 * n_cand and st["d2h_bytes"] > 0 and st["n_rejected"] == 0
+        st2 = ctx.serve_stats()
+        assert st2["n_queries"] == 0 and st2["h2d_bytes"] == 0 and st2["d2h_bytes"] == 0
+        assert st2["n_rejected"] == 0 and st2["max_us"] == 0
         with pytest.raises(B.PMError) as e:
             ctx.serve_set_weights(Wm)      # weights are fixed while serving
         assert e.value.code == -6

@@ -302,6 +302,85 @@ def test_predict_cancellation_and_k1():
     assert oracle.predict(F1, np.array([[3.3e-11]]))[0, 0] == 123456789012 * 3.3e-11
 
 
+
+# ----------------------------------------------------------------------------- Sigma |F_i w_i|
+
+def _abs_within(A, F, Wm):
+    """Sigma_i |F_i w_i| of every (row, model), each within (k + 2) 2^-52 of the exact
+    rational sum: k products and k sums, each rounded once, plus the int64 -> double
+    conversion of counts above 2^53."""
+    k = F.shape[1]
+    for r in range(F.shape[0]):
+        for m in range(Wm.shape[0]):
+            ex = sum(abs(Fraction(int(f)) * Fraction(float(x))) for f, x in zip(F[r], Wm[m]))
+            if abs(Fraction(float(A[r, m])) - ex) > ex * Fraction(k + 2, 2 ** 52):
+                return False
+    return True
+
+
+def test_predict_abs_exact_and_planted_mistakes():
+    """Sec. 2's sum Sigma alpha_i p_i, term by term in absolute value: the scale of every
+    cancellation-aware tolerance.  Counts up to 2^62 (so the conversion to double rounds),
+    weights of both signs over Table 2's range (Sec. 5: 3.9e-13 .. 1.3e-4)."""
+    rng = np.random.default_rng(11)
+    k = 32
+    F = rng.integers(0, 2 ** 62, size=(24, k), dtype=np.int64)
+    F[:8] = rng.integers(0, 2 ** 31, size=(8, k), dtype=np.int64)       # counts below 2^32 too
+    F[8:10, ::3] = 0                                                    # zero counts
+    mag = np.exp(rng.uniform(np.log(3.9e-13), np.log(1.3e-4), size=(4, k)))
+    Wm = mag * rng.choice([-1.0, 1.0], size=(4, k))
+    A = oracle.predict_abs(F, Wm)
+    assert _abs_within(A, F, Wm)
+    # the pin rejects plausible mistakes planted in the same computation
+    hi = (F >> 32) << 32
+    assert not _abs_within(np.abs(hi.astype(np.float64)) @ np.abs(Wm).T, F, Wm)       # high halves only
+    assert not _abs_within(np.abs(oracle.predict(F, Wm)), F, Wm)                        # |sum| for sum |.|
+    assert not _abs_within(F.astype(np.float64) @ Wm.T, F, Wm)                          # signs kept
+    assert not _abs_within(A[:, ::-1], F, Wm)                                           # models swapped
+
+
+# ----------------------------------------------------------------------------- batched baseline
+
+def _ranked(t, topk):
+    """Full sort on (time, variant) per point, as orc_topk does: the reading of Sec. 6.1's
+    selection where duplicate variants tie exactly."""
+    return oracle.topk(np.ascontiguousarray(t.T), topk)
+
+
+@pytest.mark.parametrize("template,topk", [("stencil", 16), ("matmul", 16), ("vecadd", 40)])
+def test_eval_predict_topk_is_count_predict_sort(template, topk):
+    """The timed CPU baseline (per point: counts, Dot2 prediction, insertion into a
+    sorted list) equals the composition of the pinned parts: the per-axis counts, the
+    32-column layout, Dot2 (orc_predict) and the full sort (orc_topk).  The variant
+    list repeats variants (exact ties broken by index) and the vecadd case asks for
+    more entries than there are variants."""
+    allv = [v for v in W.all_variants() if v.template == template]
+    rng = np.random.default_rng(21)
+    pick = [allv[i] for i in rng.choice(len(allv), size=12, replace=False)]
+    vs = pick + [pick[3], pick[0], pick[7], pick[3]] + pick[:4]          # duplicates, out of order
+    P = len(W.TEMPLATE_PARAMS[template])
+    pts = W.draw_points(P, 48, 31)
+    kernels = [kern(v) for v in vs]
+    w = W.draw_weights(32, 1, 4)[0]
+    idx, val = oracle.eval_predict_topk(kernels, pts, w, topk, n_threads=2)
+    t = np.stack([oracle.predict(k.features(pts, 32, "struct"), w[None])[:, 0] for k in kernels])
+    ridx, rval = _ranked(t, topk)
+    assert np.array_equal(idx, ridx)
+    assert np.array_equal(val, rval)
+    if topk > len(vs):
+        assert (idx[:, len(vs):] == -1).all() and np.isinf(val[:, len(vs):]).all()
+    # a tie-break that lets a later equal time in (insertion with <=) gives other lists
+    bad = []
+    for p in range(len(pts)):
+        lst = []
+        for v in range(len(vs)):
+            q = len(lst)
+            while q > 0 and t[v, p] <= t[lst[q - 1], p]:
+                q -= 1
+            lst.insert(q, v)
+        bad.append((lst + [-1] * topk)[:topk])
+    assert not np.array_equal(np.array(bad), idx)
+
 # ----------------------------------------------------------------------------- top-k
 
 def test_topk_full_sort_and_ties():

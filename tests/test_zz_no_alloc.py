@@ -1,11 +1,13 @@
 """pm_predict_argmin_static: the argmin entry point for callers that cannot allocate
 device memory (it uses a fixed array inside the library and needs no context).  Its
-results must equal those of pm_predict_argmin on the same inputs, on consecutive
-calls that reuse the shared array.  Collected last so that a failure here comes
+results must equal those of pm_predict_argmin on the same inputs bit for bit (the two
+share their arithmetic), on consecutive calls that reuse the shared array, and agree
+with the oracle's FP64-accurate times.  Collected last so that a failure here comes
 after every other test has run."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1604_04997_gb300 import binding as B
 from paper_1604_04997_gb300 import workloads as W
 
@@ -37,7 +39,18 @@ def test_static_argmin_matches_allocating_entry_point():
             torch.cuda.synchronize()
             a_ref, m_ref, a, m = (x.cpu().numpy() for x in (a_ref, m_ref, a, m))
             assert np.array_equal(a, a_ref)
-            assert np.all(np.abs(m - m_ref) <= 1e-12 * np.abs(m_ref))
+            assert np.array_equal(m, m_ref)
+            # the oracle: the returned row's time is the minimum, within the FP64 path's 1e-9
+            T = oracle.predict(F, Wm)
+            tmin = T.min(axis=0)
+            assert np.all(np.abs(m - tmin) <= 1e-9 * np.abs(tmin))
+            assert np.all(np.abs(T[a, np.arange(M)] - tmin) <= 1e-9 * np.abs(tmin))
+        # no rows: every model gets row -1 and time +inf
+        a0 = torch.zeros(3, dtype=torch.int64, device=dev)
+        m0 = torch.zeros(3, dtype=torch.float64, device=dev)
+        B.predict_argmin_static(torch.zeros((0, 32), dtype=torch.int64, device=dev), dW[:3], a0, m0)
+        torch.cuda.synchronize()
+        assert (a0.cpu().numpy() == -1).all() and np.isinf(m0.cpu().numpy()).all()
         with pytest.raises(B.PMError) as e:     # more models than the fixed array is sized for
             B.predict_argmin_static(dF, torch.zeros((65, 32), dtype=torch.float64, device=dev), a_ref, m_ref)
         assert e.value.code == -1
