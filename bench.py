@@ -303,7 +303,7 @@ def run_ours(args):
     measured_ops = B.pmm_int_issue_rate()          # integer multiply-add / xor / add chains, every lane
     traffic = _profile_traffic("eval_predict_topk_coupled_10000x4096.md" if coupled else
                                "eval_predict_topk_batched_10000x4096.md",
-                               ("eval.cu", "eval_common.cuh", "pm_table.h", "plan.cpp"))
+                               ("rank.cu", "eval_common.cuh", "kernels.h", "plan.cpp"))
 
     if rank == 0:
         line = {
@@ -315,7 +315,9 @@ def run_ours(args):
                        "distinct_variants": bp.n_distinct,
                        "points_per_template": args.points, "evals_per_step": evals, "topk": 16,
                        "l2": "flushed (256 MB write) before every timed step",
-                       "launch": {"warps_per_cta": info["nw"], "ctas": info["grid"], "units": info["units"]},
+                       "launch": {"warps_per_cta": info["nw"], "ctas": info["grid"], "units": info["units"],
+                                  "ranking_groups": info["groups"], "slice": info["slice"] or None,
+                                  "tuned": info["tuned"]},
                        "timed_region_wall_ms": wall * 1e3},
             "e2e": {"value": evals * ws / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(bp.points.nbytes),
@@ -323,7 +325,7 @@ def run_ours(args):
             "gpu_launches": 2 * args.steps,   # per step: the weight prepass and the fused ranking kernel
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T lane-ops/s", "frac": achieved / peak_ops, "traffic": traffic,
-                         "kernel": "k_eval_predict_topk",
+                         "kernel": "k_rank",
                          "ops_per_eval": info["work_per_eval"],
                          "peak_note": f"{sms} SMs x 128 lanes x {max_mhz:.0f} MHz (issue bound, derived)",
                          "measured_peak": measured_ops / 1e12, "frac_of_measured": achieved / measured_ops,

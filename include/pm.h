@@ -132,9 +132,10 @@ pm_status pm_eval_counts(pm_ctx *ctx, const int32_t *h_table_ids, int32_t n_tabl
 /* ------------------------------------------------------------------ prediction (Sec. 2) */
 
 /* d_T[r][m] = sum_i d_F[r][i] * d_W[m][i]   (F int64 [R][k], W fp64 [M][k], T fp64 [R][M]).
- * precision PM_PREC_FP64: weights rounded to 58-bit fixed point per model, products and
- *   sums exact in 128 bits: error <= 2^-59 (max_i|W_mi| / min_i|W_mi|) sum_i |F_ri W_mi|
- *   plus 2^-56 |T|;
+ * precision PM_PREC_FP64: weights rounded to fixed point per model (W = round(w 2^E),
+ *   E the largest with sum_i |W_i| <= 2^62), products and sums exact in 128 bits for
+ *   any int64 F: error <= 2^-62 (sum_i|W_mi| / min_i|W_mi|) sum_i |F_ri W_mi| plus
+ *   2^-56 |T|, e.g. 4e-11 of sum_i |F_ri W_mi| for weights spread like Table 2's;
  * PM_PREC_BF16X3: <= ~1e-6 of the same (tensor cores, power-of-two column scaling);
  *   needs k == 32, M <= 64 and d_F 16-byte aligned (else PM_ERR_INVALID_ARG);
  * PM_PREC_NATIVE_FP64: double FMA. */
@@ -192,7 +193,10 @@ pm_status pm_predict_argmin_static(const int64_t *d_F, int64_t R, int32_t k, con
  * unused parameter slots ignored).  Every (variant, point) pair is evaluated,
  * predicted with the weights d_w (fp64 [32], PM_LAYOUT_32 tables) to FP64
  * accuracy, and the topk (<= 16) smallest predicted times per point are
- * returned, ordered by (time, variant index within the template):
+ * returned, ordered by (time, variant index within the template).  The ranking is
+ * on the exact fixed-point sums (weights as in pm_predict); a returned time keeps
+ * 40 bits of its sum's mantissa (rounded toward -infinity), so its error is at most 2^-40 |t|
+ * plus pm_predict's weight-rounding bound:
  * d_top_idx int32 [total][topk] (-1 if fewer variants), d_top_t fp64 [total][topk].
  * One persistent launch; the host-side schedule is built once per distinct
  * argument set and cached. */
@@ -209,10 +213,18 @@ pm_status pm_eval_predict_topk(pm_ctx *ctx, const int32_t *h_tables, const int32
 pm_status pm_tune(pm_ctx *ctx, int32_t enable, const char *cache_path);
 
 /* Schedule of a pm_eval_predict_topk argument set (built and cached if new):
- * h_out[0] work units, [1] (variant, point) evaluations, [2] estimated integer
- * operations per evaluation x 1000, [3] warps per CTA, [4] CTAs, [5] tuned. */
+ * h_out[0] work units, [1] (variant, point) evaluations, [2] algorithmic integer
+ * operations per evaluation x 1000, [3] warps per CTA, [4] CTAs, [5] tuned,
+ * [6] ranking groups (variants of one template sharing one basis of values),
+ * [7] the tuned slice size (at most this many variants per group; 0 = unlimited).
+ * h_out: host int64 [8]. */
 pm_status pm_plan_info(pm_ctx *ctx, const int32_t *h_tables, const int32_t *h_var_off, int32_t n_templates,
                        const int64_t *h_pt_off, int64_t *h_out);
+/* The autotuner's measurements for an argument set already planned and tuned:
+ * rows (slice size, warps per CTA, CTAs per SM, ms per launch), h_out fp64 [cap][4].
+ * Returns the number of rows (which may exceed cap), 0 if not tuned, -1 on bad args. */
+int32_t pm_plan_tune_log(pm_ctx *ctx, const int32_t *h_tables, const int32_t *h_var_off, int32_t n_templates,
+                         const int64_t *h_pt_off, double *h_out, int32_t cap);
 
 /* ------------------------------------------------------------------ fit (Sec. 4.3) */
 

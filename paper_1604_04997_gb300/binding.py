@@ -95,6 +95,7 @@ def lib():
             "pm_eval_predict_topk": ([vp, vp, vp, i32, vp, vp, vp, i32, vp, vp, vp], i32),
             "pm_tune": ([vp, i32, ctypes.c_char_p], i32),
             "pm_plan_info": ([vp, vp, vp, i32, vp, vp], i32),
+            "pm_plan_tune_log": ([vp, vp, vp, i32, vp, vp, i32], i32),
             "pm_fit_weights": ([vp, vp, i64, i32, vp, i32, i32, i32, i32, vp, ctypes.POINTER(FitReport), vp], i32),
             "pm_serve_set_weights": ([vp, vp, i32], i32),
             "pm_serve_start": ([vp, ctypes.POINTER(ServeConfig)], i32),
@@ -120,7 +121,7 @@ def exported_symbols() -> Sequence[str]:
     return ("pm_create", "pm_destroy", "pm_last_error", "pm_sync_status", "pm_compile_counts", "pm_table_image",
             "pm_eval_counts", "pm_predict", "pm_predict_argmin", "pm_predict_argmin_static",
             "pm_eval_predict_topk", "pm_tune",
-            "pm_plan_info", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
+            "pm_plan_info", "pm_plan_tune_log", "pm_fit_weights", "pm_serve_set_weights", "pm_serve_start", "pm_serve_submit",
             "pm_serve_poll", "pm_serve_stats", "pm_serve_stop", "pmm_time", "pmm_int_issue_rate", "pm_table_load",
             "pm_predict_topk")
 
@@ -237,11 +238,21 @@ class Context:
         t = np.ascontiguousarray(tables, dtype=np.int32)
         vo = np.ascontiguousarray(var_off, dtype=np.int32)
         po = np.ascontiguousarray(pt_off, dtype=np.int64)
-        out = np.zeros(6, dtype=np.int64)
+        out = np.zeros(8, dtype=np.int64)
         _check(lib().pm_plan_info(self.h, t.ctypes.data, vo.ctypes.data, len(vo) - 1, po.ctypes.data,
                                   out.ctypes.data))
         return dict(units=int(out[0]), evals=int(out[1]), work_per_eval=out[2] / 1000.0, nw=int(out[3]),
-                    grid=int(out[4]), tuned=bool(out[5]))
+                    grid=int(out[4]), tuned=bool(out[5]), groups=int(out[6]), slice=int(out[7]))
+
+    def plan_tune_log(self, tables, var_off, pt_off) -> list:
+        """The autotuner's candidates: (slice, warps per CTA, CTAs per SM, ms)."""
+        t = np.ascontiguousarray(tables, dtype=np.int32)
+        vo = np.ascontiguousarray(var_off, dtype=np.int32)
+        po = np.ascontiguousarray(pt_off, dtype=np.int64)
+        out = np.zeros((64, 4), dtype=np.float64)
+        n = lib().pm_plan_tune_log(self.h, t.ctypes.data, vo.ctypes.data, len(vo) - 1, po.ctypes.data,
+                                   out.ctypes.data, 64)
+        return [tuple(r) for r in out[:max(0, min(n, 64))]]
 
     # -- fit
     def fit_weights(self, F, T, W_out, objective=FIT_RELATIVE, precision=PREC_BF16X3, refine_steps=3, stream=None):

@@ -78,6 +78,7 @@ extern "C" void pm_destroy(pm_ctx *c) {
     for (auto &kv : c->plans) {
       if (kv.second->graph_exec) cudaGraphExecDestroy(kv.second->graph_exec);
       for (void *p : kv.second->dev) cudaFree(p);
+      delete kv.second;
     }
     cudaFree(c->arena);
     cudaFree(c->d_status);
@@ -380,7 +381,7 @@ extern "C" pm_status pm_eval_predict_topk(pm_ctx *c, const int32_t *tables, cons
   Plan *plan = nullptr;
   pm_status s = ctx_plan_k2(c, tables, var_off, n_templates, pt_off, &plan);
   if (s) return s;
-  return ctx_run_k2(c, plan, d_points, d_w, topk, d_top_idx, d_top_t, (cudaStream_t)stream);
+  return ctx_run_k2(c, plan, tables, var_off, pt_off, d_points, d_w, topk, d_top_idx, d_top_t, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------------------------- fit (Sec. 4.3)

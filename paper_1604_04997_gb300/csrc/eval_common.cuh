@@ -130,46 +130,55 @@ __device__ __forceinline__ bool point_in_box(const uint32_t *T, const int64_t *p
 }
 
 // ---- Exact fixed-point prediction on the integer pipes.
-// Weights become integers W = round(w * 2^E) (|W| < 2^56, one E per weight vector);
-// each exact count 0 <= v < 2^62 contributes v * W, so the sum S = sum_i v_i W_i is
-// exact and T = S * 2^-E differs from sum_i v_i w_i by at most 2^-(E+1) sum_i v_i,
-// i.e. <= 2^-57 (max|w| / min|w|) of sum_i |v_i w_i|.
-//
-// The products are formed from 28-bit limbs, v = v2 2^56 + v1 2^28 + v0 and
-// W = w1 2^28 + w0 (w1 signed), with one 32 x 32 -> 64 multiply-add per limb pair into
-// four 64-bit accumulators by power of 2^28 (each sums < 2^7 products below 2^56, so
-// none overflows); they are combined into 128 bits once per evaluation.
+// Weights become integers W = round(w * 2^E) with one E per weight vector, the largest
+// for which sum_i |W_i| <= 2^62 (weight_exponent).  Any counts |v_i| <= 2^63 then give
+// |sum_i v_i W_i| < 2^126, so the exact sum S = sum_i v_i W_i never wraps its 128 bits,
+// and T = S * 2^-E differs from sum_i v_i w_i by at most 2^-(E+1) sum_i |v_i|, i.e. by
+// at most 2^-62 (sum_i |w_i| / min_i |w_i|) of sum_i |v_i w_i|: 4e-11 for weights with
+// the spread of the paper's fitted set (Table 2: 1.29e-4 s next to 3.91e-13 s).
 struct Acc128 {
   uint64_t lo, hi;  // two's complement
   __device__ __forceinline__ void zero() { lo = hi = 0; }
 };
 
-// Exact sum of count x weight products in four 64-bit limb accumulators.  A count
-// v (0 <= v < 2^62) is split into 28-bit limbs v0, v1 and the top bits v2; a weight
-// W = w.y 2^28 + w.x (w.x in [0, 2^28), |w.y| < 2^28).  Each partial product is one
-// 32x32 -> 64-bit multiply-add; with at most 34 terms no accumulator overflows.
+// A fixed-point weight W (|W| <= 2^62) as three limbs: W = w2 2^56 + w1 2^28 + w0 with
+// w0, w1 in [0, 2^28) and w2 signed (|w2| <= 2^6).
+struct Limbs3 { uint32_t w0, w1; int32_t w2; };
+__host__ __device__ __forceinline__ Limbs3 to_limbs3(int64_t W) {
+  return Limbs3{(uint32_t)(W & 0x0FFFFFFF), (uint32_t)((W >> 28) & 0x0FFFFFFF), (int32_t)(W >> 56)};
+}
+
+// Exact sum of count x weight products in five 64-bit limb accumulators.  A count
+// v (0 <= v < 2^62) is split into 28-bit limbs v0, v1 and the top bits v2 (< 2^6);
+// each limb pair is one 32 x 32 -> 64-bit multiply-add into the accumulator of its
+// power of 2^28.  Every partial product is below 2^56 in magnitude, at most three
+// meet in one accumulator per term, so 34 terms never overflow.
 struct LimbAcc {
   uint64_t l0;
-  int64_t l1, l2, l3;
-  __device__ __forceinline__ void zero() { l0 = 0; l1 = l2 = l3 = 0; }
-  __device__ __forceinline__ void add(uint64_t v, uint2 w) {
+  int64_t l1, l2, l3, l4;
+  __device__ __forceinline__ void zero() { l0 = 0; l1 = l2 = l3 = l4 = 0; }
+  __device__ __forceinline__ void add(uint64_t v, Limbs3 w) {
     const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
     const uint32_t v0 = lo & 0x0FFFFFFFu;
     const uint32_t v1 = __funnelshift_r(lo, hi, 28) & 0x0FFFFFFFu;
     const uint32_t v2 = hi >> 24;
-    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l0) : "r"(v0), "r"(w.x));
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l1) : "r"(v0), "r"(w.y));
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l1) : "r"(v1), "r"(w.x));
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v1), "r"(w.y));
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v2), "r"(w.x));
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l3) : "r"(v2), "r"(w.y));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l0) : "r"(v0), "r"(w.w0));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l1) : "r"(v0), "r"(w.w1));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l1) : "r"(v1), "r"(w.w0));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v0), "r"(w.w2));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v1), "r"(w.w1));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l2) : "r"(v2), "r"(w.w0));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l3) : "r"(v1), "r"(w.w2));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(l3) : "r"(v2), "r"(w.w1));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(l4) : "r"(v2), "r"(w.w2));
   }
   __device__ __forceinline__ Acc128 sum() const {
-    // S = l0 + l1 2^28 + l2 2^56 + l3 2^84, in 128-bit two's complement
+    // S = l0 + l1 2^28 + l2 2^56 + l3 2^84 + l4 2^112 (mod 2^128, two's complement)
     const uint64_t a1 = (uint64_t)l1 << 28, a2 = (uint64_t)l2 << 56;
-    const uint64_t h1 = (uint64_t)(l1 >> 36), h2 = (uint64_t)(l2 >> 8), h3 = (uint64_t)l3 << 20;
+    const uint64_t h1 = (uint64_t)(l1 >> 36), h2 = (uint64_t)(l2 >> 8), h3 = (uint64_t)l3 << 20,
+                   h4 = (uint64_t)l4 << 48;
     uint64_t lo = l0 + a1;
-    uint64_t hi = h1 + h2 + h3 + (lo < a1 ? 1ull : 0ull);
+    uint64_t hi = h1 + h2 + h3 + h4 + (lo < a1 ? 1ull : 0ull);
     const uint64_t lo2 = lo + a2;
     hi += lo2 < a2 ? 1ull : 0ull;
     return Acc128{lo2, hi};
@@ -227,13 +236,17 @@ __device__ __forceinline__ double key_value(int64_t k, int E) {
   return neg ? -v : v;
 }
 
-// Fixed-point weights: W_i = round(w_i * 2^E) with max |W_i| in [2^55, 2^56).
+// Exponent E of the fixed-point weights W_i = round(w_i 2^E): the largest with
+// sum_i |w_i| 2^E <= 2^62 (the sum is rounded up by 2^-40 relative to cover its own
+// rounding), so that sum_i |W_i| <= 2^62 + k/2.  Every kernel that ranks or converts
+// with E calls this same serial loop, so all of them agree on E bit for bit.
 __device__ __forceinline__ int weight_exponent(const double *w, int k) {
-  double mx = 0;
-  for (int c = 0; c < k; c++) mx = fmax(mx, fabs(w[c]));
+  double s = 0;
+  for (int c = 0; c < k; c++) s += fabs(w[c]);
+  s *= 1.0 + 0x1p-40;
   int e = 0;
-  if (mx > 0) frexp(mx, &e);  // mx in [2^(e-1), 2^e)
-  return 56 - e;
+  if (s > 0) frexp(s, &e);  // s in [2^(e-1), 2^e)
+  return 62 - e;
 }
 
 }  // namespace pmd

@@ -12,35 +12,56 @@ enum StatusBits { ST_OUT_OF_BOX = 1, ST_BAD_TABLE = 2, ST_TIMEOUT = 4, ST_BAD_IN
 cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, int n_tables, const int64_t *points,
                                int64_t n_points, int P, int K, int64_t *out, int *status, cudaStream_t st);
 
-// K2 (eval.cu)
-constexpr int K2_MAX_SLICES = 16;
-struct K2Args {
-  const uint32_t *prog;        // K2 programs: table words followed by the weight image
-  const uint64_t *tab_off;     // [n_variants] word offset into prog | program words << 40
-  const int32_t *var_off;      // [n_templates+1] CSR into tab_off
-  const int32_t *tmpl_nparams; // [n_templates]
-  const int32_t *tmpl_slices;  // [n_templates] variant slices S per point chunk (<= K2_MAX_SLICES)
-  const int4 *tmpl_box;        // [n_templates][2] parameter box (lo, hi) shared by the template's tables
-  const int4 *chunks;          // [n_chunks] (template, first point, point count <= 256, first partial slot)
-  const int4 *units;           // [n_units] (chunk, slice, first variant, end variant), schedule order
+// Fused ranking (rank.cu).  A ranking group's image (32-bit words, 16-byte aligned
+// sections; built by plan.cpp):
+//   header [HDR_WORDS]: basis entries B, dependency levels, conditions, image words,
+//     the end of each level (entries are ordered by level), section offsets;
+//   basis definitions, 8 words each: [a0 a1 a2 a3 | b c magic kind] for an atom
+//     floor((a . n + b) / c) (kind = 2 | shift << 8 | numerator-may-be-negative << 16),
+//     [i j . . | . . . kind] for a parameter (kind 0, i = its index), the constant
+//     (kind 1) or a product of entries i and j (kind 3);
+//   conditions (at most 64): [n_terms, const_lo, const_hi, (entry, coef_lo, coef_hi) *
+//     n_terms], bit q of a point's two mask words when const + sum coef * value >= 0:
+//     the tables' piece conditions and the signs of undecided post-op differences A - B;
+//   programs (one per distinct table), as records of four words:
+//     condition node [1 | n << 8 | piece records << 16, condition ids 0-4 (6 bits each),
+//       ids 5-9, LUT offset]: the LUT byte of the n condition bits names a piece record;
+//     sub node [2 | n << 8, condition ids, children, 0]: child record = children + 4 * bits;
+//     leaf [n64 << 8 | n32 << 16 | nwide << 24, term records, denominator block or 0,
+//       constant present]: term records are the constant's 128-bit weight (if present),
+//       then [w0 w1 w2 entry] per term with a 96-bit weight (n64 terms whose basis value
+//       may leave [0, 2^32), then n32 terms), then [w0 w1 w2 w3][entry 0 0 0] per term
+//       with a 128-bit weight; the denominator block is [shift, 0, 0, 0, d^-1 mod 2^128];
+//   the variant map: each variant's root record offset (16 bits).
+struct RankLayout {
+  static constexpr int POINTS = 32;   // points per work unit: one per lane
+  enum { H_B = 0, H_NLEV = 1, H_NCOND = 2, H_WORDS = 3, H_LEVEL_END = 4, H_OFF_BASIS = 12, H_OFF_COND = 13,
+         H_OFF_VARMAP = 14, HDR_WORDS = 16 };
+};
+struct RankArgs {
+  const uint32_t *img;         // every group's image (weights filled per call)
+  const int4 *groups;          // [n_groups][2]: (image word offset, image words, first variant
+                               //   (template-relative), variants), (template, group index in template, 0, 0)
+  const int4 *tmpl;            // [T][3]: (parameters, groups, 0, 0), box lo, box hi
+  const int4 *chunks;          // [n_chunks] (template, first point, point count <= 32, first partial slot or -1)
+  const int2 *units;           // [n_units] (chunk, group or -1 for a template without variants), schedule order
   int n_units;
   int *unit_counter;           // reset to 0 before each launch
-  int *chunk_count;            // [n_chunks] slices finished, reset to 0 before each launch
-  int64_t *part_k;             // [slots][16][points per chunk] partial lists (packed entries) of chunks with S > 1
+  int *chunk_count;            // [n_chunks] groups finished, reset to 0 before each launch
+  int64_t *part_k;             // [slots][16][32] partial lists of chunks with several groups
   const int64_t *points;       // [total][4]
   const double *w;             // [32]
   int topk;
   int32_t *top_idx;            // [total][topk]
   double *top_t;               // [total][topk]
   int *status;
+  int img_words, basis_cap;    // shared-memory layout: the largest image and basis of the plan
 };
-cudaError_t launch_eval_predict_topk(const K2Args &args, int nw, int grid, cudaStream_t st);
-// fill the 128-bit weights of the K2 programs from w (fp64 [32])
+cudaError_t launch_rank(const RankArgs &args, int nw, int grid, cudaStream_t st);
+int rank_max_blocks_per_sm(int nw, int img_words, int basis_cap);
+// fill the 128-bit term weights of the ranking programs from w (fp64 [32])
 cudaError_t launch_k2_weights(uint32_t *prog, const uint4 *targets, const uint4 *contrib, int n_targets,
                               const double *w, cudaStream_t st);
-int k2_max_blocks_per_sm(int nw);
-int k2_table_words();
-int k2_points_per_cta(int nw);
 
 // predict.cu
 struct ArgPart { double t; int64_t r; };   // a partial per-model minimum: time and row

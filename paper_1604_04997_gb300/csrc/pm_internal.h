@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <map>
 #include <mutex>
 #include <string>
@@ -14,24 +15,25 @@ struct ServeState;
 // Cached schedule of one pm_eval_predict_topk argument set.
 struct Plan {
   std::vector<void *> dev;          // device allocations owned by the plan
-  const uint64_t *d_tab_off = nullptr;    // per variant: program word offset | program words << 40
-  uint32_t *d_prog = nullptr;             // K2 programs (tables + weight images) of the distinct tables
-  const uint4 *d_targets = nullptr;       // weight-fill recipe: (word, first contribution, count)
-  const uint4 *d_contrib = nullptr;       // contributions (column, -, coef lo, coef hi)
+  uint32_t *d_img = nullptr;        // ranking-group images (weights filled per call)
+  const uint4 *d_targets = nullptr; // weight-fill recipe: (word, first contribution, count)
+  const uint4 *d_contrib = nullptr; // contributions (column, -, coef lo, coef hi)
   int n_targets = 0;
-  const int32_t *d_var_off = nullptr;
-  const int32_t *d_nparams = nullptr;
-  const int32_t *d_slices = nullptr;
-  const int4 *d_box = nullptr;              // [T][2] parameter box per template
+  const int4 *d_groups = nullptr;
+  const int4 *d_tmpl = nullptr;
   const int4 *d_chunks = nullptr;
-  const int4 *d_units = nullptr;
+  const int2 *d_units = nullptr;
   int *d_counter = nullptr;
   int64_t *d_part_k = nullptr;
-  int n_units = 0, n_templates = 0, n_chunks = 0;
+  int n_units = 0, n_templates = 0, n_chunks = 0, n_groups = 0;
+  int img_words = 0, basis_cap = 1;  // the largest group image and basis (shared-memory layout)
+  int slice_max = 0;                 // at most this many variants per group
   int64_t total_points = 0, total_evals = 0;
-  double work_per_eval = 0;         // average (atoms + conditions + monomials) per evaluation
-  int nw = 8, grid = 0;             // launch shape (autotuned when enabled)
+  double work_per_eval = 0;          // algorithmic integer operations per evaluation
+  int nw = 8, grid = 0;              // launch shape (autotuned when enabled)
   bool tuned = false;
+  std::string key;
+  std::vector<std::array<double, 4>> tune_log;   // (slice, warps, CTAs per SM, ms) per candidate
   // CUDA graph of the last argument set
   cudaGraphExec_t graph_exec = nullptr;
   const void *g_key[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -70,7 +72,8 @@ pm_status ctx_scratch(pm_ctx *c, size_t bytes, void **d);
 pm_status ctx_table_offsets(pm_ctx *c, const int32_t *ids, int n, int *P, int *K, const int64_t **d_off);
 pm_status ctx_plan_k2(pm_ctx *c, const int32_t *tables, const int32_t *var_off, int n_templates,
                       const int64_t *pt_off, Plan **out);
-pm_status ctx_run_k2(pm_ctx *c, Plan *p, const int64_t *d_points, const double *d_w, int topk, int32_t *d_idx,
-                     double *d_t, cudaStream_t st);
+pm_status ctx_run_k2(pm_ctx *c, Plan *p, const int32_t *tables, const int32_t *var_off, const int64_t *pt_off,
+                     const int64_t *d_points, const double *d_w, int topk, int32_t *d_idx, double *d_t,
+                     cudaStream_t st);
 pm_status pm_predict_bf16x3(pm_ctx *c, const int64_t *F, int64_t R, int k, const double *W, int M, double *T,
                             int64_t *arg, double *mn, void *stream);

@@ -15,27 +15,18 @@ namespace pmd {
 constexpr int SV_THREADS = 128;      // candidates per k_serve_eval CTA
 constexpr int SV_TOPK_THREADS = 256;
 
-// Per-model fixed-point weights W_i = round(w_i 2^E) as 28-bit limb pairs, computed by
-// warp 0 (lane i holds weight i); every CTA of a batch derives the same values.
-__device__ __forceinline__ void load_model_limbs(const double *w, uint2 *s_w, int *s_E) {
-  const int lane = threadIdx.x & 31;
-  if (threadIdx.x < 32) {
-    const double x = w[lane];
-    double mx = fabs(x);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    int e = 0;
-    if (mx > 0) frexp(mx, &e);
-    const int E = 56 - e;
-    const int64_t W = llrint(ldexp(x, E));   // |W| < 2^56
-    s_w[lane] = make_uint2((uint32_t)(W & 0x0FFFFFFF), (uint32_t)(int32_t)(W >> 28));
-    if (lane == 0) *s_E = E;
-  }
+// Per-model fixed-point weights W_i = round(w_i 2^E) (sum |W_i| <= 2^62) as 28-bit limb
+// triples; thread 0 finds E with the same serial loop in every CTA of a batch, so every
+// CTA derives the same values.
+__device__ __forceinline__ void load_model_limbs(const double *w, Limbs3 *s_w, int *s_E) {
+  if (threadIdx.x == 0) *s_E = weight_exponent(w, 32);
+  __syncthreads();
+  if (threadIdx.x < 32) s_w[threadIdx.x] = to_limbs3(llrint(ldexp(w[threadIdx.x], *s_E)));
 }
 
 __global__ void __launch_bounds__(SV_THREADS) k_serve_eval(ServeArgs a) {
   __shared__ int64_t slots[pmt::MAX_SLOTS * SV_THREADS];
-  __shared__ uint2 s_w[32];
+  __shared__ Limbs3 s_w[32];
   __shared__ int s_E;
   const int2 b = a.blocks[blockIdx.x];
   const SQuery q = a.queries[b.x];
@@ -95,7 +86,7 @@ __device__ __forceinline__ bool pair_less(int64_t ka, int32_t ia, int64_t kb, in
 }
 
 __global__ void __launch_bounds__(SV_TOPK_THREADS) k_serve_topk(ServeArgs a) {
-  __shared__ uint2 s_w[32];
+  __shared__ Limbs3 s_w[32];
   __shared__ int s_E;
   __shared__ int64_t r_k[SV_TOPK_THREADS / 32];
   __shared__ int32_t r_i[SV_TOPK_THREADS / 32];
