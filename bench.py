@@ -199,6 +199,95 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _plain_form(ctx, bp, d_w, dev, stream, fused_idx, reps=2):
+    """The plain per-call form of the same (variant, point) pairs: per template, one
+    pm_eval_counts into int64 [variants][points][32], then one pm_predict_topk of the
+    FP64-accurate times with the per-point row list (group p = the rows v * n + p).
+    Returns timings (ms per pass over all templates) and the share of points whose
+    top-16 variant list equals the fused launch's."""
+    import numpy as np
+    import torch
+    from paper_1604_04997_gb300 import workloads as W
+    calls = []
+    for t in range(len(bp.templates)):
+        ids = bp.tables[bp.var_off[t]:bp.var_off[t + 1]]
+        nv, n = len(ids), int(bp.pt_off[t + 1] - bp.pt_off[t])
+        if nv == 0 or n == 0:
+            continue
+        P = len(W.TEMPLATE_PARAMS[bp.templates[t]])
+        pts = torch.from_numpy(np.ascontiguousarray(bp.points[bp.pt_off[t]:bp.pt_off[t + 1], :P])).to(dev)
+        F = torch.empty((nv, n, 32), dtype=torch.int64, device=dev)
+        rows = torch.from_numpy((np.arange(nv, dtype=np.int64)[None, :] * n +
+                                 np.arange(n, dtype=np.int64)[:, None]).reshape(-1)).to(dev)
+        seg = np.arange(n + 1, dtype=np.int64) * nv
+        ti = torch.empty(n * 16, dtype=torch.int64, device=dev)
+        tt = torch.empty(n * 16, dtype=torch.float64, device=dev)
+        calls.append((t, ids, pts, F, rows, seg, ti, tt, n))
+    W1 = d_w.view(1, 32)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in calls]
+
+    def run(timed):
+        for (t, ids, pts, F, rows, seg, ti, tt, n), e in zip(calls, ev):
+            if timed:
+                e[0].record(stream)
+            ctx.eval_counts(ids, pts, F, stream=stream)
+            if timed:
+                e[1].record(stream)
+            ctx.predict_topk(F.view(-1, 32), W1, seg, 16, ti, tt, rows=rows, stream=stream)
+            if timed:
+                e[2].record(stream)
+
+    with torch.cuda.stream(stream):
+        run(False)
+    torch.cuda.synchronize()
+    eval_ms = rank_ms = 0.0
+    for _ in range(reps):
+        with torch.cuda.stream(stream):
+            run(True)
+        torch.cuda.synchronize()
+        eval_ms += sum(e[0].elapsed_time(e[1]) for e in ev) / reps
+        rank_ms += sum(e[1].elapsed_time(e[2]) for e in ev) / reps
+    ctx.sync_status(stream)
+    same = total = 0
+    fi = fused_idx.cpu().numpy()
+    for t, ids, pts, F, rows, seg, ti, tt, n in calls:
+        plain_v = (ti.cpu().numpy().reshape(n, 16) // n).astype(np.int64)
+        fv = fi[bp.pt_off[t]:bp.pt_off[t + 1]].astype(np.int64)
+        same += int((plain_v == fv).all(axis=1).sum())
+        total += n
+    del calls
+    torch.cuda.empty_cache()
+    return {"ms": eval_ms + rank_ms, "eval_counts_ms": eval_ms, "predict_topk_ms": rank_ms,
+            "points_with_identical_top16": same / max(1, total),
+            "note": "per template: pm_eval_counts (all 32 counts to HBM, 10.5 GB) then pm_predict_topk "
+                    "(PM_PREC_FP64, one model, per-point row lists); pm_predict_topk lays models on lanes "
+                    "(up to 64 per tile), so one model uses 1/64 of its product lanes"}
+
+
+def _serve_summary(ctx, bp, n_points, n_q):
+    """A short autotuner query stream on the batched workload's tables and points:
+    Poisson arrivals at 2,000 queries/s (1-50,000 candidates each, log-uniform), one of
+    64 resident models per query, top-16 per query, host buffers in and out; then the
+    first 200 of the same queries served one at a time."""
+    from paper_1604_04997_gb300 import tuning
+    from paper_1604_04997_gb300 import workloads as W
+    ctx.serve_set_weights(W.draw_weights(32, 64, 4))
+    nv = [int(bp.var_off[t + 1] - bp.var_off[t]) for t in range(len(bp.templates))]
+    qs = W.draw_queries(n_q, 2000.0, nv, n_points, 64, 9, 50000)
+    arrays = [tuning.query_arrays(bp, q) for q in qs]
+    wall, st = _serve_stream(ctx, bp, qs, arrays, 200)
+    n1 = min(200, n_q)
+    wall1, st1 = _serve_stream(ctx, bp, qs[:n1], arrays[:n1], 0, sync=True)
+    cand = sum(len(q.variant) for q in qs)
+    cand1 = sum(len(q.variant) for q in qs[:n1])
+    return {"queries": n_q, "rate_per_s": 2000.0, "batch_interval_us": 200, "p50_us": round(st["p50_us"], 1),
+            "p99_us": round(st["p99_us"], 1), "max_us": round(st["max_us"], 1),
+            "served_evals_per_s": cand / wall, "offered_evals_per_s": cand / qs[-1].arrival_s,
+            "queries_per_batch": round(st["n_queries"] / max(1, st["n_batches"]), 2),
+            "one_at_a_time_evals_per_s": cand1 / wall1, "one_at_a_time_p50_us": round(st1["p50_us"], 1),
+            "latency_note": "submit to results in the caller's host buffers, measured in the library"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -219,7 +308,7 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     ctx = B.Context(local)
-    ctx.tune(not args.no_tune, None)
+    ctx.tune(not args.no_tune, args.tune_cache)
     # weak scaling: every rank ranks its own point batch (independent units, no exchange)
     coupled = args.workload == "coupled"
     bp = tuning.build(ctx, args.variants, args.points, point_seed=sharding.rank_point_seed(3, rank),
@@ -291,6 +380,12 @@ def run_ours(args):
 
     evals = bp.total_evals
     value = evals * ws / (ms / 1e3)
+    plain = serve = None
+    if not args.no_plain:
+        plain = _plain_form(ctx, bp, d_w, dev, stream, idx)
+        plain["vs_plain"] = plain["ms"] / ms
+    if not args.no_serve and rank == 0:
+        serve = _serve_summary(ctx, bp, args.points, args.serve_queries)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -318,7 +413,9 @@ def run_ours(args):
                        "launch": {"warps_per_cta": info["nw"], "ctas": info["grid"], "units": info["units"],
                                   "ranking_groups": info["groups"], "slice": info["slice"] or None,
                                   "tuned": info["tuned"]},
-                       "timed_region_wall_ms": wall * 1e3},
+                       "timed_region_wall_ms": wall * 1e3,
+                       "plain_form": plain, "vs_plain": plain["vs_plain"] if plain else None,
+                       "serve": serve},
             "e2e": {"value": evals * ws / (e2e_ms / 1e3), "unit": UNIT,
                     "h2d_bytes_per_step": int(bp.points.nbytes),
                     "d2h_bytes_per_step": int(n * 16 * (4 + 8))},
@@ -498,15 +595,15 @@ def run_other(args):
         gram_flops = 2.0 * 32 * 32 * R * M          # the 64 Gram matrices' useful flops
         line = dict(base, metric="weight fits/s (200,000 rows x 32 features, 64 models, 3 refinement steps)",
                     value=M / (ms / 1e3), unit="model fits/s", ms_per_step=ms, higher_is_better=True,
-                    dtype="Gram exact on tcgen05 from bf16 digits (47-bit fixed point), FP64 Cholesky, "
-                          "exact residual products",
+                    dtype="Gram on tcgen05 from three bf16 terms of A, fp32 accumulation per 4096-row chunk "
+                          "(exact bf16-digit Gram if refinement stalls), FP64 Cholesky, exact residual products",
                     config={"workload": "200,000 x 32 int64 features, 64 device models, relative objective",
                             "float_float_gram_ms_per_step": ms_ff},
                     roofline={"bound": "tensor", "achieved": gram_flops / (ms / 1e3) / 1e12, "peak": peak_tc,
                               "unit": "TFLOP/s", "frac": gram_flops / (ms / 1e3) / 1e12 / peak_tc, "traffic": None,
                               "kernel": "pm_fit_weights (whole call; the Gram kernel is a third of it)",
-                              "note": "useful Gram flops 2 k^2 R M over the whole fit; the digit split executes "
-                                      "49 digit-pair products per useful product on the tensor pipe"},
+                              "note": "useful Gram flops 2 k^2 R M over the whole fit; the three-term split "
+                                      "executes 9 bf16 term-pair products (one 128 x 96 MMA tile) per useful product"},
                     clocks=ck, gpu_launches=None)
     print(json.dumps(line))
     ctx.close()
@@ -656,10 +753,14 @@ def main():
     ap.add_argument("--ref-step-s", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="use the default launch shape")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of tuned schedules: read if it holds this workload, else written")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "eval", "predict", "fit", "serve", "calibrate", "coupled"])
     ap.add_argument("--calib-out", default=None, help="write the full calibration result (JSON) here")
     ap.add_argument("--serve-queries", type=int, default=1000)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain per-call form")
+    ap.add_argument("--no-serve", action="store_true", help="skip the short serving stream")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

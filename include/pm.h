@@ -240,12 +240,16 @@ typedef struct {
 
 /* Fit M weight vectors at once: d_F int64 [R][k], d_T fp64 [R][M] (measured
  * times > 0), d_W_out fp64 [M][k], h_report [M] (host).  Each column of F is
- * scaled by a power of two; the Gram matrices A^T A are formed exactly from a 47-bit
- * fixed-point image of A split into seven bf16 digits, on the tensor cores with FP32
- * accumulation that stays exact (precision PM_PREC_BF16X3), or with float-float
- * products and compensated FP32 sums (PM_PREC_FP64; about 2^-44 relative);
- * the k x k systems are solved by FP64 Cholesky and refined with FP64 residuals
- * (refine_steps, e.g. 3).  Synchronises `stream` to fill h_report.
+ * scaled by a power of two; the Gram matrices A^T A are formed on the tensor cores
+ * from three bf16 terms of every entry (24 significant bits) with FP32 accumulation
+ * (precision PM_PREC_BF16X3), or with float-float products and compensated FP32 sums
+ * (PM_PREC_FP64; about 2^-44 relative); the k x k systems are solved by FP64
+ * Cholesky and refined with residuals from exact products (refine_steps, e.g. 3),
+ * which recovers the accuracy of the three-term Gram when cond(A)^2 2^-24 is well
+ * below one.  If after the steps some model's last correction is still above 1e-10
+ * of its weights, or its factor lost rank, the PM_PREC_BF16X3 fit is repeated with a
+ * Gram formed exactly on the tensor cores (a 47-bit fixed-point image of A in seven
+ * bf16 digits).  Synchronises `stream` to fill h_report.
  * Returns PM_OK or PM_WARN_RANK_DEFICIENT. */
 pm_status pm_fit_weights(pm_ctx *ctx, const int64_t *d_F, int64_t R, int32_t k, const double *d_T,
                          int32_t M, int32_t objective, int32_t precision, int32_t refine_steps,

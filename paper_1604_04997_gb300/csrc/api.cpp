@@ -410,10 +410,22 @@ extern "C" pm_status pm_fit_weights(pm_ctx *c, const int64_t *F, int64_t R, int3
   h.rr = h.upd + 64;
   h.bb = h.rr + 64;
   cudaStream_t st = (cudaStream_t)stream;
-  CU(pmd::launch_fit(F, R, k, T, M, objective, precision, refine_steps, scr, W_out, &h, c->d_status, st));
-  CU(cudaStreamSynchronize(st));
-  s = pm_sync_status(c, stream);
-  if (s) return s;
+  // PM_PREC_BF16X3: the Gram from three bf16 terms first; refinement with exact residuals
+  // makes it accurate when cond(G) 2^-24 is well below one.  If some model's last
+  // correction is still large (or its factor reports a rank drop the exact Gram may not
+  // have), the fit is repeated with the exact digit Gram.
+  int gram = precision == PM_PREC_BF16X3 ? 1 : 0;
+  for (;;) {
+    CU(pmd::launch_fit(F, R, k, T, M, objective, gram, refine_steps, scr, W_out, &h, c->d_status, st));
+    CU(cudaStreamSynchronize(st));
+    s = pm_sync_status(c, stream);
+    if (s) return s;
+    if (gram != 1 || refine_steps == 0) break;
+    bool converged = true;
+    for (int m = 0; m < M; m++) converged &= h.upd[m] < 1e-10 && h.info[m * 4 + 2] == 0;
+    if (converged) break;
+    gram = 2;
+  }
   bool deficient = false;
   for (int m = 0; m < M; m++) {
     pm_fit_report &r = rep[m];

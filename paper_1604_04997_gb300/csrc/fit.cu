@@ -6,8 +6,10 @@
 // [1/2, 1).  The normal equations A^T A x = A^T b (b = 1, or b = t_m) are formed
 // in float-float arithmetic on the FP32 pipes (entries split exactly into hi + lo
 // pairs, error-free products by FMA, compensated sums; about 2^-44 relative) per row
-// chunk, chunks summed in FP64 (precision PM_PREC_FP64), or exactly on the tensor
-// cores from bf16 digits of a 47-bit fixed-point image of A (PM_PREC_BF16X3, gram_tc.cu);
+// chunk, chunks summed in FP64 (precision PM_PREC_FP64), or on the tensor cores from
+// three bf16 terms of A with FP32 accumulation (PM_PREC_BF16X3), or exactly from bf16
+// digits of a 47-bit fixed-point image of A when refinement on the three-term Gram
+// does not converge (gram_tc.cu);
 // the k x k systems are factored by FP64 Cholesky.  Iterative refinement then
 // recovers the accuracy: r = b - A x is formed from the exact fixed-point product
 // F w (the prediction kernel's arithmetic) and an FP64 division, the correction
@@ -422,7 +424,7 @@ static char *carve(char *&p, size_t bytes) {
   return r;
 }
 
-cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int precision,
+cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int gram,
                        int steps, void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st) {
   char *p = (char *)scratch;
   unsigned long long *cmax = (unsigned long long *)carve(p, 256);
@@ -461,10 +463,11 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   const int groups = (M + ATQ_MODELS - 1) / ATQ_MODELS;
   const int achunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / groups + 1, (R + 255) / 256));
   const int64_t arpc = (R + achunks - 1) / achunks;
-  if (precision == PM_PREC_BF16X3) {
-    // Gram on the tensor cores (exact digits of the 47-bit fixed-point A); right-hand
-    // side A^T b = U^T (rowfactor b) with the float-float product kernel
-    if ((e = launch_gram_tc(U, Ul, rf, R, k, M, amax, G, status, st)) != cudaSuccess) return e;
+  if (gram != 0) {
+    // Gram on the tensor cores (three bf16 terms of A, or the exact digits of its 47-bit
+    // fixed-point image); right-hand side A^T b = U^T (rowfactor b) with the
+    // float-float product kernel
+    if ((e = launch_gram_tc(U, Ul, rf, R, k, M, amax, G, gram == 2, status, st)) != cudaSuccess) return e;
     k_atq<<<dim3(achunks, groups), FIT_THREADS, 0, st>>>(U, Ul, objective == PM_FIT_RELATIVE ? rf : bt, R, k, M,
                                                          arpc, amax, rhs);
   } else {

@@ -16,6 +16,13 @@
 // The only error is the rounding of A to 47 bits (relative 2^-47 of the column's
 // largest entry), below the 2^-44 of the float-float path.
 //
+// Three-term mode (precision PM_PREC_BF16X3): every entry of A is instead split into
+// three bf16 terms, A ~ h + m + l (h = bf16(A), m = bf16(A - h), l = bf16(A - h - m):
+// 24 significant bits), at operand rows 32 q + c (q = 0, 1, 2; rows 96..127 zero); one
+// MMA (M = 128, N = 96) per K-step gives the nine term-pair sums in FP32, whose sum is
+// G to about 2^-24 relative per 4096-row chunk.  The fit's iterative refinement, with
+// exact residuals, recovers full accuracy as long as cond(G) 2^-24 is well below 1.
+//
 // One CTA per SM (the two accumulators take 448 of the 512 TMEM columns), persistent
 // over (model, chunk) work items, 16 warps; 128-row stages are double-buffered so the
 // digits of stage s + 1 are written while the MMAs of stage s run, and each thread's
@@ -23,6 +30,8 @@
 // kernel records ST_TIMEOUT and stops.
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -34,20 +43,24 @@ namespace pmd {
 namespace {
 
 constexpr int GT_THREADS = 512;
-constexpr int GT_DIG = 7;                 // digits per entry
 constexpr int GT_COLS = 32;               // feature columns (padded)
-constexpr int GT_N = GT_DIG * GT_COLS;    // 224: MMA N
-constexpr int GT_MN = 256;                // operand rows (224 digits + zero padding)
 constexpr int GT_KS = 128;                // rows per stage (8 per warp): 8 MMA K-steps of 16
-constexpr int GT_CHUNK = 4096;            // rows per exact accumulation
+constexpr int GT_CHUNK = 4096;            // rows per accumulation in TMEM
 constexpr uint32_t GT_SBO = (GT_KS / 8) * 128;          // 2048 B between 8-row operand groups
-constexpr uint32_t GT_STAGE = GT_MN / 8 * GT_SBO;        // 64 KB per stage buffer
-constexpr uint32_t GT_CONTRIB = GT_DIG * GT_COLS * GT_COLS * 8;   // per-chunk partial sums
 constexpr unsigned long long GT_WAIT_NS = 2000000000ull;
 
-// instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, N = 224, M = 128
-constexpr uint32_t GT_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GT_N >> 3) << 17) |
-                              ((uint32_t)(128 >> 4) << 24);
+// the two modes: DIG terms per entry (7 exact digits, or 3 bf16 terms); operand rows
+// DIG * 32 (padded to MN); MMA N = DIG * 32; stage and TMEM sizes
+template <int DIG> struct GtMode {
+  static constexpr int N = DIG * GT_COLS;                            // 224 or 96
+  static constexpr int MN = DIG == 7 ? 256 : 128;                    // operand rows with padding
+  static constexpr uint32_t STAGE = MN / 8 * GT_SBO;                 // 64 KB or 32 KB per stage
+  static constexpr uint32_t CONTRIB = DIG * GT_COLS * GT_COLS * 8;   // per-chunk partial sums
+  static constexpr uint32_t TMEM_COLS = DIG == 7 ? 512 : 128;
+  // instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, N, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                                    ((uint32_t)(128 >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t gt_saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -61,11 +74,11 @@ __device__ __forceinline__ uint64_t gt_desc(uint32_t saddr) {
   return d;
 }
 
-__device__ __forceinline__ void gt_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+__device__ __forceinline__ void gt_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(GT_IDESC), "r"(accumulate));
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ bool gt_try(uint32_t addr, uint32_t parity) {
@@ -176,16 +189,34 @@ __device__ __forceinline__ void gt_digits(int64_t a, int (&d)[7]) {
   }
 }
 
+// the three bf16 terms of a float-float value x + y: h = bf16(x), m = bf16((x - h) + y),
+// l = bf16(that - m); returned as floats (exact in bf16)
+__device__ __forceinline__ void gt_split3(float x, float y, float (&t)[3]) {
+  const float h = __bfloat162float(__float2bfloat16_rn(x));
+  const float r = __fadd_rn(__fsub_rn(x, h), y);
+  const float m = __bfloat162float(__float2bfloat16_rn(r));
+  t[0] = h;
+  t[1] = m;
+  t[2] = __bfloat162float(__float2bfloat16_rn(__fsub_rn(r, m)));
+}
+
+// two floats exact in bf16 -> packed bf16 pair, the first in the low half
+__device__ __forceinline__ uint32_t gt_pack(float a, float b) {
+  return __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);
+}
+
 }  // namespace
 
+template <int DIG>
 __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restrict__ Uh, const float *__restrict__ Ul,
                                                            const float2 *__restrict__ rf, int64_t R, int k, int M,
                                                            const unsigned *__restrict__ amax, double *__restrict__ G,
                                                            int *status) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((128u - (gt_saddr(smem_raw) & 127u)) & 127u);
-  uint8_t *stage[2] = {smem, smem + GT_STAGE};
-  double *contrib = (double *)(smem + 2 * GT_STAGE);          // [q][c][c']
+  using Md = GtMode<DIG>;
+  uint8_t *stage[2] = {smem, smem + Md::STAGE};
+  double *contrib = (double *)(smem + 2 * Md::STAGE);         // [q][c][c']
   __shared__ __align__(8) uint64_t mbar[2];
   __shared__ uint32_t tmem_base;
 
@@ -193,8 +224,8 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
   const int64_t chunks = (R + GT_CHUNK - 1) / GT_CHUNK;
   const int64_t items = chunks * M;
 
-  // operand rows 224..255 stay zero
-  for (int i = tid; i < (int)(2 * GT_STAGE / 16); i += GT_THREADS) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
+  // the padding operand rows (224..255, or 96..127) stay zero
+  for (int i = tid; i < (int)(2 * Md::STAGE / 16); i += GT_THREADS) ((uint4 *)smem)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(gt_saddr(&mbar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(gt_saddr(&mbar[1])));
@@ -202,7 +233,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(gt_saddr(&tmem_base)),
-                 "r"(512));
+                 "r"(Md::TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
@@ -246,21 +277,36 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
         if (!gt_wait(gt_saddr(&mbar[sbuf]), waited[sbuf] & 1)) { aborted = true; break; }
         waited[sbuf]++;
       }
-      uint32_t pk[GT_DIG][4];
+      uint32_t pk[DIG][4];
+      if constexpr (DIG == 7) {
 #pragma unroll
-      for (int i = 0; i < 8; i += 2) {
-        int d0[GT_DIG], d1[GT_DIG];
-        {
+        for (int i = 0; i < 8; i += 2) {
+          int d0[DIG], d1[DIG];
+          {
+            const float2 v0 = gt_ffmul(uh[i], ul[i], uf[i].x, uf[i].y);
+            const float2 v1 = gt_ffmul(uh[i + 1], ul[i + 1], uf[i + 1].x, uf[i + 1].y);
+            gt_digits(gt_fix(v0.x, s_c) + gt_fix_lo(v0.y, s_c), d0);   // rows past the end hold zeros
+            gt_digits(gt_fix(v1.x, s_c) + gt_fix_lo(v1.y, s_c), d1);
+          }
+#pragma unroll
+          for (int q = 0; q < DIG; q++) pk[q][i >> 1] = gt_bf2(d0[q], d1[q]);
+        }
+      } else {
+        // A = (U hi + lo)(rowfactor hi + lo) 2^-f as a float-float, then its three bf16 terms
+        const float sc = __uint_as_float((uint32_t)(127 + s_c - 47) << 23);   // 2^-f, exact
+#pragma unroll
+        for (int i = 0; i < 8; i += 2) {
+          float t0[3], t1[3];
           const float2 v0 = gt_ffmul(uh[i], ul[i], uf[i].x, uf[i].y);
           const float2 v1 = gt_ffmul(uh[i + 1], ul[i + 1], uf[i + 1].x, uf[i + 1].y);
-          gt_digits(gt_fix(v0.x, s_c) + gt_fix_lo(v0.y, s_c), d0);   // rows past the end hold zeros
-          gt_digits(gt_fix(v1.x, s_c) + gt_fix_lo(v1.y, s_c), d1);
-        }
+          gt_split3(__fmul_rn(v0.x, sc), __fmul_rn(v0.y, sc), t0);
+          gt_split3(__fmul_rn(v1.x, sc), __fmul_rn(v1.y, sc), t1);
 #pragma unroll
-        for (int q = 0; q < GT_DIG; q++) pk[q][i >> 1] = gt_bf2(d0[q], d1[q]);
+          for (int q = 0; q < DIG; q++) pk[q][i >> 1] = gt_pack(t0[q], t1[q]);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < GT_DIG; q++) {
+      for (int q = 0; q < DIG; q++) {
         const int mn = q * GT_COLS + c;
         *(uint4 *)(stage[sbuf] + (mn >> 3) * GT_SBO + warp * 128 + (mn & 7) * 16) =
             make_uint4(pk[q][0], pk[q][1], pk[q][2], pk[q][3]);
@@ -275,8 +321,9 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
         for (int ks = 0; ks < GT_KS / 16; ks++) {
           const uint64_t b = gt_desc(base + ks * 256);
           const uint32_t acc = (st | ks) != 0;
-          gt_mma(tmem, gt_desc(base + ks * 256), b, acc);                  // rows 0..127
-          gt_mma(tmem + 256, gt_desc(base + 16 * GT_SBO + ks * 256), b, acc);   // rows 128..255
+          gt_mma(tmem, gt_desc(base + ks * 256), b, Md::IDESC, acc);                  // rows 0..127
+          if constexpr (DIG == 7)
+            gt_mma(tmem + 256, gt_desc(base + 16 * GT_SBO + ks * 256), b, Md::IDESC, acc);   // rows 128..255
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
             gt_saddr(&mbar[sbuf])));
@@ -294,28 +341,49 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
     }
     if (aborted) break;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
-    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of D1 (w % 8 < 4) or D2:
-    // operand row 32 q + c with q = w % 8 (D1) or 4 + w % 4 (D2), c = lane; warps w and
-    // w + 8 share the lanes and split the 8-column blocks
-    const int w8 = warp & 7, quarter = w8 & 3, q = w8 < 4 ? w8 : 4 + quarter;
-    const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (w8 < 4 ? 0u : 256u);
-    if (q < GT_DIG) {
+    if constexpr (DIG == 7) {
+      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 of D1 (w % 8 < 4) or D2:
+      // operand row 32 q + c with q = w % 8 (D1) or 4 + w % 4 (D2), c = lane; warps w and
+      // w + 8 share the lanes and split the 8-column blocks
+      const int w8 = warp & 7, quarter = w8 & 3, q = w8 < 4 ? w8 : 4 + quarter;
+      const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (w8 < 4 ? 0u : 256u);
+      if (q < DIG) {
 #pragma unroll 1
-      for (int cb = warp < 8 ? 0 : 2; cb < (warp < 8 ? 2 : 4); cb++) {
-        float v[GT_DIG][8];
+        for (int cb = warp < 8 ? 0 : 2; cb < (warp < 8 ? 2 : 4); cb++) {
+          float v[DIG][8];
 #pragma unroll
-        for (int qq = 0; qq < GT_DIG; qq++) gt_ld8(tbase + qq * GT_COLS + cb * 8, v[qq]);
+          for (int qq = 0; qq < DIG; qq++) gt_ld8(tbase + qq * GT_COLS + cb * 8, v[qq]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            // sum_q' 128^q' P_q' = lo + 2^28 hi, each part exact in 64 bits (|P| <= 2^24)
+            int64_t lo = 0, hi = 0;
+#pragma unroll
+            for (int qq = 0; qq < 4; qq++) lo += (int64_t)__float2int_rn(v[qq][j]) << (7 * qq);
+#pragma unroll
+            for (int qq = 4; qq < DIG; qq++) hi += (int64_t)__float2int_rn(v[qq][j]) << (7 * (qq - 4));
+            const double val = fma((double)hi, 268435456.0, (double)lo);
+            contrib[(q * GT_COLS + c) * GT_COLS + cb * 8 + j] = ldexp(val, 7 * q - 94);
+          }
+        }
+      }
+    } else {
+      // epilogue: warp w reads TMEM lanes 32 q .. +31 (q = w % 4: operand row 32 q + c of
+      // term q, c = lane) and the columns 32 q' + 8 cb .. +7 (cb = w / 4) of the three
+      // terms q'; their sum is row (q, c) of the term-pair sums, columns 8 cb ..
+      const int q = warp & 3, cb = warp >> 2;
+      if (q < DIG) {
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16);
+        float v[DIG][8];
+#pragma unroll
+        for (int qq = 0; qq < DIG; qq++) gt_ld8(tbase + qq * GT_COLS + cb * 8, v[qq]);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::);
 #pragma unroll
         for (int j = 0; j < 8; j++) {
-          // sum_q' 128^q' P_q' = lo + 2^28 hi, each part exact in 64 bits (|P| <= 2^24)
-          int64_t lo = 0, hi = 0;
+          double val = 0;
 #pragma unroll
-          for (int qq = 0; qq < 4; qq++) lo += (int64_t)__float2int_rn(v[qq][j]) << (7 * qq);
-#pragma unroll
-          for (int qq = 4; qq < GT_DIG; qq++) hi += (int64_t)__float2int_rn(v[qq][j]) << (7 * (qq - 4));
-          const double val = fma((double)hi, 268435456.0, (double)lo);
-          contrib[(q * GT_COLS + c) * GT_COLS + cb * 8 + j] = ldexp(val, 7 * q - 94);
+          for (int qq = 0; qq < DIG; qq++) val += (double)v[qq][j];
+          contrib[(q * GT_COLS + c) * GT_COLS + cb * 8 + j] = val;
         }
       }
     }
@@ -326,7 +394,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
       if (a <= b && b < k) {
         double s = 0;
 #pragma unroll
-        for (int qq = 0; qq < GT_DIG; qq++) s += contrib[qq * GT_COLS * GT_COLS + e];
+        for (int qq = 0; qq < DIG; qq++) s += contrib[qq * GT_COLS * GT_COLS + e];
         atomicAdd(&G[((int64_t)m * 32 + a) * 32 + b], s);
       }
     }
@@ -340,24 +408,29 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(512));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(Md::TMEM_COLS));
 }
 
-size_t gram_tc_smem_bytes() { return 2 * GT_STAGE + GT_CONTRIB + 128; }
-
-cudaError_t launch_gram_tc(const float *Uh, const float *Ul, const float2 *rf, int64_t R, int k, int M,
-                           const unsigned *amax, double *G, int *status, cudaStream_t st) {
-  if (R <= 0 || M <= 0) return cudaSuccess;
+template <int DIG>
+static cudaError_t launch_mode(const float *Uh, const float *Ul, const float2 *rf, int64_t R, int k, int M,
+                               const unsigned *amax, double *G, int *status, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t items = ((R + GT_CHUNK - 1) / GT_CHUNK) * M;
   const int grid = (int)std::min<int64_t>(sms, items);
-  const size_t sm = gram_tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = 2 * GtMode<DIG>::STAGE + GtMode<DIG>::CONTRIB + 128;
+  cudaError_t e = cudaFuncSetAttribute(k_gram_tc<DIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_gram_tc<<<grid, GT_THREADS, sm, st>>>(Uh, Ul, rf, R, k, M, amax, G, status);
+  k_gram_tc<DIG><<<grid, GT_THREADS, sm, st>>>(Uh, Ul, rf, R, k, M, amax, G, status);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc(const float *Uh, const float *Ul, const float2 *rf, int64_t R, int k, int M,
+                           const unsigned *amax, double *G, int exact, int *status, cudaStream_t st) {
+  if (R <= 0 || M <= 0) return cudaSuccess;
+  return exact ? launch_mode<7>(Uh, Ul, rf, R, k, M, amax, G, status, st)
+               : launch_mode<3>(Uh, Ul, rf, R, k, M, amax, G, status, st);
 }
 
 }  // namespace pmd

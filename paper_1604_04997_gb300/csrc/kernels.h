@@ -32,11 +32,14 @@ cudaError_t launch_eval_counts(const uint32_t *arena, const int64_t *d_tab_off, 
 //       then [w0 w1 w2 entry] per term with a 96-bit weight (n64 terms whose basis value
 //       may leave [0, 2^32), then n32 terms), then [w0 w1 w2 w3][entry 0 0 0] per term
 //       with a 128-bit weight; the denominator block is [shift, 0, 0, 0, d^-1 mod 2^128];
-//   the variant map: each variant's root record offset (16 bits).
+//   the walk order: variants sorted by program shape (every leaf of a program is padded
+//     to one count of 64-bit- and of 32-bit-class terms): per position its program's
+//     root record offset and its variant index in the group (16 bits each), and runs
+//     [shape = n64 | n32 << 8 (0xFFFF: 128-bit weights), first position, count, 0].
 struct RankLayout {
   static constexpr int POINTS = 32;   // points per work unit: one per lane
   enum { H_B = 0, H_NLEV = 1, H_NCOND = 2, H_WORDS = 3, H_LEVEL_END = 4, H_OFF_BASIS = 12, H_OFF_COND = 13,
-         H_OFF_VARMAP = 14, HDR_WORDS = 16 };
+         H_OFF_VARMAP = 14, H_OFF_VIDMAP = 15, H_OFF_RUNS = 16, H_NRUNS = 17, HDR_WORDS = 20 };
 };
 struct RankArgs {
   const uint32_t *img;         // every group's image (weights filled per call)
@@ -124,10 +127,11 @@ struct FitHost {            // pinned host buffers filled by the fit (per model)
   double *ratio, *upd, *rr, *bb;
 };
 size_t fit_scratch_bytes(int64_t R, int k, int M);
-cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int precision,
+cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int M, int objective, int gram,
                        int steps, void *scratch, double *W_out, FitHost *host, int *status, cudaStream_t st);
 // exact tensor-core Gram matrices of the fit (adds into G, upper triangle, [M][32][32])
+// gram: 0 float-float (k_gram), 1 three bf16 terms on the tensor cores, 2 exact bf16 digits
 cudaError_t launch_gram_tc(const float *Uh, const float *Ul, const float2 *rf, int64_t R, int k, int M,
-                           const unsigned *amax, double *G, int *status, cudaStream_t st);
+                           const unsigned *amax, double *G, int exact, int *status, cudaStream_t st);
 
 }  // namespace pmd

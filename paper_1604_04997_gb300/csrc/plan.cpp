@@ -446,11 +446,13 @@ size_t emit_group(const Group &g0, std::vector<uint32_t> &img, std::vector<uint4
   // or 0, constant present] and its term records
   auto emit_leaf = [&](uint32_t rec, const LeafForm &lf, uint32_t den_off) {
     const uint32_t toff = (uint32_t)img.size();
-    if (lf.const_first) { add_target(toff, lf.const_c, 0); img.resize(img.size() + 4, 0); }
+    // the constant's weight comes first, zero when the leaf has no constant term
+    add_target(toff, lf.const_first ? lf.const_c : Contribs{}, 0);
+    img.resize(img.size() + 4, 0);
     for (auto *cls : {&lf.t64, &lf.t32})
       for (auto &t : *cls) {
         add_target((uint32_t)img.size(), t.second, 1);
-        img.insert(img.end(), {0u, 0u, 0u, (uint32_t)remap[t.first]});
+        img.insert(img.end(), {0u, 0u, 0u, (uint32_t)remap[t.first]});   // padding: entry 0, weight 0
       }
     for (auto &t : lf.twide) {
       add_target((uint32_t)img.size(), t.second, 0);
@@ -459,12 +461,33 @@ size_t emit_group(const Group &g0, std::vector<uint32_t> &img, std::vector<uint4
     img[rec + 0] = ((uint32_t)lf.t64.size() << 8) | ((uint32_t)lf.t32.size() << 16) | ((uint32_t)lf.twide.size() << 24);
     img[rec + 1] = toff;
     img[rec + 2] = den_off;
-    img[rec + 3] = lf.const_first ? 1u : 0u;
+    img[rec + 3] = 1;
   };
-  std::vector<uint32_t> prog_off(g0.progs.size());
+  // Every leaf of a program is padded to the program's widest shape (zero weights on
+  // basis entry 0), so that a program has one shape: its 64-bit- and 32-bit-class term
+  // counts, or no shape (0xFFFF) when it has 128-bit weights.  Variants are walked in
+  // runs of one shape, each run by a loop with fixed term counts.
+  std::vector<ProgForm> progs = g0.progs;
+  std::vector<uint32_t> shape(progs.size());
+  for (size_t pi = 0; pi < progs.size(); pi++) {
+    size_t n64 = 0, n32 = 0, nw = 0;
+    for (auto &pc : progs[pi].pieces)
+      for (auto &lf : pc.leaves) {
+        n64 = std::max(n64, lf.t64.size());
+        n32 = std::max(n32, lf.t32.size());
+        nw = std::max(nw, lf.twide.size());
+      }
+    for (auto &pc : progs[pi].pieces)
+      for (auto &lf : pc.leaves) {
+        while (lf.t64.size() < n64) lf.t64.push_back({0, Contribs{}});
+        while (lf.t32.size() < n32) lf.t32.push_back({0, Contribs{}});
+      }
+    shape[pi] = nw ? 0xFFFFu : (uint32_t)(n64 | (n32 << 8));
+  }
+  std::vector<uint32_t> prog_off(progs.size());
   prog_work.clear();
-  for (size_t pi = 0; pi < g0.progs.size(); pi++) {
-    const ProgForm &pf = g0.progs[pi];
+  for (size_t pi = 0; pi < progs.size(); pi++) {
+    const ProgForm &pf = progs[pi];
     const uint32_t base = (uint32_t)img.size();
     prog_off[pi] = base;
     prog_work.push_back(pf.work);
@@ -516,14 +539,36 @@ size_t emit_group(const Group &g0, std::vector<uint32_t> &img, std::vector<uint4
       throw BuildError{PM_ERR_UNSUPPORTED, "a table's ranking program exceeds " + std::to_string(PROG_MAX_WORDS * 4) +
                                                " bytes"};
   }
-  // variant -> program word offset (16 bits each)
+  // walk order: variants by shape (stable), as runs [shape, first position, count]; per
+  // position the program's root record and the variant's index in the group (16 bits each)
+  const size_t nvar = g0.var_prog.size();
+  std::vector<uint32_t> walk(nvar);
+  std::iota(walk.begin(), walk.end(), 0u);
+  std::stable_sort(walk.begin(), walk.end(),
+                   [&](uint32_t a, uint32_t b) { return shape[g0.var_prog[a]] < shape[g0.var_prog[b]]; });
+  auto put16 = [&](auto value_of) {
+    for (size_t q = 0; q < nvar; q += 2) {
+      uint32_t x = value_of(walk[q]);
+      if (q + 1 < nvar) x |= value_of(walk[q + 1]) << 16;
+      img.push_back(x);
+    }
+    pad4(img);
+  };
   img[RankLayout::H_OFF_VARMAP] = (uint32_t)img.size();
-  for (size_t v = 0; v < g0.var_prog.size(); v += 2) {
-    uint32_t x = prog_off[g0.var_prog[v]];
-    if (v + 1 < g0.var_prog.size()) x |= prog_off[g0.var_prog[v + 1]] << 16;
-    img.push_back(x);
+  put16([&](uint32_t v) { return prog_off[g0.var_prog[v]]; });
+  img[RankLayout::H_OFF_VIDMAP] = (uint32_t)img.size();
+  put16([&](uint32_t v) { return v; });
+  img[RankLayout::H_OFF_RUNS] = (uint32_t)img.size();
+  uint32_t nruns = 0;
+  for (size_t q = 0; q < nvar;) {
+    size_t e = q;
+    const uint32_t sh = shape[g0.var_prog[walk[q]]];
+    while (e < nvar && shape[g0.var_prog[walk[e]]] == sh) e++;
+    img.insert(img.end(), {sh, (uint32_t)q, (uint32_t)(e - q), 0u});
+    nruns++;
+    q = e;
   }
-  pad4(img);
+  img[RankLayout::H_NRUNS] = nruns;
   img[RankLayout::H_WORDS] = (uint32_t)img.size();
   return img.size();
 }
@@ -1011,7 +1056,7 @@ static pm_status tune_plan(pm_ctx *c, Plan *p, const int32_t *tables, const int3
   for (int cand_slice : {DEFAULT_SLICE, 2048, 1024, 512}) {
     pm_status s = replan(c, p, tables, var_off, pt_off, cand_slice);
     if (s) return s;
-    for (int cand_nw : {4, 8, 16}) {
+    for (int cand_nw : {4, 8}) {
       const int mx = std::max(1, pmd::rank_max_blocks_per_sm(cand_nw, p->img_words, p->basis_cap));
       for (int cand_bps = std::max(1, mx - 2); cand_bps <= mx; cand_bps++) {
         const int grid = c->n_sms * cand_bps;

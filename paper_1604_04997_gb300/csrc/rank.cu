@@ -142,6 +142,43 @@ struct TopK {
     for (int q = RK_TOPK - 1; q > 0; q--) k[q] = e < k[q - 1] ? k[q - 1] : (e < k[q] ? e : k[q]);
     if (e < k[0]) k[0] = e;
   }
+  // sort the 16 entries ascending (bitonic sorting network)
+  __device__ __forceinline__ void sort() {
+#pragma unroll
+    for (int kk = 2; kk <= RK_TOPK; kk <<= 1)
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int i = 0; i < RK_TOPK; i++) {
+          const int l = i ^ j;
+          if (l > i) {
+            const int64_t a = k[i], b = k[l];
+            const bool up = (i & kk) == 0;
+            k[i] = (a < b) == up ? a : b;
+            k[l] = (a < b) == up ? b : a;
+          }
+        }
+  }
+  // the 16 smallest of this list and RK_BUF sorted entries b (ascending)
+  __device__ __forceinline__ void merge_short(const int64_t (&b)[RK_BUF]) {
+#pragma unroll
+    for (int q = 0; q < RK_BUF; q++) {
+      const int i = RK_TOPK - 1 - q;
+      k[i] = b[q] < k[i] ? b[q] : k[i];
+    }
+    bitonic_clean();
+  }
+  __device__ __forceinline__ void bitonic_clean() {
+#pragma unroll
+    for (int d = RK_TOPK / 2; d > 0; d >>= 1)
+#pragma unroll
+      for (int q = 0; q < RK_TOPK; q++)
+        if ((q & d) == 0) {
+          const int64_t a = k[q], c = k[q + d];
+          k[q] = a < c ? a : c;
+          k[q + d] = a < c ? c : a;
+        }
+  }
   // the 16 smallest of this list and another sorted list (element q at p[q * stride]):
   // the elementwise minimum of this list and the other one reversed is a bitonic
   // sequence holding them, sorted by a four-stage bitonic merge
@@ -151,41 +188,36 @@ struct TopK {
       const int64_t e = p[(RK_TOPK - 1 - q) * stride];
       k[q] = e < k[q] ? e : k[q];
     }
-#pragma unroll
-    for (int d = RK_TOPK / 2; d > 0; d >>= 1)
-#pragma unroll
-      for (int q = 0; q < RK_TOPK; q++)
-        if ((q & d) == 0) {
-          const int64_t a = k[q], b = k[q + d];
-          k[q] = a < b ? a : b;
-          k[q + d] = a < b ? b : a;
-        }
+    bitonic_clean();
   }
 };
 
-// Candidate threshold: an entry (key48, variant) that the final 16th entry of the point
-// cannot exceed.  For a positive key, key48(S) < K <=> S < key_floor(K), and
-// key48(S) == K <=> key_floor(K) <= S < key_floor(K + 2^16), so the test needs no key.
+// Candidate threshold: an entry e = (key48, variant) that the point's final 16th entry
+// cannot exceed.  For a positive key K, key48(S) < K <=> S < key_floor(K) = lo and
+// key48(S) == K <=> lo <= S < key_floor(K + 2^16) = hi, so the common test is one
+// 128-bit compare S < hi; only then is the entry formed (a tie at K takes K itself).
+// Without a threshold, or with a key <= 0, lo = hi = the largest value and every
+// candidate's entry is formed and compared.
 struct Threshold {
   int64_t e;
   Acc128 lo, hi;
-  int vid;
-  bool pos;
   __device__ __forceinline__ void set(int64_t x) {
     e = x;
-    pos = x != RK_EMPTY && entry_key(x) > 0;
-    if (pos) {
+    if (x != RK_EMPTY && entry_key(x) > 0) {
       lo = key_floor(entry_key(x));
       hi = key_floor(entry_key(x) + 0x10000);
-      vid = entry_vid(x);
+    } else {
+      lo.lo = hi.lo = ~0ull;
+      lo.hi = hi.hi = (uint64_t)INT64_MAX;
     }
   }
-  __device__ __forceinline__ bool pass(const Acc128 &S, int v) const {
-    if (pos) return acc_less(S, lo) || (acc_less(S, hi) && v < vid);
-    if (e == RK_EMPTY) return true;
-    return pack_entry(acc_key(S), v) < e;
+  __device__ __forceinline__ bool maybe(const Acc128 &S) const { return acc_less(S, hi); }
+  __device__ __forceinline__ int64_t entry(const Acc128 &S, int v) const {
+    return acc_less(S, lo) ? pack_entry(acc_key(S), v) : (entry_key(e) | (uint32_t)v);
   }
 };
+
+template <int N> struct IC { static constexpr int value = N; };   // a compile-time count
 
 __device__ __forceinline__ int32_t pick4(const int32_t (&n)[4], uint32_t i) {
   int32_t x = n[0];
@@ -209,7 +241,7 @@ size_t rank_smem_bytes(int nw, int img_words, int basis_cap) {
 }
 
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) __maxnreg__(NW == 16 ? 128 : 96) k_rank(RankArgs a) {
+__global__ void __maxnreg__(96) k_rank(RankArgs a) {
   extern __shared__ __align__(16) uint8_t smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int img_cap = (a.img_words + 3) & ~3;
@@ -325,79 +357,182 @@ __global__ void __launch_bounds__(NW * 32) __maxnreg__(NW == 16 ? 128 : 96) k_ra
       th.set(RK_EMPTY);
       int nbuf = 0;
       auto flush = [&]() {
-        for (int b = 0; b < nbuf; b++) tk.insert(mybuf[b * 32]);
+        // the buffered entries, sorted, merged into the list by a bitonic network
+        int64_t b[RK_BUF];
+#pragma unroll
+        for (int q = 0; q < RK_BUF; q++) b[q] = q < nbuf ? mybuf[q * 32] : RK_EMPTY;
+#pragma unroll
+        for (int i = 0; i < RK_BUF; i++)
+#pragma unroll
+          for (int j = 0; j + 1 < RK_BUF - i; j++) {
+            const int64_t x = b[j], y = b[j + 1];
+            b[j] = x < y ? x : y;
+            b[j + 1] = x < y ? y : x;
+          }
+        tk.merge_short(b);
         nbuf = 0;
         if (tk.k[RK_TOPK - 1] < th.e) th.set(tk.k[RK_TOPK - 1]);
       };
-      int since = 0;
-      for (int v = warp; v < nv; v += NW) {
-        if (valid) {
-          // walk the program's nodes to its leaf: the table's conditions pick the piece,
-          // the post-op conditions pick the leaf (most programs are a single leaf)
-          uint4 N = *(const uint4 *)(img + vmap[v]);
-          while (N.x & 3) {
-            const uint32_t nc = (N.x >> 8) & 0xFF;
-            uint32_t bits = 0;
-            for (uint32_t c = 0; c < nc; c++) {
-              const uint32_t gi = c < 5 ? (N.y >> (6 * c)) & 63 : (N.z >> (6 * (c - 5))) & 63;
-              bits |= (((gi < 32 ? cm0 : cm1) >> (gi & 31)) & 1u) << c;
-            }
-            uint32_t off;
-            if ((N.x & 3) == 1) off = (N.x >> 16) + 4 * ((img[N.w + (bits >> 2)] >> (8 * (bits & 3))) & 0xFF);
-            else off = N.z + 4 * bits;
-            N = *(const uint4 *)(img + off);
+      const uint16_t *vidm = (const uint16_t *)(img + img[RankLayout::H_OFF_VIDMAP]);
+      const uint4 *runs = (const uint4 *)(img + img[RankLayout::H_OFF_RUNS]);
+      const int nruns = (int)img[RankLayout::H_NRUNS];
+      // walk a program's nodes to its leaf at this lane's point: the table's conditions
+      // pick the piece, the post-op conditions the leaf (most programs are one leaf)
+      auto leaf_of = [&](uint32_t off) -> uint4 {
+        uint4 N = *(const uint4 *)(img + off);
+        while (N.x & 3) {
+          const uint32_t nc = (N.x >> 8) & 0xFF;
+          uint32_t bits = 0;
+#pragma unroll 1
+          for (uint32_t c = 0; c < nc; c++) {
+            const uint32_t gi = c < 5 ? (N.y >> (6 * c)) & 63 : (N.z >> (6 * (c - 5))) & 63;
+            bits |= (((gi < 32 ? cm0 : cm1) >> (gi & 31)) & 1u) << c;
           }
-          // the leaf: S = sum over terms of weight * basis value, exact modulo 2^128
-          uint32_t A[4] = {0, 0, 0, 0};
-          const uint4 *rec = (const uint4 *)(img + N.y);
-          if (N.w) {
-            const uint4 c0 = *rec++;
-            A[0] = c0.x; A[1] = c0.y; A[2] = c0.z; A[3] = c0.w;
-          }
-          const uint32_t n64 = (N.x >> 8) & 0xFF, n32 = (N.x >> 16) & 0xFF, nwide = N.x >> 24;
-          for (uint32_t i = 0; i < n64; i++, rec++) {
-            const uint4 R = *rec;
-            const uint4 W = make_uint4(R.x, R.y, R.z, (uint32_t)((int32_t)R.z >> 31));
-            const uint32_t e = min(R.w, bmax) * 32 + lane;
-            mac128(A, W, (int64_t)((uint64_t)blo[e] | ((uint64_t)bhi[e] << 32)));
-          }
-          for (uint32_t i = 0; i < n32; i++, rec++) {
-            const uint4 R = *rec;
-            mac128_u32(A, make_uint4(R.x, R.y, R.z, (uint32_t)((int32_t)R.z >> 31)), blo[min(R.w, bmax) * 32 + lane]);
-          }
-          for (uint32_t i = 0; i < nwide; i++, rec += 2) {
-            const uint32_t e = min(rec[1].x, bmax) * 32 + lane;
-            mac128(A, rec[0], (int64_t)((uint64_t)blo[e] | ((uint64_t)bhi[e] << 32)));
-          }
-          Acc128 S;
-          S.lo = (uint64_t)A[0] | ((uint64_t)A[1] << 32);
-          S.hi = (uint64_t)A[2] | ((uint64_t)A[3] << 32);
-          if (N.z) {   // S = D * prediction exactly: shift by t, times d^-1 mod 2^128
-            const uint32_t *D = img + N.z;
-            const uint32_t sh = D[0] & 63;
-            const uint64_t lo = sh ? (S.lo >> sh) | (S.hi << (64 - sh)) : S.lo;
-            const uint64_t hi = (uint64_t)((int64_t)S.hi >> sh);
-            const uint64_t ilo = ld64(D + 4), ihi = ld64(D + 6);
-            S.lo = lo * ilo;
-            S.hi = __umul64hi(lo, ilo) + lo * ihi + hi * ilo;
-          }
-          const int vid = vbase + v;
-          if (th.pass(S, vid)) {
-            mybuf[nbuf * 32] = pack_entry(acc_key(S), vid);
-            nbuf++;
-          }
+          uint32_t o;
+          if ((N.x & 3) == 1) o = (N.x >> 16) + 4 * ((img[N.w + (bits >> 2)] >> (8 * (bits & 3))) & 0xFF);
+          else o = N.z + 4 * bits;
+          N = *(const uint4 *)(img + o);
         }
-        if (__any_sync(0xffffffffu, nbuf == RK_BUF)) flush();
-        if (++since == RK_EXCHANGE) {   // share 16th entries with the other warps
-          since = 0;
-          thrx[warp * 32 + lane] = tk.k[RK_TOPK - 1];
-          int64_t m = th.e;
+        return N;
+      };
+      auto term64 = [&](uint32_t (&A)[4], const uint4 &R) {
+        const uint32_t e = min(R.w, bmax) * 32 + lane;
+        mac128(A, make_uint4(R.x, R.y, R.z, (uint32_t)((int32_t)R.z >> 31)),
+               (int64_t)((uint64_t)blo[e] | ((uint64_t)bhi[e] << 32)));
+      };
+      auto term32 = [&](uint32_t (&A)[4], const uint4 &R) {
+        mac128_u32(A, make_uint4(R.x, R.y, R.z, (uint32_t)((int32_t)R.z >> 31)), blo[min(R.w, bmax) * 32 + lane]);
+      };
+      // S from the leaf's accumulator; a table with a denominator D holds D * prediction,
+      // divided exactly: a shift by t, then the inverse of d modulo 2^128
+      auto finish = [&](const uint32_t (&A)[4], uint32_t dz) -> Acc128 {
+        Acc128 S;
+        S.lo = (uint64_t)A[0] | ((uint64_t)A[1] << 32);
+        S.hi = (uint64_t)A[2] | ((uint64_t)A[3] << 32);
+        if (dz) {
+          const uint32_t *D = img + dz;
+          const uint32_t sh = D[0] & 63;
+          const uint64_t lo = sh ? (S.lo >> sh) | (S.hi << (64 - sh)) : S.lo;
+          const uint64_t hi = (uint64_t)((int64_t)S.hi >> sh);
+          const uint64_t ilo = ld64(D + 4), ihi = ld64(D + 6);
+          S.lo = lo * ilo;
+          S.hi = __umul64hi(lo, ilo) + lo * ihi + hi * ilo;
+        }
+        return S;
+      };
+      // any leaf: term counts read from the leaf record
+      auto evaluate = [&](int pos) -> Acc128 {
+        const uint4 N = leaf_of(vmap[pos]);
+        const uint4 *rec = (const uint4 *)(img + N.y);
+        const uint4 c0 = *rec++;
+        uint32_t A[4] = {c0.x, c0.y, c0.z, c0.w};
+        const uint32_t n64 = (N.x >> 8) & 0xFF, n32 = (N.x >> 16) & 0xFF, nwide = N.x >> 24;
+#pragma unroll 1
+        for (uint32_t i = 0; i < n64; i++) term64(A, *rec++);
+#pragma unroll 1
+        for (uint32_t i = 0; i < n32; i++) term32(A, *rec++);
+#pragma unroll 1
+        for (uint32_t i = 0; i < nwide; i++, rec += 2) {
+          const uint32_t e = min(rec[1].x, bmax) * 32 + lane;
+          mac128(A, rec[0], (int64_t)((uint64_t)blo[e] | ((uint64_t)bhi[e] << 32)));
+        }
+        return finish(A, N.z);
+      };
+      auto exchange = [&]() {   // share 16th entries with the other warps
+        thrx[warp * 32 + lane] = tk.k[RK_TOPK - 1];
+        int64_t m = th.e;
 #pragma unroll
-          for (int w = 0; w < NW; w++) {
-            const int64_t x = thrx[w * 32 + lane];
-            m = x < m ? x : m;
+        for (int w = 0; w < NW; w++) {
+          const int64_t x = thrx[w * 32 + lane];
+          m = x < m ? x : m;
+        }
+        if (m < th.e) th.set(m);
+      };
+      int since = 0;
+      // one candidate after the fill: one 128-bit compare; the few that may pass are buffered
+      auto consider = [&](const Acc128 &S, int pos) {
+        const bool m = valid && th.maybe(S);
+        if (__any_sync(0xffffffffu, m)) {
+          if (m) {
+            const int64_t e = th.entry(S, vbase + vidm[pos]);
+            if (e < th.e) {
+              mybuf[nbuf * 32] = e;
+              nbuf++;
+            }
           }
-          if (m < th.e) th.set(m);
+          if (__any_sync(0xffffffffu, nbuf == RK_BUF)) flush();
+        }
+        if (++since == RK_EXCHANGE) {
+          since = 0;
+          exchange();
+        }
+      };
+      // the first 16 positions of the warp fill its list, sorted once
+      const int fill_end = min(nv, RK_TOPK * NW);
+#pragma unroll 1
+      for (int f = 0, pos = warp; f < RK_TOPK; f++, pos += NW) {
+        int64_t e = RK_EMPTY;
+        if (pos < fill_end) {   // lanes without a valid point evaluate the box's corner
+          const int64_t x = pack_entry(acc_key(evaluate(pos)), vbase + vidm[pos]);
+          e = valid ? x : RK_EMPTY;
+        }
+#pragma unroll
+        for (int q = 0; q + 1 < RK_TOPK; q++) tk.k[q] = tk.k[q + 1];
+        tk.k[RK_TOPK - 1] = e;
+      }
+      tk.sort();
+      th.set(tk.k[RK_TOPK - 1]);
+      exchange();
+      // a run of one shape: term counts fixed at compile time, two variants per step
+      // (independent carry chains)
+      auto run_fixed = [&](auto c64, auto c32, int pos, int end) {
+        constexpr int N64 = decltype(c64)::value, N32 = decltype(c32)::value;
+        for (; pos + NW < end; pos += 2 * NW) {
+          const uint4 N1 = leaf_of(vmap[pos]), N2 = leaf_of(vmap[pos + NW]);
+          const uint4 *r1 = (const uint4 *)(img + N1.y), *r2 = (const uint4 *)(img + N2.y);
+          uint4 c = r1[0];
+          uint32_t A1[4] = {c.x, c.y, c.z, c.w};
+          c = r2[0];
+          uint32_t A2[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int i = 1; i <= N64; i++) {
+            term64(A1, r1[i]);
+            term64(A2, r2[i]);
+          }
+#pragma unroll
+          for (int i = N64 + 1; i <= N64 + N32; i++) {
+            term32(A1, r1[i]);
+            term32(A2, r2[i]);
+          }
+          const Acc128 S1 = finish(A1, N1.z), S2 = finish(A2, N2.z);
+          consider(S1, pos);
+          consider(S2, pos + NW);
+        }
+        if (pos < end) {
+          const uint4 N1 = leaf_of(vmap[pos]);
+          const uint4 *r1 = (const uint4 *)(img + N1.y);
+          const uint4 c = r1[0];
+          uint32_t A1[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+          for (int i = 1; i <= N64; i++) term64(A1, r1[i]);
+#pragma unroll
+          for (int i = N64 + 1; i <= N64 + N32; i++) term32(A1, r1[i]);
+          consider(finish(A1, N1.z), pos);
+        }
+      };
+      for (int r = 0; r < nruns; r++) {
+        const uint4 R = runs[r];
+        const int start = max((int)R.y, fill_end), end = (int)(R.y + R.z);
+        if (start >= end) continue;
+        const int pos = start + ((warp - start % NW) + NW) % NW;   // this warp's first position
+        switch (R.x) {
+#define PM_RUN(a, b) case (a) | ((b) << 8): run_fixed(IC<a>{}, IC<b>{}, pos, end); break;
+          PM_RUN(0, 1) PM_RUN(0, 2) PM_RUN(0, 3) PM_RUN(1, 1) PM_RUN(1, 2) PM_RUN(1, 3) PM_RUN(1, 6)
+          PM_RUN(1, 10) PM_RUN(2, 1) PM_RUN(2, 2) PM_RUN(3, 2) PM_RUN(3, 3) PM_RUN(4, 2) PM_RUN(5, 1)
+#undef PM_RUN
+          default:
+#pragma unroll 1
+            for (int p = pos; p < end; p += NW) consider(evaluate(p), p);
         }
       }
       flush();
@@ -460,7 +595,6 @@ static cudaError_t launch_nw(const RankArgs &args, int grid, cudaStream_t st) {
 cudaError_t launch_rank(const RankArgs &args, int nw, int grid, cudaStream_t st) {
   if (nw == 4) return launch_nw<4>(args, grid, st);
   if (nw == 8) return launch_nw<8>(args, grid, st);
-  if (nw == 16) return launch_nw<16>(args, grid, st);
   return cudaErrorInvalidValue;
 }
 
@@ -476,7 +610,6 @@ static int occupancy(int img_words, int basis_cap) {
 int rank_max_blocks_per_sm(int nw, int img_words, int basis_cap) {
   if (nw == 4) return occupancy<4>(img_words, basis_cap);
   if (nw == 8) return occupancy<8>(img_words, basis_cap);
-  if (nw == 16) return occupancy<16>(img_words, basis_cap);
   return 0;
 }
 

@@ -155,3 +155,25 @@ def test_fit_tensor_gram_ragged_rows_and_k12(env, R):
                 assert rep1[m]["rank"] == rep2[m]["rank"]
             p1, p2 = oracle.predict(F, W1[m][None])[:, 0], oracle.predict(F, W2[m][None])[:, 0]
             assert np.allclose(p1, p2, rtol=1e-7, atol=0), (k, m)
+
+
+def test_fit_ill_conditioned_uses_exact_gram(env):
+    """Two nearly collinear columns (cond(A) ~ 1e4-1e5, so cond(G) 2^-24 > 1): refinement
+    on the three-bf16-term Gram cannot converge, and PM_PREC_BF16X3 repeats the fit on
+    the exact digit Gram; the weights must still match the QR fit to 1e-8."""
+    ctx, dev = env
+    rng = np.random.default_rng(31)
+    F = W.fit_features(20000, 32, 31)
+    F[:, 9] = 2 * F[:, 8] + rng.integers(0, 4, size=len(F))   # almost dependent columns
+    wt = W.draw_weights(32, 3, 32)
+    T = W.synth_timings(F, wt, 33)
+    rc, rep, Wg = _fit(ctx, dev, F, T)
+    checked = 0
+    for m in range(3):
+        wref, rank, cond, res = oracle.fit(F, T[:, m], "relative")
+        if rank == 32 and cond <= 1e6:
+            assert cond > 1e3
+            assert _scaled_err(F, T, m, Wg[m], wref, "relative") <= 1e-8
+            assert rep[m]["status"] == 0
+            checked += 1
+    assert checked > 0

@@ -101,11 +101,51 @@ def _w96(r):
     return x - (1 << 96) if x >= (1 << 95) else x
 
 
-def program_value(img, v, vals, mask, den):
-    """The kernel's exact value of variant v: D * prediction, divided by D."""
-    off_v = img[14]
-    w = img[off_v + v // 2]
-    off = (w >> (16 * (v & 1))) & 0xFFFF
+def _u16(img, off, i):
+    return (img[off + i // 2] >> (16 * (i & 1))) & 0xFFFF
+
+
+def positions(img):
+    """The walk order: (position, variant index in the group) pairs, after checking
+    that the runs cover every position once and that each program's leaves all have
+    its run's shape."""
+    n_runs, off_r = img[17], img[16]
+    covered = []
+    for r in range(n_runs):
+        shape, first, count = img[off_r + 4 * r: off_r + 4 * r + 3]
+        covered += list(range(first, first + count))
+        for pos in range(first, first + count):
+            if shape != 0xFFFF:
+                for N in _leaves(img, _u16(img, img[14], pos)):
+                    assert (N[0] >> 8) & 0xFF == shape & 0xFF and (N[0] >> 16) & 0xFF == shape >> 8
+                    assert N[0] >> 24 == 0
+    assert covered == list(range(len(covered)))
+    vids = [_u16(img, img[15], p) for p in covered]
+    assert sorted(vids) == list(range(len(vids)))
+    return list(zip(covered, vids))
+
+
+def _leaves(img, off):
+    out, todo, seen = [], [off], set()
+    while todo:
+        o = todo.pop()
+        if o in seen:
+            continue
+        seen.add(o)
+        N = img[o: o + 4]
+        if N[0] & 3 == 0:
+            out.append(N)
+        elif N[0] & 3 == 2:
+            todo += [N[2] + 4 * i for i in range(1 << ((N[0] >> 8) & 0xFF))]
+        else:
+            nc = (N[0] >> 8) & 0xFF
+            todo += [(N[0] >> 16) + 4 * ((img[N[3] + (b >> 2)] >> (8 * (b & 3))) & 0xFF) for b in range(1 << nc)]
+    return out
+
+
+def program_value(img, pos, vals, mask, den):
+    """The kernel's exact value at walk position pos: D * prediction, divided by D."""
+    off = _u16(img, img[14], pos)
     N = img[off: off + 4]
     while N[0] & 3:
         nc = (N[0] >> 8) & 0xFF
@@ -122,14 +162,13 @@ def program_value(img, v, vals, mask, den):
         N = img[off: off + 4]
     n64, n32, nwide = (N[0] >> 8) & 0xFF, (N[0] >> 16) & 0xFF, N[0] >> 24
     r = N[1]
-    S = 0
-    if N[3]:
-        S += _wide(img[r: r + 4])
-        r += 4
+    assert N[3] == 1          # the constant's weight record is always present (zero if unused)
+    S = _wide(img[r: r + 4])
+    r += 4
     for i in range(n64 + n32):
         e = img[r + 3]
-        if i >= n64:
-            assert 0 <= vals[e] < (1 << 32)      # the 32-bit class
+        if i >= n64 and _w96(img[r: r + 3]):
+            assert 0 <= vals[e] < (1 << 32)      # the 32-bit class (padding terms weigh 0)
         S += _w96(img[r: r + 3]) * vals[e]
         r += 4
     for i in range(nwide):
@@ -149,11 +188,14 @@ def _check_group(images, pts, rng, trials=2):
         if trial == 0:
             Wcol = [abs(x) for x in Wcol]   # non-negative weights, as fitted times usually are
         fill(img, tgt, con, Wcol)
+        walk = positions(img)
+        assert len(walk) == len(tabs)
         for n in pts:
             vals, mask = group_basis(img, n)
-            for v, T in enumerate(tabs):
+            for pos, v in walk:
+                T = tabs[v]
                 ref = sum(Wcol[c] * x for c, x in enumerate(T.evaluate(n, check_magic=False)))
-                assert program_value(img, v, vals, mask, T.den) == ref, (v, n)
+                assert program_value(img, pos, vals, mask, T.den) == ref, (v, n)
     return img
 
 
@@ -190,8 +232,7 @@ def _sub_nodes(img, n_var):
     variants' roots."""
     seen, count, todo = set(), 0, []
     for v in range(n_var):
-        w = img[img[14] + v // 2]
-        todo.append((w >> (16 * (v & 1))) & 0xFFFF)
+        todo.append(_u16(img, img[14], v))
     while todo:
         off = todo.pop()
         if off in seen:
@@ -332,13 +373,15 @@ def _check_plan(ctx, b, slice_, rng, pts_per_template=3):
         for p in rng.choice(np.arange(b.pt_off[t], b.pt_off[t + 1]), pts_per_template, replace=False):
             n = [int(x) for x in b.points[p][:P]]
             vals, mask = group_basis(gimg, n)
-            for v in range(int(g0[3])):
+            walk = positions(gimg)
+            assert len(walk) == int(g0[3])
+            for pos, v in walk:
                 tid = int(b.tables[b.var_off[t] + g0[2] + v])
                 if tid not in tabs:
                     tabs[tid] = Table(ctx.table_image(tid))
                 T_ = tabs[tid]
                 ref = sum(Wcol[c] * x for c, x in enumerate(T_.evaluate(n, check_magic=False)))
-                assert program_value(gimg, v, vals, mask, T_.den) == ref, (gi, v, n)
+                assert program_value(gimg, pos, vals, mask, T_.den) == ref, (gi, v, n)
     return pl
 
 
