@@ -449,9 +449,12 @@ __global__ void __maxnreg__(96) k_rank(RankArgs a) {
         if (m < th.e) th.set(m);
       };
       int since = 0;
-      // one candidate after the fill: one 128-bit compare; the few that may pass are buffered
-      auto consider = [&](const Acc128 &S, int pos) {
+      // one candidate after the fill: one 128-bit compare; the few that may pass are
+      // buffered.  Returns true when the warp should stop to flush its buffers (a lane's
+      // buffer is full) or to exchange thresholds (every RK_EXCHANGE variants).
+      auto offer = [&](const Acc128 &S, int pos) -> bool {
         const bool m = valid && th.maybe(S);
+        bool stop = ++since >= RK_EXCHANGE;
         if (__any_sync(0xffffffffu, m)) {
           if (m) {
             const int64_t e = th.entry(S, vbase + vidm[pos]);
@@ -460,12 +463,9 @@ __global__ void __maxnreg__(96) k_rank(RankArgs a) {
               nbuf++;
             }
           }
-          if (__any_sync(0xffffffffu, nbuf == RK_BUF)) flush();
+          stop = stop || __any_sync(0xffffffffu, nbuf == RK_BUF);
         }
-        if (++since == RK_EXCHANGE) {
-          since = 0;
-          exchange();
-        }
+        return stop;
       };
       // the first 16 positions of the warp fill its list, sorted once
       const int fill_end = min(nv, RK_TOPK * NW);
@@ -483,32 +483,13 @@ __global__ void __maxnreg__(96) k_rank(RankArgs a) {
       tk.sort();
       th.set(tk.k[RK_TOPK - 1]);
       exchange();
-      // a run of one shape: term counts fixed at compile time, two variants per step
-      // (independent carry chains)
-      auto run_fixed = [&](auto c64, auto c32, int pos, int end) {
+      // the variants of a run of one shape (term counts fixed at compile time) from pos
+      // on, until the warp must stop; returns the next position.  The flush and the
+      // exchange sit once in the run loop below, outside the per-shape code, which keeps
+      // the kernel's hot code small.
+      auto run_fixed = [&](auto c64, auto c32, int pos, int end) -> int {
         constexpr int N64 = decltype(c64)::value, N32 = decltype(c32)::value;
-        for (; pos + NW < end; pos += 2 * NW) {
-          const uint4 N1 = leaf_of(vmap[pos]), N2 = leaf_of(vmap[pos + NW]);
-          const uint4 *r1 = (const uint4 *)(img + N1.y), *r2 = (const uint4 *)(img + N2.y);
-          uint4 c = r1[0];
-          uint32_t A1[4] = {c.x, c.y, c.z, c.w};
-          c = r2[0];
-          uint32_t A2[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-          for (int i = 1; i <= N64; i++) {
-            term64(A1, r1[i]);
-            term64(A2, r2[i]);
-          }
-#pragma unroll
-          for (int i = N64 + 1; i <= N64 + N32; i++) {
-            term32(A1, r1[i]);
-            term32(A2, r2[i]);
-          }
-          const Acc128 S1 = finish(A1, N1.z), S2 = finish(A2, N2.z);
-          consider(S1, pos);
-          consider(S2, pos + NW);
-        }
-        if (pos < end) {
+        while (pos < end) {
           const uint4 N1 = leaf_of(vmap[pos]);
           const uint4 *r1 = (const uint4 *)(img + N1.y);
           const uint4 c = r1[0];
@@ -517,22 +498,39 @@ __global__ void __maxnreg__(96) k_rank(RankArgs a) {
           for (int i = 1; i <= N64; i++) term64(A1, r1[i]);
 #pragma unroll
           for (int i = N64 + 1; i <= N64 + N32; i++) term32(A1, r1[i]);
-          consider(finish(A1, N1.z), pos);
+          const bool stop = offer(finish(A1, N1.z), pos);
+          pos += NW;
+          if (stop) break;
         }
+        return pos;
+      };
+      auto run_generic = [&](int pos, int end) -> int {
+        while (pos < end) {
+          const bool stop = offer(evaluate(pos), pos);
+          pos += NW;
+          if (stop) break;
+        }
+        return pos;
       };
       for (int r = 0; r < nruns; r++) {
         const uint4 R = runs[r];
         const int start = max((int)R.y, fill_end), end = (int)(R.y + R.z);
         if (start >= end) continue;
-        const int pos = start + ((warp - start % NW) + NW) % NW;   // this warp's first position
-        switch (R.x) {
-#define PM_RUN(a, b) case (a) | ((b) << 8): run_fixed(IC<a>{}, IC<b>{}, pos, end); break;
-          PM_RUN(0, 1) PM_RUN(0, 2) PM_RUN(0, 3) PM_RUN(1, 1) PM_RUN(1, 2) PM_RUN(1, 3) PM_RUN(1, 6)
-          PM_RUN(1, 10) PM_RUN(2, 1) PM_RUN(2, 2) PM_RUN(3, 2) PM_RUN(3, 3) PM_RUN(4, 2) PM_RUN(5, 1)
+        int pos = start + ((warp - start % NW) + NW) % NW;   // this warp's first position
+        while (pos < end) {
+          switch (R.x) {
+#define PM_RUN(a, b) case (a) | ((b) << 8): pos = run_fixed(IC<a>{}, IC<b>{}, pos, end); break;
+            PM_RUN(0, 1) PM_RUN(0, 2) PM_RUN(0, 3) PM_RUN(1, 1) PM_RUN(1, 2) PM_RUN(1, 3) PM_RUN(1, 6)
+            PM_RUN(1, 10) PM_RUN(2, 1) PM_RUN(2, 2) PM_RUN(3, 2) PM_RUN(3, 3) PM_RUN(4, 2) PM_RUN(5, 1)
 #undef PM_RUN
-          default:
-#pragma unroll 1
-            for (int p = pos; p < end; p += NW) consider(evaluate(p), p);
+            default:
+              pos = run_generic(pos, end);
+          }
+          if (__any_sync(0xffffffffu, nbuf == RK_BUF)) flush();
+          if (since >= RK_EXCHANGE) {
+            since = 0;
+            exchange();
+          }
         }
       }
       flush();
