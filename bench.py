@@ -396,8 +396,8 @@ def run_ours(args):
     peak_ops = sms * 128 * max_mhz * 1e6           # lane-instruction issue rate at the maximum clock
     achieved = evals * info["work_per_eval"] / (ms / 1e3)
     measured_ops = B.pmm_int_issue_rate()          # integer multiply-add / xor / add chains, every lane
-    traffic = _profile_traffic("eval_predict_topk_coupled_10000x4096.md" if coupled else
-                               "eval_predict_topk_batched_10000x4096.md",
+    traffic = _profile_traffic("rank_coupled_10000x4096.md" if coupled else
+                               "rank_batched_10000x4096.md",
                                ("rank.cu", "eval_common.cuh", "kernels.h", "plan.cpp"))
 
     if rank == 0:
