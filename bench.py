@@ -260,8 +260,8 @@ def _plain_form(ctx, bp, d_w, dev, stream, fused_idx, reps=2):
     return {"ms": eval_ms + rank_ms, "eval_counts_ms": eval_ms, "predict_topk_ms": rank_ms,
             "points_with_identical_top16": same / max(1, total),
             "note": "per template: pm_eval_counts (all 32 counts to HBM, 10.5 GB) then pm_predict_topk "
-                    "(PM_PREC_FP64, one model, per-point row lists); pm_predict_topk lays models on lanes "
-                    "(up to 64 per tile), so one model uses 1/64 of its product lanes"}
+                    "(PM_PREC_FP64, one model, per-point row lists; one row per lane for M <= 8): "
+                    "the same exact arithmetic and ranking as the fused launch"}
 
 
 def _serve_summary(ctx, bp, n_points, n_q):

@@ -413,6 +413,110 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_topk(const int64_t *_
   }
 }
 
+// The same top-k for few models (M <= 8): the 64-model tile above would leave most of
+// its products and warps idle, so here each lane owns one row (a warp takes 32
+// consecutive positions of the unit, the CTA 256) and computes its M exact sums; each
+// warp keeps its own sorted lists per model, and at the end of the unit warp m merges
+// the eight warps' lists of model m.  Same products, same keys, same (time, row) order.
+template <int MN>
+__global__ void __launch_bounds__(PR_WARPS * 32) k_predict_topk_rows(const int64_t *__restrict__ F, int64_t R, int k,
+                                                                     const double *__restrict__ W, int M,
+                                                                     const int64_t *__restrict__ rows,
+                                                                     const TopkUnit *__restrict__ units, int n_units,
+                                                                     int topk, double *__restrict__ part_t,
+                                                                     int64_t *__restrict__ part_r,
+                                                                     int64_t *__restrict__ top_idx,
+                                                                     double *__restrict__ top_t, int *status) {
+  __shared__ int64_t sw[PR_MAXK][MN];
+  __shared__ int sE[MN];
+  __shared__ double st[PR_WARPS][MN][32];
+  __shared__ int64_t sr[PR_WARPS][MN][32];
+  for (int m = threadIdx.x; m < MN; m += blockDim.x) {
+    const int E = m < M ? weight_exponent(W + (int64_t)m * k, k) : 0;
+    for (int i = 0; i < PR_MAXK; i++) sw[i][m] = (m < M && i < k) ? llrint(ldexp(W[(int64_t)m * k + i], E)) : 0;
+    sE[m] = E;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+    const TopkUnit U = units[u];
+    double lt[MN];
+    int64_t lr[MN];
+#pragma unroll
+    for (int m = 0; m < MN; m++) { lt[m] = TK_INF; lr[m] = INT64_MAX; }
+    for (int64_t t0 = U.p0 + 32 * warp; t0 < U.p1; t0 += 32 * PR_WARPS) {   // warp-uniform
+      const int64_t pos = t0 + lane;
+      int64_t row = -1;
+      if (pos < U.p1) {
+        row = rows ? rows[pos] : pos;
+        if (row < 0 || row >= R) {
+          atomicOr(status, ST_BAD_ROW);
+          row = -1;
+        }
+      }
+      uint32_t a[MN][4];
+#pragma unroll
+      for (int m = 0; m < MN; m++) a[m][0] = a[m][1] = a[m][2] = a[m][3] = 0;
+      if (row >= 0) {
+        const int64_t *f = F + row * k;
+        for (int i = 0; i < k; i++) {
+          const int64_t v = __ldg(f + i);
+#pragma unroll
+          for (int m = 0; m < MN; m++) acc_mad(a[m], v, sw[i][m]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < MN; m++) {
+        if (m < M) {   // warp-uniform
+          Acc128 A;
+          A.lo = (uint64_t)a[m][0] | ((uint64_t)a[m][1] << 32);
+          A.hi = (uint64_t)a[m][2] | ((uint64_t)a[m][3] << 32);
+          warp_list_merge(lt[m], lr[m], key_value(acc_key(A), sE[m]), row, row >= 0, topk, lane);
+        }
+      }
+    }
+    __syncthreads();   // the previous unit's merge has read st / sr
+#pragma unroll
+    for (int m = 0; m < MN; m++) {
+      st[warp][m][lane] = lt[m];
+      sr[warp][m][lane] = lr[m];
+    }
+    __syncthreads();
+    if (warp < M && warp < MN) {
+      const int m = warp;
+      double ft = TK_INF;
+      int64_t fr = INT64_MAX;
+      for (int w = 0; w < PR_WARPS; w++) {
+        const double t = st[w][m][lane];
+        const int64_t r = sr[w][m][lane];
+        warp_list_merge(ft, fr, t, r, lane < topk && r != INT64_MAX, topk, lane);
+      }
+      if (lane < topk) {
+        if (U.part < 0) {
+          const int64_t o = ((int64_t)U.g * M + m) * topk + lane;
+          top_idx[o] = fr == INT64_MAX ? -1 : fr;
+          top_t[o] = ft;
+        } else {
+          const int64_t o = ((int64_t)U.part * M + m) * topk + lane;
+          part_t[o] = ft;
+          part_r[o] = fr;
+        }
+      }
+    }
+  }
+}
+
+template <int MN>
+static void launch_topk_rows(const int64_t *F, int64_t R, int k, const double *W, int M, const int64_t *rows,
+                             const TopkUnit *units, int n_units, int topk, double *part_t, int64_t *part_r,
+                             int64_t *top_idx, double *top_t, int *status, cudaStream_t st) {
+  int per_sm = 1;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_predict_topk_rows<MN>, PR_WARPS * 32, 0);
+  const int grid = std::min(n_units, num_sms() * std::max(1, per_sm));
+  k_predict_topk_rows<MN><<<grid, PR_WARPS * 32, 0, st>>>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r,
+                                                          top_idx, top_t, status);
+}
+
 // Groups split over several units: one CTA per group merges the units' sorted lists.
 __global__ void __launch_bounds__(PR_WARPS * 32) k_topk_merge(const TopkMerge *__restrict__ merges, int M, int topk,
                                                               const double *__restrict__ part_t,
@@ -450,11 +554,18 @@ cudaError_t launch_predict_topk(const int64_t *F, int64_t R, int k, const double
                                 cudaStream_t st) {
   if (k > PR_MAXK || M > PR_MAXM || topk < 1 || topk > TOPK_MAX) return cudaErrorInvalidValue;
   if (n_units <= 0) return cudaSuccess;
-  const size_t sm = predict_topk_smem();
-  cudaFuncSetAttribute(k_predict_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  const int grid = std::min(n_units, num_sms() * 2);
-  k_predict_topk<<<grid, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r,
-                                                  top_idx, top_t, status);
+  if (M <= 8) {   // few models: one row per lane
+    if (M == 1) launch_topk_rows<1>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r, top_idx, top_t, status, st);
+    else if (M == 2) launch_topk_rows<2>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r, top_idx, top_t, status, st);
+    else if (M <= 4) launch_topk_rows<4>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r, top_idx, top_t, status, st);
+    else launch_topk_rows<8>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r, top_idx, top_t, status, st);
+  } else {
+    const size_t sm = predict_topk_smem();
+    cudaFuncSetAttribute(k_predict_topk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int grid = std::min(n_units, num_sms() * 2);
+    k_predict_topk<<<grid, PR_WARPS * 32, sm, st>>>(F, R, k, W, M, rows, units, n_units, topk, part_t, part_r,
+                                                    top_idx, top_t, status);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || n_merges == 0) return e;
   k_topk_merge<<<n_merges, PR_WARPS * 32, 0, st>>>(merges, M, topk, part_t, part_r, top_idx, top_t);

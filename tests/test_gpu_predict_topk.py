@@ -98,6 +98,23 @@ def test_topk_row_list_per_point(env, n_tables, n_points):
     _check(idx, tt, Tg, oracle.predict(F, Wm), seg_off, 16, rows)
 
 
+@pytest.mark.parametrize("M", [1, 2, 5])
+def test_topk_row_list_few_models(env, M):
+    """The plain per-call form of a tuning-space ranking: [tables][points][32] counts,
+    one group per point over 1,250 tables (two units and a merge per group), few
+    models (one row per lane), ties from duplicated tables."""
+    ctx, dev = env
+    n_tables, n_points = 1250, 9
+    R = n_tables * n_points
+    F = np.random.default_rng(M).integers(0, 2 ** 36, size=(R, 32), dtype=np.int64)
+    F[7 * n_points:8 * n_points] = F[3 * n_points:4 * n_points]     # table 7 duplicates table 3
+    Wm = W.draw_weights(32, M, 6 + M)
+    rows = (np.arange(n_tables)[None, :] * n_points + np.arange(n_points)[:, None]).ravel().astype(np.int64)
+    seg_off = np.arange(0, R + 1, n_tables, dtype=np.int64)
+    idx, tt, Tg = _run(ctx, dev, F, Wm, seg_off, 16, rows)
+    _check(idx, tt, Tg, oracle.predict(F, Wm), seg_off, 16, rows)
+
+
 def test_topk_one_group_of_a_million_rows(env):
     """1,000,000 rows x 32 features x 64 models, one group: the per-model top-16
     (977 units merged per model); sampled models against the oracle."""
