@@ -225,14 +225,26 @@ __device__ __forceinline__ Acc128 key_floor(int64_t k) {
   return r;
 }
 
-// Inverse of acc_key times 2^-E, for output.
+// Inverse of acc_key times 2^-E, for output: the value (1 + f 2^-56) 2^(e - E) with its
+// 56-bit fraction f rounded once to FP64's 52 bits (to nearest, ties to even).  The
+// double is assembled from its bit fields with integer operations (this GPU's FP64 pipe
+// is narrow); values outside FP64's normal range take ldexp of the same significand.
 __device__ __forceinline__ double key_value(int64_t k, int E) {
   if (k == 0) return 0.0;
   const bool neg = k < 0;
-  const int64_t a = neg ? -k : k;
+  const uint64_t a = (uint64_t)(neg ? -k : k);
   const int e = (int)(a >> 56) - 1;
-  const double m = 1.0 + ldexp((double)(a & ((1ll << 56) - 1)), -56);
-  const double v = ldexp(m, e - E);
+  const uint64_t f = a & ((1ull << 56) - 1);
+  const uint64_t rest = f & 15;
+  uint64_t g = (f >> 4) + ((rest > 8 || (rest == 8 && ((f >> 4) & 1))) ? 1 : 0);
+  int x = e - E + 1023;                               // biased exponent
+  if (g >> 52) {                                      // rounded up to 2: next binade
+    g = 0;
+    x++;
+  }
+  if (x >= 1 && x <= 2046)
+    return __longlong_as_double((long long)(((uint64_t)neg << 63) | ((uint64_t)x << 52) | g));
+  const double v = ldexp((double)((1ull << 52) | g), x - 1023 - 52);
   return neg ? -v : v;
 }
 

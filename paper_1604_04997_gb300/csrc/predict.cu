@@ -171,8 +171,18 @@ cudaError_t launch_predict(const int64_t *F, int64_t R, int k, const double *W, 
 
 // ---------------------------------------------------------------- argmin over rows per model
 
+// The order of the times as 64-bit integers: a double's bit pattern, with the magnitude
+// bits of negative values flipped, orders like the double itself for everything these
+// kernels produce (no NaN, no -0.0).  Comparing integers keeps the comparisons off this
+// GPU's narrow FP64 pipe.
+__device__ __forceinline__ int64_t time_order(double t) {
+  const int64_t b = __double_as_longlong(t);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
 __device__ __forceinline__ bool arg_less(double a, int64_t ra, double b, int64_t rb) {
-  return a < b || (a == b && ra < rb);
+  const int64_t ka = time_order(a), kb = time_order(b);
+  return ka < kb || (ka == kb && ra < rb);
 }
 
 __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_argmin_part(const int64_t *__restrict__ F, int64_t R,
@@ -322,7 +332,7 @@ __device__ __forceinline__ void warp_list_merge(double &lt, int64_t &lr, double 
       const int64_t orr = __shfl_xor_sync(FULL, br, o);
       if (arg_less(ot, orr, bt, br)) { bt = ot; br = orr; }
     }
-    const int win = __ffs(__ballot_sync(FULL, pass && t == bt && r == br)) - 1;
+    const int win = __ffs(__ballot_sync(FULL, pass && __double_as_longlong(t) == __double_as_longlong(bt) && r == br)) - 1;
     const int pos = __popc(__ballot_sync(FULL, lane < topk && arg_less(lt, lr, bt, br)));   // <= topk - 1
     const double ut = __shfl_up_sync(FULL, lt, 1);
     const int64_t ur = __shfl_up_sync(FULL, lr, 1);
@@ -339,7 +349,10 @@ __device__ __forceinline__ void warp_list_merge(double &lt, int64_t &lr, double 
 
 constexpr int TK_MODELS_PER_WARP = PR_MAXM / PR_WARPS;   // 8
 
-size_t predict_topk_smem() { return sizeof(PredictSmem) + sizeof(double) * PR_ROWS * PR_MAXM + sizeof(int64_t) * PR_ROWS; }
+// the tile's times, [row][model] with one pad column, so that a warp reading one
+// model's 32 rows hits 32 different banks
+constexpr int TK_TSTRIDE = PR_MAXM + 1;
+size_t predict_topk_smem() { return sizeof(PredictSmem) + sizeof(double) * PR_ROWS * TK_TSTRIDE + sizeof(int64_t) * PR_ROWS; }
 
 __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_topk(const int64_t *__restrict__ F, int64_t R, int k,
                                                                 const double *__restrict__ W, int M,
@@ -351,8 +364,8 @@ __global__ void __launch_bounds__(PR_WARPS * 32) k_predict_topk(const int64_t *_
                                                                 double *__restrict__ top_t, int *status) {
   extern __shared__ __align__(16) uint8_t smem_raw[];
   PredictSmem &S = *(PredictSmem *)smem_raw;
-  double(*tT)[PR_MAXM] = (double(*)[PR_MAXM])(smem_raw + sizeof(PredictSmem));
-  int64_t *tR = (int64_t *)(smem_raw + sizeof(PredictSmem) + sizeof(double) * PR_ROWS * PR_MAXM);
+  double(*tT)[TK_TSTRIDE] = (double(*)[TK_TSTRIDE])(smem_raw + sizeof(PredictSmem));
+  int64_t *tR = (int64_t *)(smem_raw + sizeof(PredictSmem) + sizeof(double) * PR_ROWS * TK_TSTRIDE);
   load_weights(S, W, M, k);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
