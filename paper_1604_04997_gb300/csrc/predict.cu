@@ -530,33 +530,47 @@ static void launch_topk_rows(const int64_t *F, int64_t R, int k, const double *W
                                                           top_idx, top_t, status);
 }
 
-// Groups split over several units: one CTA per group merges the units' sorted lists.
+// Groups split over several units: one CTA per (group, model) merges the units' sorted
+// lists of that model; its warps take every eighth block of 32 candidates, then warp 0
+// merges the eight warp lists.
 __global__ void __launch_bounds__(PR_WARPS * 32) k_topk_merge(const TopkMerge *__restrict__ merges, int M, int topk,
                                                               const double *__restrict__ part_t,
                                                               const int64_t *__restrict__ part_r,
                                                               int64_t *__restrict__ top_idx,
                                                               double *__restrict__ top_t) {
+  __shared__ double st[PR_WARPS][32];
+  __shared__ int64_t sr[PR_WARPS][32];
   const TopkMerge G = merges[blockIdx.x];
+  const int m = blockIdx.y;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = (int64_t)G.n_parts * topk;
-  for (int m = warp; m < M; m += PR_WARPS) {
-    double lt = TK_INF;
-    int64_t lr = INT64_MAX;
-    for (int64_t c0 = 0; c0 < n; c0 += 32) {
-      const int64_t c = c0 + lane;
-      double t = TK_INF;
-      int64_t r = INT64_MAX;
-      if (c < n) {
-        const int64_t o = (((int64_t)G.part0 + c / topk) * M + m) * topk + c % topk;
-        t = part_t[o];
-        r = part_r[o];
-      }
-      warp_list_merge(lt, lr, t, r, r != INT64_MAX, topk, lane);
+  double lt = TK_INF;
+  int64_t lr = INT64_MAX;
+  for (int64_t c0 = 32 * warp; c0 < n; c0 += 32 * PR_WARPS) {   // warp-uniform
+    const int64_t c = c0 + lane;
+    double t = TK_INF;
+    int64_t r = INT64_MAX;
+    if (c < n) {
+      const int64_t o = (((int64_t)G.part0 + c / topk) * M + m) * topk + c % topk;
+      t = part_t[o];
+      r = part_r[o];
+    }
+    warp_list_merge(lt, lr, t, r, r != INT64_MAX, topk, lane);
+  }
+  st[warp][lane] = lt;
+  sr[warp][lane] = lr;
+  __syncthreads();
+  if (warp == 0) {
+    double ft = TK_INF;
+    int64_t fr = INT64_MAX;
+    for (int w = 0; w < PR_WARPS; w++) {
+      const int64_t r = sr[w][lane];
+      warp_list_merge(ft, fr, st[w][lane], r, lane < topk && r != INT64_MAX, topk, lane);
     }
     if (lane < topk) {
       const int64_t o = ((int64_t)G.g * M + m) * topk + lane;
-      top_idx[o] = lr == INT64_MAX ? -1 : lr;
-      top_t[o] = lt;
+      top_idx[o] = fr == INT64_MAX ? -1 : fr;
+      top_t[o] = ft;
     }
   }
 }
@@ -581,7 +595,8 @@ cudaError_t launch_predict_topk(const int64_t *F, int64_t R, int k, const double
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || n_merges == 0) return e;
-  k_topk_merge<<<n_merges, PR_WARPS * 32, 0, st>>>(merges, M, topk, part_t, part_r, top_idx, top_t);
+  k_topk_merge<<<dim3((unsigned)n_merges, (unsigned)M), PR_WARPS * 32, 0, st>>>(merges, M, topk, part_t, part_r,
+                                                                              top_idx, top_t);
   return cudaGetLastError();
 }
 
