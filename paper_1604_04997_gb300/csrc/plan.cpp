@@ -664,6 +664,10 @@ static pm_status build_host_plan(pm_ctx *c, const int32_t *tables, const int32_t
   int &max_words = hp.max_words, &max_basis = hp.max_basis;
   double &total_work = hp.total_work;
   int64_t &evals = hp.evals;
+  // a ranking entry keeps the variant's index within its template in 16 bits
+  for (int t = 0; t < T; t++)
+    if (var_off[t + 1] < var_off[t] || var_off[t + 1] - var_off[t] > 65536)
+      return pm_set_error(PM_ERR_INVALID_ARG, "at most 65,536 variants per template");
   // Tables with the same image evaluate alike; they share one program in a group.
   std::map<std::vector<uint32_t>, int> image_id;
   std::vector<int> canon(c->tables.size(), -1);

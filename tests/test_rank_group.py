@@ -412,3 +412,25 @@ def test_plan_coupled_and_empty_template(ctx):
                         b.points, b.pt_off, b.n_distinct)
     pl = _check_plan(ctx, b2, 0, rng)
     assert any(u[1] == -1 for u in pl["units"].tolist())
+
+
+def test_plan_refuses_more_than_65536_variants(ctx):
+    """A ranking entry keeps the variant index within its template in 16 bits: a
+    template of 65,537 variants is refused before anything is built."""
+    L = B.lib()
+    f = L.pmx_rank_plan
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    f.restype = ctypes.c_int
+    f.argtypes = [vp, vp, vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp, sz, vp, sz, vp, sz, vp, sz, vp, sz, vp, sz,
+                  vp, sz]
+    from paper_1604_04997_gb300 import tuning
+    b = tuning.build(ctx, 16, 8)
+    tid = int(b.tables[0])
+    t = np.full(65537, tid, dtype=np.int32)
+    vo = np.array([0, 65537], dtype=np.int32)
+    po = np.array([0, 8], dtype=np.int64)
+    sizes = np.zeros(8, dtype=np.int64)
+    rc = f(ctx.h, t.ctypes.data, vo.ctypes.data, 1, po.ctypes.data, 0, sizes.ctypes.data,
+           None, 0, None, 0, None, 0, None, 0, None, 0, None, 0, None, 0)
+    assert B.ERRORS[rc] == "PM_ERR_INVALID_ARG"
+    assert "65,536" in B.lib().pm_last_error().decode()
