@@ -576,7 +576,7 @@ def run_other(args):
                                                            times["fp64_topk16_4096_groups"][0]}},
                     roofline={"bound": "hbm", "achieved": nbytes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                               "frac": nbytes / (ms / 1e3) / 1e9 / hbm,
-                              "traffic": _profile_traffic("predict_tc_1e6x32x64.md", ("predict_tc.cu",)),
+                              "traffic": _profile_traffic("predict_tc_1e6x32x64.md", ("predict_tc.cu", "mbar_wait.cuh")),
                               "kernel": "k_predict_tc",
                               "algorithmic_bytes": "256 B read + 8 B written per (row, model)"},
                     clocks=ck, gpu_launches=args.steps)

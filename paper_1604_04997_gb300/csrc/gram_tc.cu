@@ -37,6 +37,7 @@
 
 #include "eval_common.cuh"
 #include "kernels.h"
+#include "mbar_wait.cuh"
 
 namespace pmd {
 
@@ -47,7 +48,6 @@ constexpr int GT_COLS = 32;               // feature columns (padded)
 constexpr int GT_KS = 128;                // rows per stage (8 per warp): 8 MMA K-steps of 16
 constexpr int GT_CHUNK = 4096;            // rows per accumulation in TMEM
 constexpr uint32_t GT_SBO = (GT_KS / 8) * 128;          // 2048 B between 8-row operand groups
-constexpr unsigned long long GT_WAIT_NS = 2000000000ull;
 
 // the two modes: DIG terms per entry (7 exact digits, or 3 bf16 terms); operand rows
 // DIG * 32 (padded to MN); MMA N = DIG * 32; stage and TMEM sizes
@@ -79,32 +79,6 @@ __device__ __forceinline__ void gt_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
       "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ bool gt_try(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long gt_time() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
-  return t;
-}
-
-// bounded wait of the whole CTA on one mbarrier phase; false if any thread gave up
-__device__ __forceinline__ bool gt_wait(uint32_t mbar, uint32_t parity) {
-  int timed_out = 0;
-  const unsigned long long t0 = gt_time();
-  while (!gt_try(mbar, parity)) {
-    if (gt_time() - t0 > GT_WAIT_NS) { timed_out = 1; break; }
-  }
-  return !__syncthreads_or(timed_out);
 }
 
 // 8 consecutive fp32 columns of this thread's TMEM lane
@@ -274,7 +248,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
       if (st + 1 < nst) fetch(r0 + (int64_t)(st + 1) * GT_KS);
       // the buffer's previous MMAs must be done before it is rewritten
       if (issued[sbuf] > waited[sbuf]) {
-        if (!gt_wait(gt_saddr(&mbar[sbuf]), waited[sbuf] & 1)) { aborted = true; break; }
+        if (!cta_wait_bounded(gt_saddr(&mbar[sbuf]), waited[sbuf] & 1)) { aborted = true; break; }
         waited[sbuf]++;
       }
       uint32_t pk[DIG][4];
@@ -335,7 +309,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
     // every MMA of the chunk is complete once both buffers' commits have arrived
     for (int b = 0; b < 2 && !aborted; b++) {
       if (issued[b] > waited[b]) {
-        if (!gt_wait(gt_saddr(&mbar[b]), waited[b] & 1)) aborted = true;
+        if (!cta_wait_bounded(gt_saddr(&mbar[b]), waited[b] & 1)) aborted = true;
         else waited[b]++;
       }
     }
@@ -404,7 +378,7 @@ __global__ void __launch_bounds__(GT_THREADS, 1) k_gram_tc(const float *__restri
     if (tid == 0) atomicOr(status, ST_TIMEOUT);
     // let the MMAs in flight finish before TMEM is freed (bounded)
     for (int b = 0; b < 2; b++)
-      if (issued[b] > waited[b]) gt_wait(gt_saddr(&mbar[b]), waited[b] & 1);
+      if (issued[b] > waited[b]) cta_wait_bounded(gt_saddr(&mbar[b]), waited[b] & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::);
   __syncthreads();

@@ -28,6 +28,7 @@
 
 #include "eval_common.cuh"
 #include "kernels.h"
+#include "mbar_wait.cuh"
 
 namespace pmd {
 
@@ -38,7 +39,6 @@ constexpr int TC_THREADS = 256;
 constexpr uint32_t TC_A_BYTES = TC_ROWS * TC_K * 2;   // one bf16 split of a row tile: 8 KB
 constexpr uint32_t TC_B_BYTES = TC_N * TC_K * 2;      // one bf16 split of the weights: 4 KB
 constexpr uint32_t TC_F_BYTES = TC_ROWS * TC_K * 8;   // one raw row tile of counts: 32 KB
-constexpr unsigned long long TC_WAIT_NS = 2000000000ull;   // give up an mbarrier wait after 2 s
 
 // instruction descriptor of kind::f16: D fp32, A and B bf16, both K-major, N = 64, M = 128
 constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
@@ -68,22 +68,6 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
       "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
-  return t;
 }
 
 // Exact float -> double bit pattern with integer operations (the conversion
@@ -178,17 +162,6 @@ __device__ __forceinline__ uint32_t swz_chunk(int r, int c) {
   return (uint32_t)(line * 128 + (((c & 7) ^ (line & 7)) << 4));
 }
 
-// Bounded mbarrier wait shared by the whole CTA: returns true if every thread saw the
-// phase complete within TC_WAIT_NS.
-__device__ __forceinline__ bool cta_wait(uint32_t mbar, uint32_t parity) {
-  int timed_out = 0;
-  const unsigned long long t0 = globaltimer();
-  while (!mbar_try(mbar, parity)) {
-    if (globaltimer() - t0 > TC_WAIT_NS) { timed_out = 1; break; }
-  }
-  return !__syncthreads_or(timed_out);
-}
-
 // packed bf16 pair -> the two floats (low half, high half)
 __device__ __forceinline__ float bf_lo(uint32_t p) { return __uint_as_float(p << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t p) { return __uint_as_float(p & 0xFFFF0000u); }
@@ -277,7 +250,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant
   bool aborted = false;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * TC_ROWS;
-    if (!cta_wait(smem_addr(&mbar_ld), ph_ld)) { aborted = true; break; }
+    if (!cta_wait_bounded(smem_addr(&mbar_ld), ph_ld)) { aborted = true; break; }
     ph_ld ^= 1;
     // operands: counts -> float -> three exact bf16 splits, 16-byte K-major core-matrix rows
     // warp w converts row groups w and w + 8 (8 rows x 4 k-groups each); lane i + 8 s takes
@@ -319,7 +292,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant
       const int64_t next = tile + gridDim.x;
       if (next < ntiles) tile_load(smem_addr(sF), &fmap, (int32_t)(next * TC_ROWS), smem_addr(&mbar_ld));
     }
-    if (!cta_wait(smem_addr(&mbar_mma), ph_mma)) { aborted = true; break; }
+    if (!cta_wait_bounded(smem_addr(&mbar_mma), ph_mma)) { aborted = true; break; }
     ph_mma ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::);
     if (MODE == 0) {
@@ -398,7 +371,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_predict_tc(const __grid_constant
   if (aborted) {
     if (tid == 0) atomicOr(status, ST_TIMEOUT);
     // let a tile load still in flight land before the CTA exits (bounded)
-    cta_wait(smem_addr(&mbar_ld), ph_ld);
+    cta_wait_bounded(smem_addr(&mbar_ld), ph_ld);
   }
   if (MODE == 1 && !aborted) {
     // combine the four row quarters of each model, then publish this CTA's partial result
