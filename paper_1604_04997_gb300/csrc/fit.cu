@@ -12,8 +12,10 @@
 // does not converge (gram_tc.cu);
 // the k x k systems are factored by FP64 Cholesky.  Iterative refinement then
 // recovers the accuracy: r = b - A x is formed from the exact fixed-point product
-// F w (the prediction kernel's arithmetic) and an FP64 division, the correction
-// solves G d = A^T r with the same factor, and x += d.
+// F w (the prediction kernel's arithmetic), t - F w in FP64 and float-float products
+// with 1/t (about 2^-45), the correction solves G d = A^T r with the same factor, and
+// x += d.  FP64 is kept to the Cholesky factors, the substitutions and the sums: this
+// GPU's FP64 pipe is narrow.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,18 +69,63 @@ __global__ void k_scale(const int64_t *__restrict__ F, int64_t R, int k, const u
   }
 }
 
-// ---- row factors as float-float: 1/t (relative) or 1 (absolute); beta = 1 or t
+// A double as a float-float pair (hi + lo within 2^-47 of x) with integer operations
+// when its exponent is in [-70, 120] (this GPU's FP64 pipe is narrow; timings,
+// predictions and residuals are well inside that range), else by FP64 conversions.
+__device__ __forceinline__ float2 ff_of_double(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -70 || e > 120) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+  }
+  const uint32_t sgn = (uint32_t)(b >> 32) & 0x80000000u;
+  const uint64_t m = b & 0xFFFFFFFFFFFFFull;                      // 52 fraction bits
+  // hi: the leading one and the next 23 bits (truncated); lo: the 29 bits below, rounded
+  const float h = __uint_as_float(sgn | ((uint32_t)(e + 127) << 23) | (uint32_t)(m >> 29));
+  const float l = __uint2float_rn((uint32_t)(m & 0x1FFFFFFFu)) * __uint_as_float((uint32_t)(e - 52 + 127) << 23);
+  return make_float2(h, sgn ? -l : l);
+}
+
+// 1/t for t > 0 as float-float (within ~2^-46): FP32 reciprocal, one Newton step with
+// the residual formed by FMA; FP64 division outside [2^-100, 2^100].
+__device__ __forceinline__ float2 ff_recip(double t) {
+  const uint64_t b = (uint64_t)__double_as_longlong(t);
+  const int e = (int)((b >> 52) & 0x7FF) - 1023;
+  if (e < -100 || e > 100) {
+    const double r = 1.0 / t;
+    const float h = __double2float_rn(r);
+    return make_float2(h, __double2float_rn(r - (double)h));
+  }
+  const float2 tt = ff_of_double(t);
+  const float y = __frcp_rn(tt.x);
+  float res = __fmaf_rn(-tt.x, y, 1.0f);       // 1 - th y, exact: th y is within 2^-23 of 1
+  res = __fmaf_rn(-tt.y, y, res);              // - tl y
+  const float lo = __fmul_rn(y, res);
+  const float hi = __fadd_rn(y, lo);           // renormalise (Fast2Sum: |y| >= |lo|)
+  return make_float2(hi, __fsub_rn(lo, __fsub_rn(hi, y)));
+}
+
+// ---- row factors as float-float: 1/t (relative) or 1 (absolute); beta = 1 or t.  The
+// residual kernel reuses the relative row factor as 1/t.
 __global__ void k_rowfac(const double *__restrict__ T, int64_t n, int objective, float2 *__restrict__ rf,
-                         float2 *__restrict__ beta, double *__restrict__ inv, int *status) {
+                         float2 *__restrict__ beta, int *status) {
+  const int64_t big = __double_as_longlong(1e300);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double t = T[i];
-    if (!(t > 0.0) || t > 1e300) atomicOr(status, ST_BAD_INPUT);
-    const double r = objective == PM_FIT_RELATIVE ? 1.0 / t : 1.0;
-    const double b = objective == PM_FIT_RELATIVE ? 1.0 : t;
-    const float rh = __double2float_rn(r), bh = __double2float_rn(b);
-    rf[i] = make_float2(rh, __double2float_rn(r - (double)rh));
-    beta[i] = make_float2(bh, __double2float_rn(b - (double)bh));
-    inv[i] = r;   // 1/t once, reused by every residual
+    const int64_t tb = __double_as_longlong(t);   // 0 < t <= 1e300 (NaN excluded) by its bits
+    if (tb <= 0 || tb > big) {
+      atomicOr(status, ST_BAD_INPUT);
+      rf[i] = beta[i] = make_float2(0.f, 0.f);
+      continue;
+    }
+    if (objective == PM_FIT_RELATIVE) {
+      rf[i] = ff_recip(t);
+      beta[i] = make_float2(1.f, 0.f);
+    } else {
+      rf[i] = make_float2(1.f, 0.f);
+      beta[i] = ff_of_double(t);
+    }
   }
 }
 
@@ -299,8 +346,11 @@ __global__ void k_unscale(const double *__restrict__ x, int k, int M, const unsi
 }
 
 // ---- residual q = (b - A x) scaled for A^T q, from the exact product p = F w:
-// relative: r = 1 - p / t, q = r / t;   absolute: r = t - p, q = r.  Also sums r^2 and b^2.
-__global__ void k_residual(const double *__restrict__ P, const double *__restrict__ T, const double *__restrict__ inv,
+// relative: r = 1 - p / t = (t - p) (1/t), q = r / t;   absolute: r = t - p, q = r.
+// Also sums r^2 and b^2 (b = 1, or t).  Relative objective: t - p in FP64 (exact while
+// p is within a factor 2 of t), then float-float products with the row factor 1/t and
+// a float-float sum of r^2, so that one FP64 operation per element remains.
+__global__ void k_residual(const double *__restrict__ P, const double *__restrict__ T, const float2 *__restrict__ rf,
                            int64_t R, int M, int objective, float2 *__restrict__ Q, double *__restrict__ rr,
                            double *__restrict__ bb) {
   __shared__ double s_r[64], s_b[64];
@@ -309,20 +359,36 @@ __global__ void k_residual(const double *__restrict__ P, const double *__restric
   const int64_t n = R * M, stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool fixed_m = stride % M == 0;   // then every element of this thread has model i0 % M
+  float sr = 0.f, cr = 0.f;               // float-float sum of r^2 (relative)
   double ar = 0, ab = 0;
+  int64_t cnt = 0;
   for (int64_t i = i0; i < n; i += stride) {
-    const int m = (int)(i % M);
     const double t = T[i], p = P[i];
-    double r, q, b;
-    // relative: r = 1 - p/t = (t - p) (1/t); q = r / t
-    if (objective == PM_FIT_RELATIVE) { const double it = inv[i]; r = (t - p) * it; q = r * it; b = 1.0; }
-    else { r = t - p; q = r; b = t; }
-    const float qh = __double2float_rn(q);
-    Q[i] = make_float2(qh, __double2float_rn(q - (double)qh));
-    if (fixed_m) { ar += r * r; ab += b * b; }
-    else { atomicAdd(&s_r[m], r * r); atomicAdd(&s_b[m], b * b); }
+    if (objective == PM_FIT_RELATIVE) {
+      const float2 d = ff_of_double(t - p), it = rf[i];
+      const float2 r = ff_mul(d.x, d.y, it.x, it.y);
+      Q[i] = ff_mul(r.x, r.y, it.x, it.y);
+      const float2 r2 = ff_mul(r.x, r.y, r.x, r.y);
+      if (fixed_m) {
+        ff_acc(sr, cr, r2);
+        cnt++;
+      } else {
+        const int m = (int)(i % M);
+        atomicAdd(&s_r[m], (double)r2.x + (double)r2.y);
+        atomicAdd(&s_b[m], 1.0);
+      }
+    } else {
+      const double r = t - p;
+      Q[i] = ff_of_double(r);
+      if (fixed_m) { ar += r * r; ab += t * t; }
+      else { const int m = (int)(i % M); atomicAdd(&s_r[m], r * r); atomicAdd(&s_b[m], t * t); }
+    }
   }
-  if (fixed_m && i0 < n) { atomicAdd(&s_r[i0 % M], ar); atomicAdd(&s_b[i0 % M], ab); }
+  if (fixed_m && i0 < n) {
+    if (objective == PM_FIT_RELATIVE) { ar = (double)sr + (double)cr; ab = (double)cnt; }
+    atomicAdd(&s_r[i0 % M], ar);
+    atomicAdd(&s_b[i0 % M], ab);
+  }
   __syncthreads();
   if (threadIdx.x < M && threadIdx.x < 64) {
     atomicAdd(&rr[threadIdx.x], s_r[threadIdx.x]);
@@ -373,32 +439,46 @@ __global__ void __launch_bounds__(FIT_THREADS) k_atq(const float *__restrict__ U
   }
 }
 
-// ---- x += L^-T L^-1 g per model; records |d| / |x|
-__global__ void k_refine_update(const double *__restrict__ Lall, const double *__restrict__ g, int k, int M,
-                                const int *__restrict__ info, double *__restrict__ x, double *__restrict__ upd) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// ---- x += L^-T L^-1 g per model; records |d| / |x|.  One warp per model, lane a owns
+// row a: the forward and backward substitutions run column by column, each step one
+// division by lane a and one multiply-add in every lane below (or above) it, so the
+// FP64 latency of a step is paid once per column, not once per term.
+__global__ void __launch_bounds__(32) k_refine_update(const double *__restrict__ Lall, const double *__restrict__ g,
+                                                      int k, int M, const int *__restrict__ info,
+                                                      double *__restrict__ x, double *__restrict__ upd) {
+  const int m = blockIdx.x, a = threadIdx.x;
   if (m >= M) return;
   const unsigned dead = (unsigned)info[m * 4 + 3];
   const double *L = Lall + (int64_t)m * FIT_MAXK * FIT_MAXK;
-  double y[FIT_MAXK], d[FIT_MAXK];
-  for (int a = 0; a < k; a++) {
-    double s = (dead >> a) & 1 ? 0.0 : g[(int64_t)m * FIT_MAXK + a];
-    for (int p = 0; p < a; p++) s -= L[a * FIT_MAXK + p] * y[p];
-    y[a] = s / L[a * FIT_MAXK + a];
+  const bool live = a < k;
+  const double diag = live ? L[a * FIT_MAXK + a] : 1.0;
+  // L y = g: s_a = g_a - sum_{p<a} L[a][p] y_p, subtracted in the order p = 0, 1, ...
+  double s = (live && !((dead >> a) & 1)) ? g[(int64_t)m * FIT_MAXK + a] : 0.0;
+  double y = 0.0;
+  for (int c = 0; c < k; c++) {
+    if (a == c) y = s / diag;
+    const double yc = __shfl_sync(0xffffffffu, y, c);
+    if (live && a > c) s -= L[a * FIT_MAXK + c] * yc;
   }
-  double dn = 0, xn = 0;
-  for (int a = k - 1; a >= 0; a--) {
-    double s = y[a];
-    for (int p = a + 1; p < k; p++) s -= L[p * FIT_MAXK + a] * d[p];
-    d[a] = s / L[a * FIT_MAXK + a];
+  // L^T d = y: t_a = y_a - sum_{p>a} L[p][a] d_p
+  double t = y, d = 0.0;
+  for (int c = k - 1; c >= 0; c--) {
+    if (a == c) d = t / diag;
+    const double dc = __shfl_sync(0xffffffffu, d, c);
+    if (live && a < c) t -= L[c * FIT_MAXK + a] * dc;
   }
-  for (int a = 0; a < k; a++) {
-    if ((dead >> a) & 1) d[a] = 0;
-    x[(int64_t)m * FIT_MAXK + a] += d[a];
-    dn += d[a] * d[a];
-    xn += x[(int64_t)m * FIT_MAXK + a] * x[(int64_t)m * FIT_MAXK + a];
+  if (!live || ((dead >> a) & 1)) d = 0.0;
+  double xa = 0.0;
+  if (live) {
+    xa = x[(int64_t)m * FIT_MAXK + a] + d;
+    x[(int64_t)m * FIT_MAXK + a] = xa;
   }
-  upd[m] = xn > 0 ? sqrt(dn / xn) : 0.0;
+  double dn = d * d, xn = xa * xa;
+  for (int o = 16; o; o >>= 1) {
+    dn += __shfl_xor_sync(0xffffffffu, dn, o);
+    xn += __shfl_xor_sync(0xffffffffu, xn, o);
+  }
+  if (a == 0) upd[m] = xn > 0 ? sqrt(dn / xn) : 0.0;
 }
 
 // ------------------------------------------------------------------------------------ host side
@@ -411,7 +491,6 @@ size_t fit_scratch_bytes(int64_t R, int k, int M) {
   b += (size_t)R * M * 16;                         // row factors, beta
   b += (size_t)R * M * 8;                          // Q
   b += (size_t)R * M * 8;                          // P
-  b += (size_t)R * M * 8;                          // 1 / t
   b += (size_t)M * FIT_MAXK * FIT_MAXK * 8;        // G / L
   b += (size_t)M * FIT_MAXK * 8 * 3;               // rhs, x, g
   b += (size_t)M * (4 * 4 + 8 * 4);                // info, ratio, upd, rr, bb
@@ -435,7 +514,6 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   float2 *bt = (float2 *)carve(p, (size_t)R * M * 8);
   float2 *Q = (float2 *)carve(p, (size_t)R * M * 8);
   double *P = (double *)carve(p, (size_t)R * M * 8);
-  double *inv = (double *)carve(p, (size_t)R * M * 8);
   double *G = (double *)carve(p, (size_t)M * FIT_MAXK * FIT_MAXK * 8);
   double *rhs = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
   double *x = (double *)carve(p, (size_t)M * FIT_MAXK * 8);
@@ -456,7 +534,7 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   k_colmax<<<sms * 2, 256, 0, st>>>(F, R, k, cmax);
   k_scale<<<sms * 8, 256, 0, st>>>(F, R, k, cmax, U, Ul);
-  k_rowfac<<<sms * 8, 256, 0, st>>>(T, R * M, objective, rf, bt, inv, status);
+  k_rowfac<<<sms * 8, 256, 0, st>>>(T, R * M, objective, rf, bt, status);
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / std::max(1, M) + 1, (R + 255) / 256));
   const int64_t rpc = (R + chunks - 1) / chunks;
   k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, rf, R, k, M, rpc, amax);
@@ -480,16 +558,16 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
     cudaMemsetAsync(rr, 0, (size_t)M * 8, st);
     cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
     cudaMemsetAsync(g, 0, (size_t)M * FIT_MAXK * 8, st);
-    k_residual<<<sms * 4, 256, 0, st>>>(P, T, inv, R, M, objective, Q, rr, bb);
+    k_residual<<<sms * 4, 256, 0, st>>>(P, T, rf, R, M, objective, Q, rr, bb);
     k_atq<<<dim3(achunks, groups), FIT_THREADS, 0, st>>>(U, Ul, Q, R, k, M, arpc, amax, g);
-    k_refine_update<<<(M + 31) / 32, 32, 0, st>>>(G, g, k, M, info, x, upd);
+    k_refine_update<<<M, 32, 0, st>>>(G, g, k, M, info, x, upd);
   }
   k_unscale<<<(k * M + 255) / 256, 256, 0, st>>>(x, k, M, cmax, amax, W_out);
   // final residual for the report
   if ((e = launch_predict(F, R, k, W_out, M, PM_PREC_FP64, P, st)) != cudaSuccess) return e;
   cudaMemsetAsync(rr, 0, (size_t)M * 8, st);
   cudaMemsetAsync(bb, 0, (size_t)M * 8, st);
-  k_residual<<<sms * 4, 256, 0, st>>>(P, T, inv, R, M, objective, Q, rr, bb);
+  k_residual<<<sms * 4, 256, 0, st>>>(P, T, rf, R, M, objective, Q, rr, bb);
   cudaMemcpyAsync(host->info, info, (size_t)M * 16, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(host->ratio, ratio, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(host->upd, upd, (size_t)M * 8, cudaMemcpyDeviceToHost, st);
