@@ -571,6 +571,11 @@ def run_other(args):
                             "bytes_per_step": nbytes, "l2": "inputs (256 MB) and output (512 MB) larger than L2",
                             "argmin_only_ms": ms_arg, "argmin_only_gbs": nb_arg / (ms_arg / 1e3) / 1e9,
                             "fp64_accurate_ms": times["fp64_T"][0],
+                            # the exact path's integer work: ten 32-bit multiply-adds per 64 x 64-bit product
+                            "fp64_accurate_frac_of_lane_op_peak":
+                                R * M * 32 * 10 / (times["fp64_T"][0] / 1e3) /
+                                (torch.cuda.get_device_properties(dev).multi_processor_count * 128 *
+                                 float(_peaks().get("sm_max_mhz", 2070.0)) * 1e6),
                             "fp64_accurate_top16_ms": {"one group of 1e6 rows": times["fp64_topk16_one_group"][0],
                                                        "4096 groups of ~244 rows":
                                                            times["fp64_topk16_4096_groups"][0]}},
