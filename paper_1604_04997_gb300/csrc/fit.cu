@@ -537,9 +537,11 @@ cudaError_t launch_fit(const int64_t *F, int64_t R, int k, const double *T, int 
   k_rowfac<<<sms * 8, 256, 0, st>>>(T, R * M, objective, rf, bt, status);
   const int chunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / std::max(1, M) + 1, (R + 255) / 256));
   const int64_t rpc = (R + chunks - 1) / chunks;
-  k_acolmax<<<dim3(chunks, M), FIT_THREADS, 0, st>>>(U, rf, R, k, M, rpc, amax);
+  const int mchunks = (int)std::max<int64_t>(1, std::min<int64_t>(16 * sms / std::max(1, M) + 1, (R + 255) / 256));
+  k_acolmax<<<dim3(mchunks, M), FIT_THREADS, 0, st>>>(U, rf, R, k, M, (R + mchunks - 1) / mchunks, amax);
   const int groups = (M + ATQ_MODELS - 1) / ATQ_MODELS;
-  const int achunks = (int)std::max<int64_t>(1, std::min<int64_t>(4 * sms / groups + 1, (R + 255) / 256));
+  // enough row chunks for several CTAs per SM: the float-float sums are load-latency bound
+  const int achunks = (int)std::max<int64_t>(1, std::min<int64_t>(16 * sms / groups + 1, (R + 255) / 256));
   const int64_t arpc = (R + achunks - 1) / achunks;
   if (gram != 0) {
     // Gram on the tensor cores (three bf16 terms of A, or the exact digits of its 47-bit
