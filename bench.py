@@ -331,6 +331,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     ctx.sync_status(stream)
     info = ctx.plan_info(bp.tables, bp.var_off, bp.pt_off)
+    tuning = _tuning_summary(ctx, bp)
 
     clocks = Clocks(local)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -412,7 +413,7 @@ def run_ours(args):
                        "l2": "flushed (256 MB write) before every timed step",
                        "launch": {"warps_per_cta": info["nw"], "ctas": info["grid"], "units": info["units"],
                                   "ranking_groups": info["groups"], "slice": info["slice"] or None,
-                                  "tuned": info["tuned"]},
+                                  "tuned": info["tuned"], "tuning": tuning},
                        "timed_region_wall_ms": wall * 1e3,
                        "plain_form": plain, "vs_plain": plain["vs_plain"] if plain else None,
                        "serve": serve},
@@ -470,6 +471,24 @@ def _clocks_and_time(fn, steps, warmup, stream, flush=None):
     torch.cuda.synchronize()
     c = ck.stop()
     return sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / steps, c
+
+
+def _tuning_summary(ctx, bp):
+    """The autotuner's candidates for this plan, the default launch shape's time and
+    the chosen one's (None when the shape came from a tuning cache or tuning is off)."""
+    try:
+        log = ctx.plan_tune_log(bp.tables, bp.var_off, bp.pt_off)
+        if not log:
+            return None
+        default = [r for r in log if r[0] >= 2 ** 30 and int(r[1]) == 8]
+        best = min(log, key=lambda r: r[3])
+        return {"candidates": len(log),
+                "default_shape_ms": max(default, key=lambda r: r[2])[3] if default else None,
+                "chosen_shape_ms": best[3],
+                "chosen": {"variants_per_unit": None if best[0] >= 2 ** 30 else int(best[0]),
+                           "warps_per_cta": int(best[1]), "ctas_per_sm": int(best[2])}}
+    except Exception:
+        return None
 
 
 def _profile_traffic(md: str, sources) -> "int | None":

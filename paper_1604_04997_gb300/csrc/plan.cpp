@@ -1056,7 +1056,7 @@ static pm_status tune_plan(pm_ctx *c, Plan *p, const int32_t *tables, const int3
   CU(cudaEventCreate(&e1));
   float best = 1e30f;
   int b_slice = p->slice_max, b_nw = p->nw, b_bps = std::max(1, p->grid / c->n_sms);
-  p->tune_log.clear();
+  std::vector<std::array<double, 4>> log;   // every candidate (replanning resets the plan's own log)
   for (int cand_slice : {DEFAULT_SLICE, 2048, 1024, 512}) {
     pm_status s = replan(c, p, tables, var_off, pt_off, cand_slice);
     if (s) return s;
@@ -1076,14 +1076,13 @@ static pm_status tune_plan(pm_ctx *c, Plan *p, const int32_t *tables, const int3
         float ms = 0;
         CU(cudaEventElapsedTime(&ms, e0, e1));
         ms *= 0.5f;
-        p->tune_log.push_back({(double)cand_slice, (double)cand_nw, (double)cand_bps, (double)ms});
+        log.push_back({(double)cand_slice, (double)cand_nw, (double)cand_bps, (double)ms});
         if (ms < best) { best = ms; b_slice = cand_slice; b_nw = cand_nw; b_bps = cand_bps; }
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  std::vector<std::array<double, 4>> log = p->tune_log;
   pm_status s = replan(c, p, tables, var_off, pt_off, b_slice);
   if (s) return s;
   p->tune_log = log;
